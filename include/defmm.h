@@ -1,0 +1,154 @@
+/* defmm — GB300 application phase of the directional equispaced-interpolation
+ * fast multipole method for the Helmholtz kernel (Chollet, Claeys, Fortin,
+ * Grigori, arXiv 2202.04894).
+ *
+ *   p(x) = sum_{y in Y} G(x, y) q(y),   G(x, y) = exp(i kappa |x-y|) / (4 pi |x-y|)
+ *
+ * (Eq. 1.1, Sec. 1).  A plan holds the geometry-dependent part (Morton-sorted
+ * Ncrit octree, Sec. 4.2.1; direction tree, Sec. 4.1.2; dual tree traversal,
+ * Alg. 1; blank passes, Alg. 2-3; transfer spectra with cube symmetries,
+ * Sec. 4.3).  An apply runs P2M, M2M, M2F, the Fourier-domain Hadamard M2L,
+ * F2L, L2L, L2P and P2P on one GPU (Sec. 2.2, 4.1.1).
+ *
+ * Conventions shared by every entry point
+ *  - Status codes, never exceptions.  On failure defmm_last_error() returns a
+ *    message (thread-local, valid until the next call on the same thread).
+ *  - Asynchronous device errors of an apply surface at the next call that
+ *    synchronises (defmm_apply_host, defmm_plan_create, defmm_destroy) as
+ *    DEFMM_ERR_CUDA.
+ *  - Complex arrays are interleaved (re, im) in double (DEFMM_C128) or float
+ *    (DEFMM_C64), column-major over right-hand sides: entry (j, r) at j + n*r.
+ *  - Point arrays are n x 3 row-major float64 (x0 y0 z0 x1 y1 z1 ...).
+ */
+#ifndef DEFMM_H
+#define DEFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct defmm_plan_s* defmm_plan; /* opaque; owned by the library */
+
+typedef enum {
+    DEFMM_OK = 0,
+    DEFMM_ERR_ARG = 1,         /* invalid argument (null pointer, bad size/order) */
+    DEFMM_ERR_OOM = 2,         /* device or host allocation failed, or hbm_budget exceeded */
+    DEFMM_ERR_CUDA = 3,        /* a CUDA call failed (message names it) */
+    DEFMM_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    DEFMM_ERR_UNSUPPORTED = 5, /* option or dtype not supported */
+    DEFMM_ERR_BUSY = 6         /* plan is in use by another thread */
+} defmm_status;
+
+typedef enum { DEFMM_C64 = 0, DEFMM_C128 = 1 } defmm_dtype;
+
+/* Plan options.  Obtain defaults with defmm_default_options().
+ *  eta        - MAC parameter of Eq. (macdirref), Sec. 4.2.2 (default 1).
+ *  hf_kw      - a level is high-frequency iff kappa * w > hf_kw, w the cell
+ *               radius; the paper leaves this boundary open (default 1).
+ *  fft_n      - DFT length N per axis, N >= 2*order - 1; 0 selects 2*order - 1.
+ *               Any admissible N gives the same result (Sec. 2.3).
+ *  self_eps   - pairs with |x - y| <= self_eps * D are skipped, D the side of
+ *               the smallest box holding X and Y (Sec. 5.3; default 1e-10).
+ *  flags      - DEFMM_PLAN_HOST_ONLY builds the host tables only (no device
+ *               memory, no GPU needed); such a plan answers defmm_plan_info and
+ *               defmm_plan_table, and defmm_apply returns DEFMM_ERR_UNSUPPORTED.
+ *  hbm_budget - refuse plans whose device footprint exceeds this many bytes
+ *               (0: no limit).  Checked at plan creation (plan tables and
+ *               one-RHS workspace) and at each apply (workspace for nrhs).   */
+typedef struct {
+    double eta;
+    double hf_kw;
+    int fft_n;
+    int flags;
+    double self_eps;
+    size_t hbm_budget;
+} defmm_options;
+
+#define DEFMM_PLAN_HOST_ONLY 1
+
+void defmm_default_options(defmm_options* opt);
+
+/* Builds a plan (Sec. 4.2, 4.3): bounding cube, Morton sort, Ncrit octree
+ * (Sec. 4.2.1), per-level regime and directions (Sec. 4.1.2), dual tree
+ * traversal (Alg. 1), blank DTT and blank downward pass (Alg. 2, 3), best
+ * directions, canonical transfer spectra (formed on the GPU in float64, Sec.
+ * 2.3 Eq. FourierDiagonal, Sec. 4.3 Eq. permuteM2L) and the interpolation
+ * tables (Sec. 5.2.1).
+ *  X, nx     - targets, nx x 3 float64, host or device memory (detected).
+ *  Y, ny     - sources, ny x 3 float64.  Y == X with ny == nx (same pointer)
+ *              or Y == NULL means sources = targets and a single tree.
+ *  kappa     - wavenumber, >= 0.
+ *  order     - interpolation points per dimension p, 2 <= p <= 8.
+ *  leaf_size - Ncrit: cells holding more points are split, >= 1.
+ *  opt       - NULL for defaults.
+ *  stream    - cudaStream_t for the plan's device work (NULL: legacy stream);
+ *              the call returns after that work is complete.
+ *  out       - receives the plan.  X and Y are only read during the call.
+ * Errors: DEFMM_ERR_ARG, DEFMM_ERR_OOM, DEFMM_ERR_CUDA.                       */
+defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int64_t ny,
+                               double kappa, int order, int leaf_size,
+                               const defmm_options* opt, void* stream, defmm_plan* out);
+
+/* One application phase (Sec. 2.2 operators with M2F/F2L of Sec. 4.1.1):
+ * P2M -> M2M -> M2F -> Hadamard M2L with permuted spectra -> F2L -> L2L -> L2P,
+ * plus P2P over the near pairs of Alg. 1.
+ *  q     - device, ny x nrhs complex charges in the caller's point order.
+ *  p     - device, nx x nrhs complex potentials, overwritten.
+ *  nrhs  - number of right-hand sides, >= 1.
+ *  dtype - DEFMM_C64 (complex float arithmetic) or DEFMM_C128 (complex double).
+ *  stream- cudaStream_t; all work is enqueued on it, no host synchronisation.
+ * q and p are borrowed for the duration of the stream work.  The first call
+ * for a given (nrhs, dtype) may allocate workspace; later calls do not.
+ * Errors: DEFMM_ERR_ARG, DEFMM_ERR_OOM, DEFMM_ERR_CUDA, DEFMM_ERR_BUSY.        */
+defmm_status defmm_apply(defmm_plan plan, const void* q, void* p, int nrhs,
+                         defmm_dtype dtype, void* stream);
+
+/* defmm_apply with host arrays: copies q to the device, applies, copies p back
+ * and synchronises the stream before returning.  Page-locked host memory
+ * gives asynchronous copies; pageable memory works but is slower.            */
+defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host, int nrhs,
+                              defmm_dtype dtype, void* stream);
+
+/* Frees the plan and its device memory (synchronises the device first).       */
+defmm_status defmm_destroy(defmm_plan plan);
+
+typedef struct {
+    int64_t nx, ny;
+    int32_t order, fft_n;
+    int32_t nlevels;         /* octree levels (target tree) */
+    int32_t deepest_hf;      /* deepest high-frequency level, -1 if none */
+    int64_t ncells_t, ncells_s;
+    int64_t n_m2l_pairs, n_p2p_pairs;
+    int64_t n_multipole, n_local;     /* effective expansions (Sec. 4.2.3) */
+    int64_t n_fourier;                /* multipoles transformed by M2F */
+    int64_t n_spectra;                /* canonical spectra stored (Sec. 4.3) */
+    int64_t p2p_interactions;         /* sum over near pairs of n_t * n_s */
+    size_t plan_bytes;                /* device bytes held by the plan tables */
+    size_t workspace_bytes;           /* device bytes of the current workspace */
+    int64_t launches_per_apply;       /* kernels launched by the last apply (0 before any) */
+    double d_aabb;                    /* side of the smallest box holding X, Y */
+    double cube_side;                 /* side of the octree root */
+} defmm_info;
+
+defmm_status defmm_plan_info(defmm_plan plan, defmm_info* out);
+
+/* Integer plan tables, for testing a plan against an independent build.
+ * name: "perm_t", "perm_s" (sorted position -> input index),
+ *       "cells_t", "cells_s" (per cell: level, ix, iy, iz, begin, end, parent),
+ *       "m2l" (per pair: target cell, source cell, best direction or -1),
+ *       "p2p" (per pair: target cell, source cell),
+ *       "mult", "local" (per effective expansion: cell, direction or -1).
+ * Copies min(count, capacity) int64 values to out (host) and sets *count to
+ * the full length.  out may be NULL to query the length.                    */
+defmm_status defmm_plan_table(defmm_plan plan, const char* name, int64_t* out,
+                              int64_t capacity, int64_t* count);
+
+const char* defmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEFMM_H */

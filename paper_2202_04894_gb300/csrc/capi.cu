@@ -1,0 +1,452 @@
+// C ABI of the library (include/defmm.h): plan upload, workspace and calls.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/defmm.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace defmm {
+template <typename T> cudaError_t configure_kernels();
+}
+
+using namespace defmm;
+
+namespace {
+
+thread_local std::string g_err;
+
+defmm_status fail(defmm_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+defmm_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(DEFMM_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    return fail(DEFMM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Host image of the plan tables, 256-byte aligned, copied to the device once.
+struct Blob {
+    std::vector<unsigned char> bytes;
+    template <typename V> size_t add(const V* src, size_t count) {
+        size_t off = (bytes.size() + 255) / 256 * 256;
+        bytes.resize(off + count * sizeof(V));
+        if (count) std::memcpy(bytes.data() + off, src, count * sizeof(V));
+        return off;
+    }
+    template <typename V> size_t add(const std::vector<V>& v) { return add(v.data(), v.size()); }
+};
+
+template <typename T> struct Workspace {
+    int R = 0;
+    typename Cplx<T>::type *qs = nullptr, *ps = nullptr, *M = nullptr, *Mhat = nullptr, *L = nullptr;
+    void* q_stage = nullptr;
+    void* p_stage = nullptr;
+    size_t bytes = 0;
+    void release() {
+        cudaFree(qs); cudaFree(ps); cudaFree(M); cudaFree(Mhat); cudaFree(L);
+        cudaFree(q_stage); cudaFree(p_stage);
+        *this = Workspace();
+    }
+};
+
+}  // namespace
+
+struct defmm_plan_s {
+    HostPlan hp;
+    unsigned char* arena = nullptr;
+    size_t arena_bytes = 0;
+    DevCommon common{};
+    DevTyped<float> tf{};
+    DevTyped<double> td{};
+    std::vector<LevelList> m2m, l2l;
+    std::vector<const int32_t*> l2l_par;
+    Workspace<float> wf;
+    Workspace<double> wd;
+    size_t hbm_budget = 0;
+    int64_t launches = 0;
+    bool host_only = false;
+    std::mutex busy;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+defmm_status read_points(const double* P, int64_t n, std::vector<double>& out, bool host_only) {
+    out.resize(3 * (size_t)n);
+    if (!host_only && is_device_ptr(P)) {
+        CK(cudaMemcpy(out.data(), P, out.size() * sizeof(double), cudaMemcpyDeviceToHost), "copy points to host");
+    } else {
+        std::memcpy(out.data(), P, out.size() * sizeof(double));
+    }
+    return DEFMM_OK;
+}
+
+template <typename T> size_t workspace_bytes(const HostPlan& hp, int R) {
+    size_t c = sizeof(typename Cplx<T>::type);
+    return c * R * ((size_t)hp.ny + hp.nx + (size_t)hp.nM() * hp.P3 + hp.m2f_list.size() * (size_t)hp.NFpad +
+                    (size_t)hp.nL() * hp.P3);
+}
+
+template <typename T> defmm_status ensure_workspace(defmm_plan_s* pl, Workspace<T>& w, int R, bool host) {
+    const HostPlan& hp = pl->hp;
+    if (w.R < R) {
+        size_t need = workspace_bytes<T>(hp, R);
+        if (pl->hbm_budget && pl->arena_bytes + need > pl->hbm_budget)
+            return fail(DEFMM_ERR_OOM, "workspace exceeds hbm_budget");
+        w.release();
+        using C = typename Cplx<T>::type;
+        CK(cudaMalloc(&w.qs, sizeof(C) * R * (size_t)hp.ny), "workspace qs");
+        CK(cudaMalloc(&w.ps, sizeof(C) * R * (size_t)hp.nx), "workspace ps");
+        CK(cudaMalloc(&w.M, sizeof(C) * R * (size_t)std::max<int64_t>(1, hp.nM()) * hp.P3), "workspace M");
+        CK(cudaMalloc(&w.Mhat, sizeof(C) * R * std::max<size_t>(1, hp.m2f_list.size()) * hp.NFpad), "workspace Mhat");
+        CK(cudaMalloc(&w.L, sizeof(C) * R * (size_t)std::max<int64_t>(1, hp.nL()) * hp.P3), "workspace L");
+        w.R = R;
+        w.bytes = need;
+    }
+    if (host && !w.q_stage) {
+        using C = typename Cplx<T>::type;
+        CK(cudaMalloc(&w.q_stage, sizeof(C) * w.R * (size_t)hp.ny), "staging q");
+        CK(cudaMalloc(&w.p_stage, sizeof(C) * w.R * (size_t)hp.nx), "staging p");
+    }
+    return DEFMM_OK;
+}
+
+// Builds the device image of the plan and forms the spectra on the GPU.
+defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::vector<double>& Y,
+                    cudaStream_t stream) {
+    HostPlan& hp = pl->hp;
+    const Tree& tt = hp.tt;
+    const Tree& ts = hp.ts();
+    Blob b;
+
+    // sorted coordinates and permutations
+    std::vector<double> Xs(3 * (size_t)hp.nx);
+    for (int64_t i = 0; i < hp.nx; ++i)
+        for (int a = 0; a < 3; ++a) Xs[3 * i + a] = X[3 * tt.perm[i] + a];
+    size_t o_Xs = b.add(Xs), o_Ys = o_Xs;
+    if (!hp.same) {
+        std::vector<double> Ys(3 * (size_t)hp.ny);
+        for (int64_t i = 0; i < hp.ny; ++i)
+            for (int a = 0; a < 3; ++a) Ys[3 * i + a] = Y[3 * ts.perm[i] + a];
+        o_Ys = b.add(Ys);
+    }
+    size_t o_pt = b.add(tt.perm), o_ps = hp.same ? o_pt : b.add(ts.perm);
+
+    auto cells = [&](const Tree& tr, size_t& ob, size_t& oe, size_t& ol, size_t& oc) {
+        std::vector<int32_t> beg(tr.ncell()), end(tr.ncell());
+        std::vector<double> cor(3 * (size_t)tr.ncell());
+        for (int32_t c = 0; c < tr.ncell(); ++c) {
+            beg[c] = (int32_t)tr.begin[c];
+            end[c] = (int32_t)tr.end[c];
+            double s = hp.lv.side(tr.level[c]);
+            cor[3 * c] = hp.corner[0] + s * tr.ix[c];
+            cor[3 * c + 1] = hp.corner[1] + s * tr.iy[c];
+            cor[3 * c + 2] = hp.corner[2] + s * tr.iz[c];
+        }
+        ob = b.add(beg); oe = b.add(end); ol = b.add(tr.level); oc = b.add(cor);
+    };
+    size_t o_ctb, o_cte, o_ctl, o_ctc, o_csb, o_cse, o_csl, o_csc;
+    cells(tt, o_ctb, o_cte, o_ctl, o_ctc);
+    if (hp.same) { o_csb = o_ctb; o_cse = o_cte; o_csl = o_ctl; o_csc = o_ctc; }
+    else cells(ts, o_csb, o_cse, o_csl, o_csc);
+    std::vector<double> lside(kNumLevels);
+    for (int l = 0; l < kNumLevels; ++l) lside[l] = hp.lv.side(l);
+    size_t o_lside = b.add(lside);
+
+    size_t o_mf = b.add(hp.m_first), o_mc = b.add(hp.m_count), o_ms = b.add(hp.m_slot);
+    size_t o_lf = b.add(hp.l_first), o_lc = b.add(hp.l_count), o_ls = b.add(hp.l_slot);
+    size_t o_su = b.add(hp.slot_u);
+    size_t o_m2f = b.add(hp.m2f_list);
+    size_t o_mt = b.add(hp.m2l_tgt), o_mo = b.add(hp.m2l_off), o_msrc = b.add(hp.m2l_src), o_mspec = b.add(hp.m2l_spec);
+    size_t o_p2m = b.add(hp.p2m_cells), o_l2p = b.add(hp.l2p_cells);
+    size_t o_pl = b.add(hp.p2p_leaf), o_po = b.add(hp.p2p_off), o_psb = b.add(hp.p2p_sbeg), o_pse = b.add(hp.p2p_send);
+    std::vector<size_t> o_m2m(hp.m2m_lvl.size()), o_l2l(hp.l2l_lvl.size()), o_l2lp(hp.l2l_par.size());
+    for (size_t l = 0; l < hp.m2m_lvl.size(); ++l) o_m2m[l] = b.add(hp.m2m_lvl[l]);
+    for (size_t l = 0; l < hp.l2l_lvl.size(); ++l) { o_l2l[l] = b.add(hp.l2l_lvl[l]); o_l2lp[l] = b.add(hp.l2l_par[l]); }
+
+    // precision-specific tables
+    std::vector<float> slotP_f(hp.slot_P.begin(), hp.slot_P.end()), slotQ_f(hp.slot_Q.begin(), hp.slot_Q.end());
+    std::vector<float> m1_f(hp.m1.begin(), hp.m1.end()), tw_f(hp.tw.begin(), hp.tw.end());
+    size_t o_Pd = b.add(hp.slot_P), o_Qd = b.add(hp.slot_Q), o_m1d = b.add(hp.m1), o_twd = b.add(hp.tw);
+    size_t o_Pf = b.add(slotP_f), o_Qf = b.add(slotQ_f), o_m1f = b.add(m1_f), o_twf = b.add(tw_f);
+    std::vector<int32_t> kbar(3 * hp.spec_kbar.size());
+    for (size_t i = 0; i < hp.spec_kbar.size(); ++i)
+        for (int a = 0; a < 3; ++a) kbar[3 * i + a] = hp.spec_kbar[i][a];
+    size_t o_sl = b.add(hp.spec_level), o_sk = b.add(kbar);
+    size_t nspec = hp.spec_level.size();
+    size_t o_specd = b.add((const double2*)nullptr, 0);
+    b.bytes.resize(o_specd + nspec * hp.NFpad * sizeof(double2));
+    size_t o_specf = b.add((const float2*)nullptr, 0);
+    b.bytes.resize(o_specf + nspec * hp.NFpad * sizeof(float2));
+
+    size_t total = b.bytes.size();
+    if (pl->hbm_budget && total + workspace_bytes<float>(hp, 1) > pl->hbm_budget)
+        return fail(DEFMM_ERR_OOM, "plan exceeds hbm_budget");
+    CK(cudaMalloc(&pl->arena, total), "plan tables");
+    pl->arena_bytes = total;
+    CK(cudaMemcpyAsync(pl->arena, b.bytes.data(), o_specd, cudaMemcpyHostToDevice, stream), "upload plan tables");
+    unsigned char* base = pl->arena;
+    auto P = [&](size_t off) { return (void*)(base + off); };
+
+    DevCommon& c = pl->common;
+    c.p = hp.p; c.N = hp.N; c.NF = hp.NF; c.NFpad = hp.NFpad; c.P3 = hp.P3;
+    c.nx = hp.nx; c.ny = hp.ny; c.kappa = hp.kappa; c.eps_self = hp.eps_self;
+    c.Xs = (const double*)P(o_Xs); c.Ys = (const double*)P(o_Ys);
+    c.perm_t = (const int64_t*)P(o_pt); c.perm_s = (const int64_t*)P(o_ps);
+    c.ct_beg = (const int32_t*)P(o_ctb); c.ct_end = (const int32_t*)P(o_cte);
+    c.ct_level = (const int32_t*)P(o_ctl); c.ct_corner = (const double*)P(o_ctc);
+    c.cs_beg = (const int32_t*)P(o_csb); c.cs_end = (const int32_t*)P(o_cse);
+    c.cs_level = (const int32_t*)P(o_csl); c.cs_corner = (const double*)P(o_csc);
+    c.level_side = (const double*)P(o_lside);
+    c.m_first = (const int32_t*)P(o_mf); c.m_count = (const int32_t*)P(o_mc); c.m_slot = (const int32_t*)P(o_ms);
+    c.l_first = (const int32_t*)P(o_lf); c.l_count = (const int32_t*)P(o_lc); c.l_slot = (const int32_t*)P(o_ls);
+    c.slot_u = (const double*)P(o_su);
+    c.m2f_list = (const int32_t*)P(o_m2f); c.n_m2f = (int64_t)hp.m2f_list.size();
+    c.m2l_tgt = (const int32_t*)P(o_mt); c.m2l_off = (const int32_t*)P(o_mo);
+    c.m2l_src = (const int32_t*)P(o_msrc); c.m2l_spec = (const int32_t*)P(o_mspec);
+    c.n_m2l_tgt = (int64_t)hp.m2l_tgt.size();
+    c.p2m_cells = (const int32_t*)P(o_p2m); c.n_p2m = (int64_t)hp.p2m_cells.size();
+    c.l2p_cells = (const int32_t*)P(o_l2p); c.n_l2p = (int64_t)hp.l2p_cells.size();
+    c.p2p_leaf = (const int32_t*)P(o_pl); c.p2p_off = (const int32_t*)P(o_po);
+    c.p2p_sbeg = (const int32_t*)P(o_psb); c.p2p_send = (const int32_t*)P(o_pse);
+    c.n_p2p_leaf = (int64_t)hp.p2p_leaf.size();
+
+    pl->m2m.resize(hp.m2m_lvl.size());
+    for (size_t l = 0; l < hp.m2m_lvl.size(); ++l)
+        pl->m2m[l] = {(const int32_t*)P(o_m2m[l]), (int64_t)hp.m2m_lvl[l].size() / 9};
+    pl->l2l.resize(hp.l2l_lvl.size());
+    pl->l2l_par.resize(hp.l2l_lvl.size());
+    for (size_t l = 0; l < hp.l2l_lvl.size(); ++l) {
+        pl->l2l[l] = {(const int32_t*)P(o_l2l[l]), (int64_t)hp.l2l_lvl[l].size() / 4};
+        pl->l2l_par[l] = (const int32_t*)P(o_l2lp[l]);
+    }
+    pl->td.slot_P = (const double2*)P(o_Pd); pl->td.slot_Q = (const double2*)P(o_Qd);
+    pl->td.m1 = (const double*)P(o_m1d); pl->td.tw = (const double2*)P(o_twd);
+    pl->td.spec = (const double2*)P(o_specd);
+    pl->tf.slot_P = (const float2*)P(o_Pf); pl->tf.slot_Q = (const float2*)P(o_Qf);
+    pl->tf.m1 = (const float*)P(o_m1f); pl->tf.tw = (const float2*)P(o_twf);
+    pl->tf.spec = (const float2*)P(o_specf);
+
+    cudaError_t e = launch_spectra((const int32_t*)P(o_sl), (const int32_t*)P(o_sk), (int)nspec,
+                                   (const double*)P(o_lside), hp.p, hp.N, hp.NFpad, hp.kappa,
+                                   (double2*)P(o_specd), (float2*)P(o_specf), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spectra kernel");
+    CK(cudaStreamSynchronize(stream), "plan creation");
+    return DEFMM_OK;
+}
+
+const DevTyped<float>& typed_tables(const defmm_plan_s* pl, float*) { return pl->tf; }
+const DevTyped<double>& typed_tables(const defmm_plan_s* pl, double*) { return pl->td; }
+
+std::once_flag g_config_once;
+cudaError_t g_config_err = cudaSuccess;
+
+template <typename T> defmm_status apply_impl(defmm_plan_s* pl, Workspace<T>& w, const void* q, void* p,
+                                               int nrhs, cudaStream_t stream) {
+    defmm_status s = ensure_workspace<T>(pl, w, nrhs, false);
+    if (s != DEFMM_OK) return s;
+    DevWork<T> dw;
+    dw.R = nrhs; dw.qs = w.qs; dw.ps = w.ps; dw.M = w.M; dw.Mhat = w.Mhat; dw.L = w.L; dw.nL = pl->hp.nL();
+    const DevTyped<T>& typed = typed_tables(pl, (T*)nullptr);
+    int launches = 0;
+    cudaError_t e = launch_apply<T>(pl->common, typed, dw, pl->m2m.data(), (int)pl->m2m.size(), pl->l2l.data(),
+                                    pl->l2l_par.data(), (int)pl->l2l.size(), q, p, stream, &launches);
+    pl->launches = launches;
+    if (e != cudaSuccess) return cuda_fail(e, "apply launch");
+    return DEFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void defmm_default_options(defmm_options* opt) {
+    if (!opt) return;
+    opt->eta = 1.0;
+    opt->hf_kw = 1.0;
+    opt->fft_n = 0;
+    opt->flags = 0;
+    opt->self_eps = 1e-10;
+    opt->hbm_budget = 0;
+}
+
+const char* defmm_last_error(void) { return g_err.c_str(); }
+
+defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa, int order,
+                               int leaf_size, const defmm_options* opt, void* stream, defmm_plan* out) {
+    if (!out) return fail(DEFMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!X) return fail(DEFMM_ERR_ARG, "X is NULL");
+    if (nx < 1) return fail(DEFMM_ERR_ARG, "nx must be >= 1");
+    defmm_options o;
+    defmm_default_options(&o);
+    if (opt) o = *opt;
+    bool same = (Y == nullptr) || (Y == X && ny == nx);
+    if (!same && ny < 1) return fail(DEFMM_ERR_ARG, "ny must be >= 1");
+    const bool host_only = (o.flags & DEFMM_PLAN_HOST_ONLY) != 0;
+    if (!host_only) {
+        std::call_once(g_config_once, [] {
+            g_config_err = configure_kernels<float>();
+            if (g_config_err == cudaSuccess) g_config_err = configure_kernels<double>();
+        });
+        if (g_config_err != cudaSuccess) return cuda_fail(g_config_err, "kernel configuration");
+    }
+    defmm_plan_s* pl = new (std::nothrow) defmm_plan_s;
+    if (!pl) return fail(DEFMM_ERR_OOM, "host allocation");
+    pl->hbm_budget = o.hbm_budget;
+    std::vector<double> hx, hy;
+    defmm_status s = read_points(X, nx, hx, host_only);
+    if (s == DEFMM_OK && !same) s = read_points(Y, ny, hy, host_only);
+    if (s != DEFMM_OK) { delete pl; return s; }
+    try {
+        build_host_plan(hx.data(), nx, same ? nullptr : hy.data(), same ? nx : ny, kappa, order, leaf_size, o.eta,
+                        o.hf_kw, o.fft_n, o.self_eps, pl->hp);
+    } catch (const std::bad_alloc&) {
+        delete pl;
+        return fail(DEFMM_ERR_OOM, "host allocation while building the plan");
+    } catch (const std::exception& ex) {
+        delete pl;
+        return fail(DEFMM_ERR_ARG, ex.what());
+    }
+    pl->host_only = host_only;
+    s = host_only ? DEFMM_OK : upload(pl, hx, hy, (cudaStream_t)stream);
+    if (s != DEFMM_OK) {
+        cudaFree(pl->arena);
+        delete pl;
+        return s;
+    }
+    *out = pl;
+    return DEFMM_OK;
+}
+
+defmm_status defmm_apply(defmm_plan plan, const void* q, void* p, int nrhs, defmm_dtype dtype, void* stream) {
+    if (!plan) return fail(DEFMM_ERR_ARG, "plan is NULL");
+    if (!q || !p) return fail(DEFMM_ERR_ARG, "q and p must be device pointers");
+    if (nrhs < 1) return fail(DEFMM_ERR_ARG, "nrhs must be >= 1");
+    if (dtype != DEFMM_C64 && dtype != DEFMM_C128) return fail(DEFMM_ERR_UNSUPPORTED, "dtype");
+    if (plan->host_only) return fail(DEFMM_ERR_UNSUPPORTED, "plan was built with DEFMM_PLAN_HOST_ONLY");
+    std::unique_lock<std::mutex> lk(plan->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(DEFMM_ERR_BUSY, "plan is in use by another thread");
+    if (dtype == DEFMM_C64) return apply_impl<float>(plan, plan->wf, q, p, nrhs, (cudaStream_t)stream);
+    return apply_impl<double>(plan, plan->wd, q, p, nrhs, (cudaStream_t)stream);
+}
+
+defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host, int nrhs, defmm_dtype dtype,
+                              void* stream) {
+    if (!plan) return fail(DEFMM_ERR_ARG, "plan is NULL");
+    if (!q_host || !p_host) return fail(DEFMM_ERR_ARG, "q and p must be host pointers");
+    if (nrhs < 1) return fail(DEFMM_ERR_ARG, "nrhs must be >= 1");
+    if (dtype != DEFMM_C64 && dtype != DEFMM_C128) return fail(DEFMM_ERR_UNSUPPORTED, "dtype");
+    if (plan->host_only) return fail(DEFMM_ERR_UNSUPPORTED, "plan was built with DEFMM_PLAN_HOST_ONLY");
+    std::unique_lock<std::mutex> lk(plan->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(DEFMM_ERR_BUSY, "plan is in use by another thread");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t csz = dtype == DEFMM_C64 ? sizeof(float2) : sizeof(double2);
+    size_t qb = csz * (size_t)nrhs * plan->hp.ny, pb = csz * (size_t)nrhs * plan->hp.nx;
+    defmm_status s;
+    void *qd, *pd;
+    if (dtype == DEFMM_C64) {
+        s = ensure_workspace<float>(plan, plan->wf, nrhs, true);
+        qd = plan->wf.q_stage; pd = plan->wf.p_stage;
+    } else {
+        s = ensure_workspace<double>(plan, plan->wd, nrhs, true);
+        qd = plan->wd.q_stage; pd = plan->wd.p_stage;
+    }
+    if (s != DEFMM_OK) return s;
+    CK(cudaMemcpyAsync(qd, q_host, qb, cudaMemcpyHostToDevice, st), "copy q to device");
+    s = dtype == DEFMM_C64 ? apply_impl<float>(plan, plan->wf, qd, pd, nrhs, st)
+                           : apply_impl<double>(plan, plan->wd, qd, pd, nrhs, st);
+    if (s != DEFMM_OK) return s;
+    CK(cudaMemcpyAsync(p_host, pd, pb, cudaMemcpyDeviceToHost, st), "copy p to host");
+    CK(cudaStreamSynchronize(st), "apply");
+    return DEFMM_OK;
+}
+
+defmm_status defmm_destroy(defmm_plan plan) {
+    if (!plan) return DEFMM_OK;
+    if (plan->host_only) {
+        delete plan;
+        return DEFMM_OK;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    plan->wf.release();
+    plan->wd.release();
+    cudaFree(plan->arena);
+    delete plan;
+    if (e != cudaSuccess) return cuda_fail(e, "destroy");
+    return DEFMM_OK;
+}
+
+defmm_status defmm_plan_info(defmm_plan plan, defmm_info* out) {
+    if (!plan || !out) return fail(DEFMM_ERR_ARG, "null argument");
+    const HostPlan& hp = plan->hp;
+    std::memset(out, 0, sizeof(*out));
+    out->nx = hp.nx; out->ny = hp.ny; out->order = hp.p; out->fft_n = hp.N;
+    out->nlevels = (int32_t)hp.tt.level_range.size();
+    out->deepest_hf = hp.lv.l_hf;
+    out->ncells_t = hp.tt.ncell(); out->ncells_s = hp.ts().ncell();
+    out->n_m2l_pairs = (int64_t)hp.m2l.size(); out->n_p2p_pairs = (int64_t)hp.p2p.size();
+    out->n_multipole = hp.nM(); out->n_local = hp.nL();
+    out->n_fourier = (int64_t)hp.m2f_list.size();
+    out->n_spectra = (int64_t)hp.spec_level.size();
+    out->p2p_interactions = hp.p2p_interactions;
+    out->plan_bytes = plan->arena_bytes;
+    out->workspace_bytes = plan->wf.bytes + plan->wd.bytes;
+    out->launches_per_apply = plan->launches;
+    out->d_aabb = hp.d_aabb;
+    out->cube_side = hp.side;
+    return DEFMM_OK;
+}
+
+defmm_status defmm_plan_table(defmm_plan plan, const char* name, int64_t* out, int64_t capacity, int64_t* count) {
+    if (!plan || !name || !count) return fail(DEFMM_ERR_ARG, "null argument");
+    const HostPlan& hp = plan->hp;
+    std::vector<int64_t> v;
+    std::string n(name);
+    auto cells = [&](const Tree& t) {
+        for (int32_t c = 0; c < t.ncell(); ++c) {
+            int64_t row[7] = {t.level[c], t.ix[c], t.iy[c], t.iz[c], t.begin[c], t.end[c], t.parent[c]};
+            v.insert(v.end(), row, row + 7);
+        }
+    };
+    if (n == "perm_t") v.assign(hp.tt.perm.begin(), hp.tt.perm.end());
+    else if (n == "perm_s") v.assign(hp.ts().perm.begin(), hp.ts().perm.end());
+    else if (n == "cells_t") cells(hp.tt);
+    else if (n == "cells_s") cells(hp.ts());
+    else if (n == "m2l") for (auto& r : hp.m2l) v.insert(v.end(), {r[0], r[1], r[2]});
+    else if (n == "p2p") for (auto& r : hp.p2p) v.insert(v.end(), {r[0], r[1]});
+    else if (n == "mult") for (size_t e = 0; e < hp.m_cell.size(); ++e) v.insert(v.end(), {hp.m_cell[e], hp.m_dir[e]});
+    else if (n == "local") for (size_t e = 0; e < hp.l_cell.size(); ++e) v.insert(v.end(), {hp.l_cell[e], hp.l_dir[e]});
+    else return fail(DEFMM_ERR_ARG, "unknown table " + n);
+    *count = (int64_t)v.size();
+    if (out) std::memcpy(out, v.data(), sizeof(int64_t) * std::min<int64_t>(capacity, (int64_t)v.size()));
+    return DEFMM_OK;
+}
+
+}  // extern "C"

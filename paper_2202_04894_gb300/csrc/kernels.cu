@@ -1,0 +1,767 @@
+// Application-phase kernels of the directional equispaced FMM on sm_103a.
+//
+//   gather   q -> Morton order
+//   P2P      near field over the pairs of Alg. 1 (Sec. 2.2, Sec. 5.3)
+//   P2M      S_a^u[c](y) = exp(i kappa <y_a - y, u>) S_a[c](y)   (Sec. 2.2)
+//   M2M      D0(v) (x)M^(p) D1(v), tensorised (Sec. 5.2.1, Eq. dlefturight)
+//   M2F      F chi: zero-pad + forward DFT (Sec. 4.1.1)
+//   M2L      Hadamard products with symmetry-permuted spectra, summed over
+//            each target's list (Sec. 2.3, Eq. permuteM2L), fused with
+//   F2L      chi^T F*: inverse DFT + crop (Sec. 4.1.1)
+//   L2L      transpose of M2M (Sec. 2.2)
+//   L2P      S_a^u[c](x) at the targets (Sec. 2.2)
+//   scatter  p <- Morton order
+//
+// Every output is produced by exactly one thread block with a fixed
+// summation order (no atomics), so results are deterministic.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "symmetry.h"
+
+namespace defmm {
+
+__constant__ int kPermDev[6][3] = DEFMM_PERM_TABLE;
+
+// ------------------------------------------------------------------ complex
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
+    return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(a.x) s) { return mk(a.x * s, a.y * s); }
+template <typename C> __device__ __forceinline__ C czero() { return mk((decltype(C{}.x))0, (decltype(C{}.x))0); }
+
+__device__ __forceinline__ void sincos_t(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sincos_t(double a, double* s, double* c) { sincos(a, s, c); }
+
+// Lagrange basis l_m(t) on {0, 1/(p-1), ..., 1}, evaluated at s = (p-1) t.
+template <typename T> __device__ __forceinline__ T lagrange(int p, int m, T s) {
+    T v = (T)1;
+    for (int n = 0; n < p; ++n)
+        if (n != m) v *= (s - (T)n) / (T)(m - n);
+    return v;
+}
+
+constexpr double kInv4Pi = 0.0795774715459476678844418816863;  // 1/(4 pi)
+constexpr double kInv2Pi = 0.159154943091895335768883763373;   // 1/(2 pi)
+
+// ------------------------------------------------------------------ gather / scatter
+template <typename C>
+__global__ void k_gather(const C* __restrict__ q, C* __restrict__ qs, const int64_t* __restrict__ perm,
+                         int64_t n, int R) {
+    int64_t total = n * R;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i / n, j = i - r * n;
+        qs[i] = q[r * n + perm[j]];
+    }
+}
+
+template <typename C>
+__global__ void k_scatter(const C* __restrict__ ps, C* __restrict__ p, const int64_t* __restrict__ perm,
+                          int64_t n, int R) {
+    int64_t total = n * R;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i / n, j = i - r * n;
+        p[r * n + perm[j]] = ps[i];
+    }
+}
+
+// ------------------------------------------------------------------ P2P
+// Kernel value G(x, y) for a difference d, zero when |d|^2 <= eps2 (Sec. 5.3).
+__device__ __forceinline__ float2 helmholtz(float dx, float dy, float dz, float kap2pi, float eps2) {
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float rinv = rsqrtf(r2);
+    float r = r2 * rinv;
+    // exp(i kappa r) with the phase reduced exactly to [-1/2, 1/2] turns
+    float t = r * kap2pi;
+    t -= rintf(t);
+    float s, c;
+    __sincosf(6.28318530717958647692f * t, &s, &c);
+    float g = rinv * (float)kInv4Pi;
+    float2 out = make_float2(c * g, s * g);
+    if (!(r2 > eps2)) out = make_float2(0.f, 0.f);
+    return out;
+}
+__device__ __forceinline__ double2 helmholtz(double dx, double dy, double dz, double kappa, double eps2) {
+    double r2 = dx * dx + dy * dy + dz * dz;
+    double r = sqrt(r2);
+    double s, c;
+    sincos(kappa * r, &s, &c);
+    double g = kInv4Pi / r;
+    double2 out = make_double2(c * g, s * g);
+    if (!(r2 > eps2)) out = make_double2(0.0, 0.0);
+    return out;
+}
+
+template <typename T, int RB>
+__global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>::type* __restrict__ qs,
+                                             typename Cplx<T>::type* __restrict__ ps, int R, int rb0) {
+    using C = typename Cplx<T>::type;
+    __shared__ T sx[128], sy[128], sz[128];
+    __shared__ C sq[RB][128];
+    __shared__ C red[4][64][RB];
+    const int li = blockIdx.x;
+    const int cell = c.p2p_leaf[li];
+    const int tb = c.ct_beg[cell], te = c.ct_end[cell];
+    const double side = c.level_side[c.ct_level[cell]];
+    const double cx = c.ct_corner[3 * cell] + 0.5 * side;
+    const double cy = c.ct_corner[3 * cell + 1] + 0.5 * side;
+    const double cz = c.ct_corner[3 * cell + 2] + 0.5 * side;
+    const int nr = min(RB, R - rb0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T kpar = sizeof(T) == 4 ? (T)(c.kappa * kInv2Pi) : (T)c.kappa;
+    const T eps2 = (T)(c.eps_self * c.eps_self);
+    const int r0 = c.p2p_off[li], r1 = c.p2p_off[li + 1];
+    for (int t0 = tb; t0 < te; t0 += 64) {
+        const int ia = t0 + lane, ib = t0 + lane + 32;
+        T xa = 0, ya = 0, za = 0, xb = 0, yb = 0, zb = 0;
+        if (ia < te) {
+            xa = (T)(c.Xs[3 * (int64_t)ia] - cx); ya = (T)(c.Xs[3 * (int64_t)ia + 1] - cy); za = (T)(c.Xs[3 * (int64_t)ia + 2] - cz);
+        }
+        if (ib < te) {
+            xb = (T)(c.Xs[3 * (int64_t)ib] - cx); yb = (T)(c.Xs[3 * (int64_t)ib + 1] - cy); zb = (T)(c.Xs[3 * (int64_t)ib + 2] - cz);
+        }
+        C acca[RB], accb[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) { acca[r] = czero<C>(); accb[r] = czero<C>(); }
+        for (int rr = r0; rr < r1; ++rr) {
+            const int sb = c.p2p_sbeg[rr], se = c.p2p_send[rr];
+            for (int s0 = sb; s0 < se; s0 += 128) {
+                const int ns = min(128, se - s0);
+                __syncthreads();
+                if (threadIdx.x < ns) {
+                    const int64_t j = s0 + threadIdx.x;
+                    sx[threadIdx.x] = (T)(c.Ys[3 * j] - cx);
+                    sy[threadIdx.x] = (T)(c.Ys[3 * j + 1] - cy);
+                    sz[threadIdx.x] = (T)(c.Ys[3 * j + 2] - cz);
+#pragma unroll
+                    for (int r = 0; r < RB; ++r)
+                        sq[r][threadIdx.x] = r < nr ? qs[(int64_t)(rb0 + r) * c.ny + j] : czero<C>();
+                }
+                __syncthreads();
+                for (int k = warp; k < ns; k += 4) {
+                    const C ga = helmholtz(xa - sx[k], ya - sy[k], za - sz[k], kpar, eps2);
+                    const C gb = helmholtz(xb - sx[k], yb - sy[k], zb - sz[k], kpar, eps2);
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        const C qv = sq[r][k];
+                        cfma(acca[r], ga, qv);
+                        cfma(accb[r], gb, qv);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r) { red[warp][lane][r] = acca[r]; red[warp][lane + 32][r] = accb[r]; }
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            const int i = t0 + threadIdx.x;
+            if (i < te) {
+                for (int r = 0; r < nr; ++r) {
+                    C s = red[0][threadIdx.x][r];
+                    s = cadd(s, red[1][threadIdx.x][r]);
+                    s = cadd(s, red[2][threadIdx.x][r]);
+                    s = cadd(s, red[3][threadIdx.x][r]);
+                    ps[(int64_t)(rb0 + r) * c.nx + i] = s;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ P2M
+template <typename T, int RB>
+__global__ void __launch_bounds__(128) k_p2m(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ qs,
+                                             typename Cplx<T>::type* __restrict__ M, int R, int rb0) {
+    using C = typename Cplx<T>::type;
+    __shared__ C phi[32][3][8];
+    __shared__ C sq[RB][32];
+    const int cell = c.p2m_cells[blockIdx.x];
+    const int b = c.cs_beg[cell], e = c.cs_end[cell];
+    const double side = c.level_side[c.cs_level[cell]];
+    const int p = c.p, P3 = c.P3;
+    const double h = side / (p - 1);
+    const double cor[3] = {c.cs_corner[3 * cell], c.cs_corner[3 * cell + 1], c.cs_corner[3 * cell + 2]};
+    const int nr = min(RB, R - rb0);
+    const T kap = (T)c.kappa;
+    for (int ex = c.m_first[cell]; ex < c.m_first[cell] + c.m_count[cell]; ++ex) {
+        const int slot = c.m_slot[ex];
+        T u[3] = {0, 0, 0};
+        if (slot >= 0) { u[0] = (T)c.slot_u[3 * slot]; u[1] = (T)c.slot_u[3 * slot + 1]; u[2] = (T)c.slot_u[3 * slot + 2]; }
+        C acc[4][RB];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[v][r] = czero<C>();
+        for (int j0 = b; j0 < e; j0 += 32) {
+            const int nj = min(32, e - j0);
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < nj * 3 * p; idx += blockDim.x) {
+                const int j = idx / (3 * p), rem = idx - j * 3 * p, ax = rem / p, m = rem - ax * p;
+                const double d = c.Ys[3 * (int64_t)(j0 + j) + ax] - cor[ax];
+                const T lag = lagrange<T>(p, m, (T)(d / h));
+                C val = mk(lag, (T)0);
+                if (slot >= 0) {
+                    T sn, cs;
+                    sincos_t(kap * (T)((double)m * h - d) * u[ax], &sn, &cs);
+                    val = mk(lag * cs, lag * sn);
+                }
+                phi[j][ax][m] = val;
+            }
+            if (threadIdx.x < nj * RB) {
+                const int j = threadIdx.x % nj, r = threadIdx.x / nj;
+                sq[r][j] = r < nr ? qs[(int64_t)(rb0 + r) * c.ny + j0 + j] : czero<C>();
+            }
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int a = threadIdx.x + v * 128;
+                if (a < P3) {
+                    const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
+                    for (int j = 0; j < nj; ++j) {
+                        const C f = cmul(cmul(phi[j][0][a0], phi[j][1][a1]), phi[j][2][a2]);
+#pragma unroll
+                        for (int r = 0; r < RB; ++r) cfma(acc[v][r], f, sq[r][j]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int a = threadIdx.x + v * 128;
+            if (a < P3)
+                for (int r = 0; r < nr; ++r) M[((int64_t)ex * R + rb0 + r) * P3 + a] = acc[v][r];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ M2M
+// One block per father expansion (entry: father id, 8 son ids or -1).
+template <typename T>
+__global__ void __launch_bounds__(128) k_m2m(DevCommon c, DevTyped<T> t, const int32_t* __restrict__ list,
+                                             typename Cplx<T>::type* __restrict__ M, int R) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + c.P3;
+    __shared__ T m1s[2 * 8 * 8];
+    __shared__ C Ps[3 * 8], Qs[3 * 2 * 8];
+    const int32_t* ent = list + 9 * (int64_t)blockIdx.x;
+    const int ep = ent[0];
+    const int slot = c.m_slot[ep];
+    const int p = c.p, P3 = c.P3;
+    for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) m1s[i] = t.m1[i];
+    for (int i = threadIdx.x; i < 3 * p; i += blockDim.x)
+        Ps[i] = slot >= 0 ? t.slot_P[(int64_t)slot * 3 * p + i] : mk((T)1, (T)0);
+    for (int i = threadIdx.x; i < 6 * p; i += blockDim.x)
+        Qs[i] = slot >= 0 ? t.slot_Q[(int64_t)slot * 6 * p + i] : mk((T)1, (T)0);
+    __syncthreads();
+    for (int r = 0; r < R; ++r) {
+        C acc[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] = czero<C>();
+        for (int o = 0; o < 8; ++o) {
+            const int ce = ent[1 + o];
+            if (ce < 0) continue;
+            const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
+            const T* mx = m1s + ox * p * p;
+            const T* my = m1s + oy * p * p;
+            const T* mz = m1s + oz * p * p;
+            for (int a = threadIdx.x; a < P3; a += blockDim.x) {
+                const int b0 = a % p, b1 = (a / p) % p, b2 = a / (p * p);
+                const C q = cmul(cmul(Qs[(0 * 2 + ox) * p + b0], Qs[(1 * 2 + oy) * p + b1]), Qs[(2 * 2 + oz) * p + b2]);
+                A[a] = cmulc(M[((int64_t)ce * R + r) * P3 + a], q);
+            }
+            __syncthreads();
+            for (int a = threadIdx.x; a < P3; a += blockDim.x) {  // x: (bz, by, ax)
+                const int a0 = a % p, rest = a - a0;
+                C s = czero<C>();
+                for (int k = 0; k < p; ++k) { C v = A[rest + k]; T m = mx[a0 * p + k]; s.x += m * v.x; s.y += m * v.y; }
+                B[a] = s;
+            }
+            __syncthreads();
+            for (int a = threadIdx.x; a < P3; a += blockDim.x) {  // y: (bz, ay, ax)
+                const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
+                C s = czero<C>();
+                for (int k = 0; k < p; ++k) { C v = B[(a2 * p + k) * p + a0]; T m = my[a1 * p + k]; s.x += m * v.x; s.y += m * v.y; }
+                A[a] = s;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {  // z: (az, ay, ax), accumulate
+                const int a = threadIdx.x + v * 128;
+                if (a < P3) {
+                    const int a01 = a % (p * p), a2 = a / (p * p);
+                    C s = acc[v];
+                    for (int k = 0; k < p; ++k) { C w = A[k * p * p + a01]; T m = mz[a2 * p + k]; s.x += m * w.x; s.y += m * w.y; }
+                    acc[v] = s;
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int a = threadIdx.x + v * 128;
+            if (a < P3) {
+                const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
+                const C ph = cmul(cmul(Ps[0 * p + a0], Ps[1 * p + a1]), Ps[2 * p + a2]);
+                M[((int64_t)ep * R + r) * P3 + a] = cmul(acc[v], ph);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ M2F
+template <typename T>
+__global__ void __launch_bounds__(128) k_m2f(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ M,
+                                             typename Cplx<T>::type* __restrict__ Mhat, int R) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    const int p = c.p, N = c.N, P3 = c.P3, NF = c.NF, NFpad = c.NFpad;
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + P3;              // [bz][by][xi_x]   p*p*N
+    C* D = B + p * p * N;       // [bz][xi_y][xi_x] p*N*N
+    __shared__ C tws[16];
+    const int e = c.m2f_list[blockIdx.x];
+    if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
+    for (int r = 0; r < R; ++r) {
+        __syncthreads();
+        for (int a = threadIdx.x; a < P3; a += blockDim.x) A[a] = M[((int64_t)e * R + r) * P3 + a];
+        __syncthreads();
+        for (int i = threadIdx.x; i < p * p * N; i += blockDim.x) {
+            const int xx = i % N, rest = i / N;  // rest = bz*p + by
+            C s = czero<C>();
+            for (int b = 0; b < p; ++b) cfma(s, A[rest * p + b], mk(tws[(xx * b) % N].x, -tws[(xx * b) % N].y));
+            B[i] = s;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < p * N * N; i += blockDim.x) {
+            const int xx = i % N, yy = (i / N) % N, bz = i / (N * N);
+            C s = czero<C>();
+            for (int b = 0; b < p; ++b) cfma(s, B[(bz * p + b) * N + xx], mk(tws[(yy * b) % N].x, -tws[(yy * b) % N].y));
+            D[i] = s;
+        }
+        __syncthreads();
+        C* out = Mhat + ((int64_t)blockIdx.x * R + r) * NFpad;
+        for (int i = threadIdx.x; i < NFpad; i += blockDim.x) {
+            C s = czero<C>();
+            if (i < NF) {
+                const int xy = i % (N * N), zz = i / (N * N);
+                for (int b = 0; b < p; ++b) cfma(s, D[b * N * N + xy], mk(tws[(zz * b) % N].x, -tws[(zz * b) % N].y));
+            }
+            out[i] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ M2L (+F2L)
+// One block per target expansion with a non-empty list.  Thread i owns the
+// Fourier samples xi = i + v*blockDim (v < VPT); for each source it reads the
+// canonical spectrum at the symmetry-permuted index xi' (xi'_{sigma(a)} =
+// s_a xi_a mod N) and accumulates spectrum(xi') * Mhat_s(xi).  The inverse DFT
+// and the crop to the p^3 grid follow in shared memory.
+template <typename T, int VPT>
+__global__ void __launch_bounds__(1024) k_m2l(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
+                                              typename Cplx<T>::type* __restrict__ L, int R) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    const int p = c.p, N = c.N, NF = c.NF, NFpad = c.NFpad, P3 = c.P3;
+    C* Lh = reinterpret_cast<C*>(smem_raw);   // NF
+    C* T1 = Lh + NF;                          // [az][xi_y][xi_x]  p*N*N
+    C* T2 = T1 + p * N * N;                   // [az][ay][xi_x]    p*p*N
+    __shared__ C tws[16];
+    const int i = blockIdx.x;
+    const int te = c.m2l_tgt[i];
+    const int j0 = c.m2l_off[i], j1 = c.m2l_off[i + 1];
+    if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
+    int xi[VPT], cx[VPT], cy[VPT], cz[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        xi[v] = threadIdx.x + v * blockDim.x;
+        const int f = xi[v] < NF ? xi[v] : 0;
+        cx[v] = f % N; cy[v] = (f / N) % N; cz[v] = f / (N * N);
+    }
+    const T scale = (T)1 / (T)NF;
+    for (int r = 0; r < R; ++r) {
+        C acc[VPT];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) acc[v] = czero<C>();
+        for (int j = j0; j < j1; ++j) {
+            const int src = c.m2l_src[j];
+            const int sc = c.m2l_spec[j];
+            const int sid = sc >> 6, code = sc & 63, pid = code >> 3;
+            const int st[3] = {kPermDev[pid][0] == 0 ? 1 : (kPermDev[pid][0] == 1 ? N : N * N),
+                               kPermDev[pid][1] == 0 ? 1 : (kPermDev[pid][1] == 1 ? N : N * N),
+                               kPermDev[pid][2] == 0 ? 1 : (kPermDev[pid][2] == 1 ? N : N * N)};
+            const bool n0 = code & 1, n1 = code & 2, n2 = code & 4;
+            const C* __restrict__ g = t.spec + (int64_t)sid * NFpad;
+            const C* __restrict__ mh = Mhat + ((int64_t)src * R + r) * NFpad;
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                if (xi[v] < NF) {
+                    const int x0 = n0 ? (N - cx[v]) % N : cx[v];
+                    const int x1 = n1 ? (N - cy[v]) % N : cy[v];
+                    const int x2 = n2 ? (N - cz[v]) % N : cz[v];
+                    const int idx = x0 * st[0] + x1 * st[1] + x2 * st[2];
+                    cfma(acc[v], __ldg(&g[idx]), __ldg(&mh[xi[v]]));
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < VPT; ++v)
+            if (xi[v] < NF) Lh[xi[v]] = acc[v];
+        __syncthreads();
+        for (int q = threadIdx.x; q < p * N * N; q += blockDim.x) {  // z
+            const int xy = q % (N * N), az = q / (N * N);
+            C s = czero<C>();
+            for (int k = 0; k < N; ++k) cfma(s, Lh[k * N * N + xy], tws[(k * az) % N]);
+            T1[q] = s;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < p * p * N; q += blockDim.x) {  // y
+            const int xx = q % N, ay = (q / N) % p, az = q / (N * p);
+            C s = czero<C>();
+            for (int k = 0; k < N; ++k) cfma(s, T1[(az * N + k) * N + xx], tws[(k * ay) % N]);
+            T2[q] = s;
+        }
+        __syncthreads();
+        for (int a = threadIdx.x; a < P3; a += blockDim.x) {  // x, crop, 1/N^3
+            const int ax = a % p, rest = a / p;  // rest = az*p + ay
+            C s = czero<C>();
+            for (int k = 0; k < N; ++k) cfma(s, T2[rest * N + k], tws[(k * ax) % N]);
+            L[((int64_t)te * R + r) * P3 + a] = cscale(s, scale);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ L2L
+// One block per son expansion (entry: son id, octant, first, count into the
+// list of father expansions feeding it).
+template <typename T>
+__global__ void __launch_bounds__(128) k_l2l(DevCommon c, DevTyped<T> t, const int32_t* __restrict__ list,
+                                             const int32_t* __restrict__ par, typename Cplx<T>::type* __restrict__ L, int R) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + c.P3;
+    __shared__ T m1s[2 * 8 * 8];
+    __shared__ C Ps[3 * 8], Qs[3 * 2 * 8];
+    const int32_t* ent = list + 4 * (int64_t)blockIdx.x;
+    const int ec = ent[0], o = ent[1], first = ent[2], cnt = ent[3];
+    const int p = c.p, P3 = c.P3;
+    const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
+    for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) m1s[i] = t.m1[i];
+    const T* mx = m1s + ox * p * p;
+    const T* my = m1s + oy * p * p;
+    const T* mz = m1s + oz * p * p;
+    for (int r = 0; r < R; ++r) {
+        C acc[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] = czero<C>();
+        for (int k = 0; k < cnt; ++k) {
+            const int pe = par[first + k];
+            const int slot = c.l_slot[pe];
+            __syncthreads();
+            for (int i = threadIdx.x; i < 3 * p; i += blockDim.x)
+                Ps[i] = slot >= 0 ? t.slot_P[(int64_t)slot * 3 * p + i] : mk((T)1, (T)0);
+            for (int i = threadIdx.x; i < 6 * p; i += blockDim.x)
+                Qs[i] = slot >= 0 ? t.slot_Q[(int64_t)slot * 6 * p + i] : mk((T)1, (T)0);
+            __syncthreads();
+            for (int a = threadIdx.x; a < P3; a += blockDim.x) {
+                const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
+                const C ph = cmul(cmul(Ps[a0], Ps[p + a1]), Ps[2 * p + a2]);
+                A[a] = cmulc(L[((int64_t)pe * R + r) * P3 + a], ph);
+            }
+            __syncthreads();
+            for (int b = threadIdx.x; b < P3; b += blockDim.x) {  // x: (az, ay, bx)
+                const int b0 = b % p, rest = b - b0;
+                C s = czero<C>();
+                for (int q = 0; q < p; ++q) { C v = A[rest + q]; T m = mx[q * p + b0]; s.x += m * v.x; s.y += m * v.y; }
+                B[b] = s;
+            }
+            __syncthreads();
+            for (int b = threadIdx.x; b < P3; b += blockDim.x) {  // y: (az, by, bx)
+                const int b0 = b % p, b1 = (b / p) % p, b2 = b / (p * p);
+                C s = czero<C>();
+                for (int q = 0; q < p; ++q) { C v = B[(b2 * p + q) * p + b0]; T m = my[q * p + b1]; s.x += m * v.x; s.y += m * v.y; }
+                A[b] = s;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {  // z: (bz, by, bx), times Q(v, o)
+                const int b = threadIdx.x + v * 128;
+                if (b < P3) {
+                    const int b0 = b % p, b1 = (b / p) % p, b01 = b % (p * p), b2 = b / (p * p);
+                    C s = czero<C>();
+                    for (int q = 0; q < p; ++q) { C w = A[q * p * p + b01]; T m = mz[q * p + b2]; s.x += m * w.x; s.y += m * w.y; }
+                    const C qq = cmul(cmul(Qs[(0 * 2 + ox) * p + b0], Qs[(1 * 2 + oy) * p + b1]), Qs[(2 * 2 + oz) * p + b2]);
+                    cfma(acc[v], s, qq);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int b = threadIdx.x + v * 128;
+            if (b < P3) {
+                C* dst = L + ((int64_t)ec * R + r) * P3 + b;
+                *dst = cadd(*dst, acc[v]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ L2P
+template <typename T, int RB>
+__global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ L,
+                                             typename Cplx<T>::type* __restrict__ ps, int R, int rb0) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C* Ls = reinterpret_cast<C*>(smem_raw);  // [RB][P3]
+    const int cell = c.l2p_cells[blockIdx.x];
+    const int b = c.ct_beg[cell], e = c.ct_end[cell];
+    const double side = c.level_side[c.ct_level[cell]];
+    const int p = c.p, P3 = c.P3;
+    const double h = side / (p - 1);
+    const double cor[3] = {c.ct_corner[3 * cell], c.ct_corner[3 * cell + 1], c.ct_corner[3 * cell + 2]};
+    const int nr = min(RB, R - rb0);
+    const T kap = (T)c.kappa;
+    for (int j0 = b; j0 < e; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        const bool valid = j < e;
+        double d[3] = {0, 0, 0};
+        if (valid)
+            for (int ax = 0; ax < 3; ++ax) d[ax] = c.Xs[3 * (int64_t)j + ax] - cor[ax];
+        T lag[3][8];
+        for (int ax = 0; ax < 3; ++ax)
+            for (int m = 0; m < p; ++m) lag[ax][m] = lagrange<T>(p, m, (T)(d[ax] / h));
+        C acc[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) acc[r] = czero<C>();
+        for (int ex = c.l_first[cell]; ex < c.l_first[cell] + c.l_count[cell]; ++ex) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < nr * P3; i += blockDim.x) {
+                const int r = i / P3, a = i - r * P3;
+                Ls[r * P3 + a] = L[((int64_t)ex * R + rb0 + r) * P3 + a];
+            }
+            __syncthreads();
+            const int slot = c.l_slot[ex];
+            C ph[3][8];
+            for (int ax = 0; ax < 3; ++ax) {
+                const T u = slot >= 0 ? (T)c.slot_u[3 * slot + ax] : (T)0;
+                for (int m = 0; m < p; ++m) {
+                    if (slot >= 0) {
+                        T sn, cs;
+                        sincos_t(kap * (T)(d[ax] - (double)m * h) * u, &sn, &cs);
+                        ph[ax][m] = mk(lag[ax][m] * cs, lag[ax][m] * sn);
+                    } else {
+                        ph[ax][m] = mk(lag[ax][m], (T)0);
+                    }
+                }
+            }
+            if (valid) {
+                for (int r = 0; r < nr; ++r) {
+                    const C* Lr = Ls + r * P3;
+                    C sz = czero<C>();
+                    for (int a2 = 0; a2 < p; ++a2) {
+                        C sy = czero<C>();
+                        for (int a1 = 0; a1 < p; ++a1) {
+                            C sx = czero<C>();
+                            for (int a0 = 0; a0 < p; ++a0) cfma(sx, Lr[(a2 * p + a1) * p + a0], ph[0][a0]);
+                            cfma(sy, sx, ph[1][a1]);
+                        }
+                        cfma(sz, sy, ph[2][a2]);
+                    }
+                    acc[r] = cadd(acc[r], sz);
+                }
+            }
+        }
+        if (valid)
+            for (int r = 0; r < nr; ++r) {
+                C* dst = ps + (int64_t)(rb0 + r) * c.nx + j;
+                *dst = cadd(*dst, acc[r]);
+            }
+    }
+}
+
+// ------------------------------------------------------------------ spectra (float64)
+// g(delta) = G(side*kbar + h*delta) placed at delta mod N, then an N^3 DFT
+// with e^{-2 pi i xi.x / N} (unnormalised) along x, y and z.
+__global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spec_level, const int32_t* __restrict__ kbar,
+                                                 const double* __restrict__ level_side, int p, int N, int NFpad,
+                                                 double kappa, double2* __restrict__ out_d, float2* __restrict__ out_f) {
+    extern __shared__ unsigned char smem_raw[];
+    const int NF = N * N * N;
+    double2* A = reinterpret_cast<double2*>(smem_raw);
+    double2* B = A + NF;
+    __shared__ double2 tw[16];
+    const int sid = blockIdx.x;
+    const double side = level_side[spec_level[sid]];
+    const double h = side / (p - 1);
+    const double k0 = kbar[3 * sid], k1 = kbar[3 * sid + 1], k2 = kbar[3 * sid + 2];
+    if (threadIdx.x < N) {
+        double s, c;
+        sincospi(-2.0 * threadIdx.x / N, &s, &c);
+        tw[threadIdx.x] = make_double2(c, s);
+    }
+    for (int i = threadIdx.x; i < NF; i += blockDim.x) A[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    const int W = 2 * p - 1;
+    for (int i = threadIdx.x; i < W * W * W; i += blockDim.x) {
+        const int dx = i % W - (p - 1), dy = (i / W) % W - (p - 1), dz = i / (W * W) - (p - 1);
+        const double vx = side * k0 + h * dx, vy = side * k1 + h * dy, vz = side * k2 + h * dz;
+        const double r = sqrt(vx * vx + vy * vy + vz * vz);
+        double s, c;
+        sincos(kappa * r, &s, &c);
+        const double g = kInv4Pi / r;
+        const int ix = (dx + N) % N, iy = (dy + N) % N, iz = (dz + N) % N;
+        A[(iz * N + iy) * N + ix] = make_double2(c * g, s * g);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NF; i += blockDim.x) {  // x
+        const int xx = i % N, rest = i - xx;
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = 0; k < N; ++k) cfma(s, A[rest + k], tw[(xx * k) % N]);
+        B[i] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NF; i += blockDim.x) {  // y
+        const int xx = i % N, yy = (i / N) % N, zz = i / (N * N);
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = 0; k < N; ++k) cfma(s, B[(zz * N + k) * N + xx], tw[(yy * k) % N]);
+        A[i] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NFpad; i += blockDim.x) {  // z
+        double2 s = make_double2(0.0, 0.0);
+        if (i < NF) {
+            const int xy = i % (N * N), zz = i / (N * N);
+            for (int k = 0; k < N; ++k) cfma(s, A[k * N * N + xy], tw[(zz * k) % N]);
+        }
+        out_d[(int64_t)sid * NFpad + i] = s;
+        out_f[(int64_t)sid * NFpad + i] = make_float2((float)s.x, (float)s.y);
+    }
+}
+
+cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
+                           const double* level_side, int p, int N, int NFpad, double kappa,
+                           double2* out_d, float2* out_f, cudaStream_t stream) {
+    if (nspec == 0) return cudaSuccess;
+    size_t smem = 2 * (size_t)N * N * N * sizeof(double2);
+    cudaError_t err = cudaFuncSetAttribute(k_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_spectra<<<nspec, 256, smem, stream>>>(spec_level, spec_kbar, level_side, p, N, NFpad, kappa, out_d, out_f);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ orchestration
+template <typename T>
+cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w,
+                         const LevelList* m2m, int n_m2m_levels, const LevelList* l2l,
+                         const int32_t* const* l2l_par, int n_l2l_levels, const void* q, void* p,
+                         cudaStream_t stream, int* launches) {
+    using C = typename Cplx<T>::type;
+    const int R = w.R;
+    int nl = 0;
+    cudaError_t err;
+#define DEFMM_CHECK_LAUNCH()                      \
+    do {                                          \
+        ++nl;                                     \
+        err = cudaGetLastError();                 \
+        if (err != cudaSuccess) {                 \
+            if (launches) *launches = nl;         \
+            return err;                           \
+        }                                         \
+    } while (0)
+    const int sms = 152 * 8;
+    // gather charges into Morton order
+    k_gather<C><<<sms, 256, 0, stream>>>(reinterpret_cast<const C*>(q), w.qs, c.perm_s, c.ny, R);
+    DEFMM_CHECK_LAUNCH();
+    // near field (writes every target potential)
+    for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
+        if (c.n_p2p_leaf == 0) break;
+        if (R == 1) k_p2p<T, 1><<<(unsigned)c.n_p2p_leaf, 128, 0, stream>>>(c, w.qs, w.ps, R, rb0);
+        else k_p2p<T, 4><<<(unsigned)c.n_p2p_leaf, 128, 0, stream>>>(c, w.qs, w.ps, R, rb0);
+        DEFMM_CHECK_LAUNCH();
+    }
+    // upward pass
+    for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
+        if (c.n_p2m == 0) break;
+        if (R == 1) k_p2m<T, 1><<<(unsigned)c.n_p2m, 128, 0, stream>>>(c, t, w.qs, w.M, R, rb0);
+        else k_p2m<T, 4><<<(unsigned)c.n_p2m, 128, 0, stream>>>(c, t, w.qs, w.M, R, rb0);
+        DEFMM_CHECK_LAUNCH();
+    }
+    const size_t sm_m2m = 2 * (size_t)c.P3 * sizeof(C);
+    for (int l = n_m2m_levels - 1; l >= 0; --l) {
+        if (m2m[l].n == 0) continue;
+        k_m2m<T><<<(unsigned)m2m[l].n, 128, sm_m2m, stream>>>(c, t, m2m[l].data, w.M, R);
+        DEFMM_CHECK_LAUNCH();
+    }
+    if (c.n_m2f > 0) {
+        const size_t sm = ((size_t)c.P3 + (size_t)c.p * c.p * c.N + (size_t)c.p * c.N * c.N) * sizeof(C);
+        k_m2f<T><<<(unsigned)c.n_m2f, 128, sm, stream>>>(c, t, w.M, w.Mhat, R);
+        DEFMM_CHECK_LAUNCH();
+    }
+    // transfer
+    err = cudaMemsetAsync(w.L, 0, (size_t)w.nL * R * c.P3 * sizeof(C), stream);
+    if (err != cudaSuccess) return err;
+    if (c.n_m2l_tgt > 0) {
+        const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
+        const size_t sm = ((size_t)c.NF + (size_t)c.p * c.N * c.N + (size_t)c.p * c.p * c.N) * sizeof(C);
+        k_m2l<T, 4><<<(unsigned)c.n_m2l_tgt, threads, sm, stream>>>(c, t, w.Mhat, w.L, R);
+        DEFMM_CHECK_LAUNCH();
+    }
+    // downward pass
+    for (int l = 1; l < n_l2l_levels; ++l) {
+        if (l2l[l].n == 0) continue;
+        k_l2l<T><<<(unsigned)l2l[l].n, 128, sm_m2m, stream>>>(c, t, l2l[l].data, l2l_par[l], w.L, R);
+        DEFMM_CHECK_LAUNCH();
+    }
+    for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
+        if (c.n_l2p == 0) break;
+        const int rb = R == 1 ? 1 : 4;
+        const size_t sm = (size_t)rb * c.P3 * sizeof(C);
+        if (R == 1) k_l2p<T, 1><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0);
+        else k_l2p<T, 4><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0);
+        DEFMM_CHECK_LAUNCH();
+    }
+    k_scatter<C><<<sms, 256, 0, stream>>>(w.ps, reinterpret_cast<C*>(p), c.perm_t, c.nx, R);
+    DEFMM_CHECK_LAUNCH();
+#undef DEFMM_CHECK_LAUNCH
+    if (launches) *launches = nl;
+    return cudaSuccess;
+}
+
+// Raises the dynamic shared-memory limit of the kernels that may need more
+// than 48 KB (large orders / FFT lengths, float64).
+template <typename T>
+cudaError_t configure_kernels() {
+    const int big = 200 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_m2l<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2f<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+template cudaError_t launch_apply<float>(const DevCommon&, const DevTyped<float>&, const DevWork<float>&,
+                                         const LevelList*, int, const LevelList*, const int32_t* const*, int,
+                                         const void*, void*, cudaStream_t, int*);
+template cudaError_t launch_apply<double>(const DevCommon&, const DevTyped<double>&, const DevWork<double>&,
+                                          const LevelList*, int, const LevelList*, const int32_t* const*, int,
+                                          const void*, void*, cudaStream_t, int*);
+template cudaError_t configure_kernels<float>();
+template cudaError_t configure_kernels<double>();
+
+}  // namespace defmm

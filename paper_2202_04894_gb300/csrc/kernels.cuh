@@ -1,0 +1,83 @@
+// Device-side tables of a plan and the launchers of the application-phase
+// kernels (Sec. 2.2 operators, Sec. 4.1.1 M2F/F2L, Sec. 4.3 symmetries,
+// Sec. 5.3 near field).  All pointers are device pointers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace defmm {
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+// Precision-independent tables.
+struct DevCommon {
+    int p, N, NF, NFpad, P3;
+    int64_t nx, ny;
+    double kappa, eps_self;
+    const double* Xs;        // nx*3 targets, Morton order
+    const double* Ys;        // ny*3 sources, Morton order
+    const int64_t* perm_t;   // sorted -> input
+    const int64_t* perm_s;
+    // target / source cells
+    const int32_t *ct_beg, *ct_end, *ct_level;
+    const double* ct_corner;  // 3 per cell
+    const int32_t *cs_beg, *cs_end, *cs_level;
+    const double* cs_corner;
+    const double* level_side;  // per level
+    // expansions
+    const int32_t *m_first, *m_count, *m_slot;  // per source cell / per multipole
+    const int32_t *l_first, *l_count, *l_slot;  // per target cell / per local
+    const double* slot_u;                       // 3 per slot
+    // tables
+    const int32_t* m2f_list;  int64_t n_m2f;
+    const int32_t *m2l_tgt, *m2l_off, *m2l_src, *m2l_spec;  int64_t n_m2l_tgt;
+    const int32_t* p2m_cells;  int64_t n_p2m;
+    const int32_t* l2p_cells;  int64_t n_l2p;
+    const int32_t *p2p_leaf, *p2p_off, *p2p_sbeg, *p2p_send;  int64_t n_p2p_leaf;
+};
+
+// Tables in the arithmetic precision T.
+template <typename T>
+struct DevTyped {
+    using C = typename Cplx<T>::type;
+    const C* slot_P;   // [slot][3][p]
+    const C* slot_Q;   // [slot][3][2][p]
+    const T* m1;       // [2][p][p]
+    const C* tw;       // [N]  e^{2 pi i m/N}
+    const C* spec;     // [nspec][NFpad]
+};
+
+// Per-apply buffers.
+template <typename T>
+struct DevWork {
+    using C = typename Cplx<T>::type;
+    int R;
+    C* qs;     // [R][ny]
+    C* ps;     // [R][nx]
+    C* M;      // [nM][R][P3]
+    C* Mhat;   // [nMhat][R][NFpad]
+    C* L;      // [nL][R][P3]
+    int64_t nL;
+};
+
+struct LevelList {
+    const int32_t* data;  // device
+    int64_t n;            // entries
+};
+
+// Launchers (enqueue on `stream`, return the launch error if any).
+template <typename T>
+cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w,
+                         const LevelList* m2m, int n_m2m_levels, const LevelList* l2l,
+                         const int32_t* const* l2l_par, int n_l2l_levels, const void* q, void* p,
+                         cudaStream_t stream, int* launches);
+
+// Forms the canonical transfer spectra in float64 (Sec. 2.3 Eq. FourierDiagonal).
+cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
+                           const double* level_side, int p, int N, int NFpad, double kappa,
+                           double2* out_d, float2* out_f, cudaStream_t stream);
+
+}  // namespace defmm

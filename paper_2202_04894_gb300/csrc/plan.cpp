@@ -1,0 +1,525 @@
+// Host-side plan construction (see plan.h).  Compiled with -ffp-contract=off
+// so that every floating-point decision (Morton quantisation, MACs, regimes)
+// is the plain IEEE result of the written expression.
+#include "plan.h"
+#include "symmetry.h"
+
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <numeric>
+#include <stdexcept>
+#include <unordered_map>
+
+namespace defmm {
+
+// ---------------------------------------------------------------- levels / MAC
+double Levels::side(int l) const { return side0 / (double)(1LL << l); }
+double Levels::radius(int l) const { return std::sqrt(3.0) / 2 * side(l); }
+
+// Strict MAC (footnote of Sec. 3.2) at low frequency, directional MAC
+// max(kappa w^2, 2w) <= eta dist (Eq. macdirref, Sec. 4.2.2) at high frequency.
+bool Levels::mac(int l, int64_t kx, int64_t ky, int64_t kz) const {
+    int64_t ax = kx < 0 ? -kx : kx, ay = ky < 0 ? -ky : ky, az = kz < 0 ? -kz : kz;
+    if (hf[l]) {
+        int64_t gx = ax > 1 ? ax - 1 : 0, gy = ay > 1 ? ay - 1 : 0, gz = az > 1 ? az - 1 : 0;
+        int64_t S = gx * gx + gy * gy + gz * gz;
+        double w = radius(l);
+        double A = std::max(kappa * w * w, 2 * w);
+        double s = side(l);
+        return A * A <= eta * eta * s * s * (double)S;
+    }
+    return std::max(ax, std::max(ay, az)) >= 2;
+}
+
+// ---------------------------------------------------------------- directions
+int64_t num_directions(int E) { return 6LL << (2 * E); }
+
+static void direction_int(int E, int64_t d, int64_t w[3]) {
+    int64_t n = 1LL << E;
+    int64_t f = d / (n * n), rem = d % (n * n);
+    int64_t i = rem / n, j = rem % n;
+    int m = (int)(f / 2);
+    int64_t sign = (f % 2 == 0) ? 1 : -1;
+    int m1 = (m == 0) ? 1 : 0, m2 = (m == 2) ? 1 : 2;
+    w[m] = sign * n;
+    w[m1] = 2 * i + 1 - n;
+    w[m2] = 2 * j + 1 - n;
+}
+
+void direction_vector(int E, int64_t d, double out[3]) {
+    int64_t w[3];
+    direction_int(E, d, w);
+    double nrm = std::sqrt((double)(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+    for (int a = 0; a < 3; ++a) out[a] = (double)w[a] / nrm;
+}
+
+int64_t direction_father(int E, int64_t d) {
+    int64_t n = 1LL << E, h = n / 2;
+    int64_t f = d / (n * n), rem = d % (n * n);
+    int64_t i = rem / n, j = rem % n;
+    return f * h * h + (i / 2) * h + (j / 2);
+}
+
+int64_t direction_negate(int E, int64_t d) {
+    int64_t n = 1LL << E;
+    int64_t f = d / (n * n), rem = d % (n * n);
+    int64_t i = rem / n, j = rem % n;
+    return (f ^ 1) * n * n + (n - 1 - i) * n + (n - 1 - j);
+}
+
+// argmax_v <v,k>/|v| over the level's directions, exact in integers; lowest
+// index among ties for k whose first non-zero entry is positive, and the
+// negated choice for the opposite k (so u(-k) = -u(k)).
+static int64_t best_positive(int E, int64_t kx, int64_t ky, int64_t kz) {
+    int64_t nd = num_directions(E);
+    int64_t best = -1;
+    __int128 bdot = 0, bn2 = 1;
+    for (int64_t d = 0; d < nd; ++d) {
+        int64_t w[3];
+        direction_int(E, d, w);
+        int64_t dot = w[0] * kx + w[1] * ky + w[2] * kz;
+        if (dot <= 0) continue;
+        int64_t n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        if (best < 0) {
+            best = d; bdot = dot; bn2 = n2;
+            continue;
+        }
+        __int128 lhs = (__int128)dot * dot * bn2;
+        __int128 rhs = bdot * bdot * (__int128)n2;
+        if (lhs > rhs) { best = d; bdot = dot; bn2 = n2; }
+    }
+    return best;
+}
+
+int64_t best_direction(int E, int64_t kx, int64_t ky, int64_t kz) {
+    int64_t first = kx != 0 ? kx : (ky != 0 ? ky : kz);
+    if (first > 0) return best_positive(E, kx, ky, kz);
+    return direction_negate(E, best_positive(E, -kx, -ky, -kz));
+}
+
+// ---------------------------------------------------------------- symmetries
+static const int kPerms[6][3] = DEFMM_PERM_TABLE;
+
+Canon canonical(int64_t kx, int64_t ky, int64_t kz) {
+    int64_t k[3] = {kx, ky, kz};
+    int order[3] = {0, 1, 2};
+    std::stable_sort(order, order + 3, [&](int a, int b) {
+        int64_t va = k[a] < 0 ? -k[a] : k[a], vb = k[b] < 0 ? -k[b] : k[b];
+        return va > vb;
+    });
+    Canon c;
+    for (int j = 0; j < 3; ++j) {
+        int64_t v = k[order[j]];
+        c.kbar[j] = (int)(v < 0 ? -v : v);
+        c.sigma[order[j]] = j;
+    }
+    for (int i = 0; i < 3; ++i) c.sign[i] = k[i] < 0 ? -1 : 1;
+    return c;
+}
+
+int transform_code(const Canon& c) {
+    int pid = -1;
+    for (int q = 0; q < 6; ++q)
+        if (kPerms[q][0] == c.sigma[0] && kPerms[q][1] == c.sigma[1] && kPerms[q][2] == c.sigma[2])
+            pid = q;
+    int mask = (c.sign[0] < 0 ? 1 : 0) | (c.sign[1] < 0 ? 2 : 0) | (c.sign[2] < 0 ? 4 : 0);
+    return pid * 8 + mask;
+}
+
+// ---------------------------------------------------------------- tree
+static void build_tree(const double* P, int64_t n, const double corner[3], double side, int ncrit,
+                       Tree& t) {
+    std::vector<int64_t> key(n);
+    const double scale = (double)(1LL << kMaxLevel);
+    const int64_t gmax = (1LL << kMaxLevel) - 1;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t g[3];
+        for (int a = 0; a < 3; ++a) {
+            double v = (P[3 * i + a] - corner[a]) / side * scale;
+            int64_t q = (int64_t)std::floor(v);
+            g[a] = q < 0 ? 0 : (q > gmax ? gmax : q);
+        }
+        int64_t k = 0;
+        for (int b = 0; b < kMaxLevel; ++b)
+            for (int a = 0; a < 3; ++a) k |= ((g[a] >> b) & 1) << (3 * b + a);
+        key[i] = k;
+    }
+    t.perm.resize(n);
+    std::iota(t.perm.begin(), t.perm.end(), 0);
+    std::stable_sort(t.perm.begin(), t.perm.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+    std::vector<int64_t> skey(n);
+    for (int64_t i = 0; i < n; ++i) skey[i] = key[t.perm[i]];
+
+    t.level = {0}; t.ix = {0}; t.iy = {0}; t.iz = {0};
+    t.begin = {0}; t.end = {n}; t.parent = {-1};
+    t.first_child.clear(); t.nchild.clear(); t.level_range.clear();
+    int32_t start = 0;
+    int lev = 0;
+    while (start < (int32_t)t.level.size()) {
+        int32_t stop = (int32_t)t.level.size();
+        t.level_range.push_back({start, stop});
+        for (int32_t c = start; c < stop; ++c) {
+            int64_t b = t.begin[c], e = t.end[c];
+            if (e - b > ncrit && lev < kMaxLevel) {
+                int shift = 3 * (kMaxLevel - lev - 1);
+                int64_t base = (skey[b] >> shift) >> 3 << 3;
+                t.first_child.push_back((int32_t)t.level.size());
+                int32_t nch = 0;
+                int64_t lo = b;
+                for (int o = 0; o < 8; ++o) {
+                    // first index in [lo, e) whose prefix exceeds base + o
+                    int64_t hi = std::upper_bound(skey.begin() + lo, skey.begin() + e, 0,
+                                                  [&](int, int64_t kk) { return (kk >> shift) > base + o; }) -
+                                 skey.begin();
+                    if (hi > lo) {
+                        t.level.push_back(lev + 1);
+                        t.ix.push_back(2 * t.ix[c] + (o & 1));
+                        t.iy.push_back(2 * t.iy[c] + ((o >> 1) & 1));
+                        t.iz.push_back(2 * t.iz[c] + ((o >> 2) & 1));
+                        t.begin.push_back(lo);
+                        t.end.push_back(hi);
+                        t.parent.push_back(c);
+                        ++nch;
+                    }
+                    lo = hi;
+                }
+                t.nchild.push_back(nch);
+            } else {
+                t.first_child.push_back(-1);
+                t.nchild.push_back(0);
+            }
+        }
+        start = stop;
+        ++lev;
+    }
+}
+
+static int octant_of(const Tree& t, int32_t c) {
+    return (t.ix[c] & 1) + 2 * (t.iy[c] & 1) + 4 * (t.iz[c] & 1);
+}
+
+static void sort_unique(std::vector<int32_t>& v) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+}
+
+// ---------------------------------------------------------------- plan
+void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa,
+                     int order, int leaf, double eta, double hf_kw, int fft_n, double self_eps,
+                     HostPlan& hp) {
+    if (nx < 1 || ny < 1) throw std::runtime_error("nx and ny must be >= 1");
+    if (order < 2 || order > kMaxOrder) throw std::runtime_error("order must be in [2, 8]");
+    if (leaf < 1) throw std::runtime_error("leaf_size must be >= 1");
+    if (!(kappa >= 0) || !std::isfinite(kappa)) throw std::runtime_error("kappa must be finite and >= 0");
+    if (!(eta > 0)) throw std::runtime_error("eta must be > 0");
+    if (nx > (1LL << 31) - 2 || ny > (1LL << 31) - 2) throw std::runtime_error("too many points (> 2^31)");
+    hp.nx = nx; hp.ny = ny; hp.same = (Y == nullptr);
+    hp.kappa = kappa; hp.p = order; hp.eta = eta; hp.hf_kw = hf_kw; hp.self_eps_rel = self_eps;
+    hp.N = fft_n > 0 ? fft_n : 2 * order - 1;
+    if (hp.N < 2 * order - 1) throw std::runtime_error("fft_n must be >= 2*order - 1");
+    if (hp.N > 16) throw std::runtime_error("fft_n must be <= 16");
+    hp.NF = hp.N * hp.N * hp.N;
+    hp.NFpad = (hp.NF + 3) / 4 * 4;
+    hp.P3 = order * order * order;
+    for (int64_t i = 0; i < 3 * nx; ++i)
+        if (!std::isfinite(X[i])) throw std::runtime_error("non-finite target coordinate");
+    if (Y)
+        for (int64_t i = 0; i < 3 * ny; ++i)
+            if (!std::isfinite(Y[i])) throw std::runtime_error("non-finite source coordinate");
+
+    // bounding cube of X u Y, enlarged by 1 + 2^-20 (Sec. 1, Sec. 2.3)
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = X[a]; hi[a] = X[a]; }
+    auto grow = [&](const double* P, int64_t n) {
+        for (int64_t i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], P[3 * i + a]);
+                hi[a] = std::max(hi[a], P[3 * i + a]);
+            }
+    };
+    grow(X, nx);
+    if (Y) grow(Y, ny);
+    double d = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    if (d == 0.0) d = 1.0;
+    hp.d_aabb = d;
+    hp.side = d * (1.0 + std::ldexp(1.0, -20));
+    for (int a = 0; a < 3; ++a) hp.corner[a] = (lo[a] + hi[a]) / 2.0 - hp.side / 2.0;
+    hp.eps_self = self_eps * d;
+
+    build_tree(X, nx, hp.corner, hp.side, leaf, hp.tt);
+    if (Y) build_tree(Y, ny, hp.corner, hp.side, leaf, hp.ts_own);
+    const Tree& tt = hp.tt;
+    const Tree& ts = hp.ts();
+
+    Levels& lv = hp.lv;
+    lv.side0 = hp.side; lv.kappa = kappa; lv.eta = eta; lv.hf_kw = hf_kw;
+    lv.l_hf = -1;
+    for (int l = 0; l < kNumLevels; ++l) {
+        lv.hf[l] = kappa * lv.radius(l) > hf_kw;
+        if (lv.hf[l]) lv.l_hf = l;
+    }
+    lv.hf[kNumLevels] = false;
+    if (lv.l_hf >= 0 && lv.l_hf > 12)
+        throw std::runtime_error("kappa*D too large: more than 12 high-frequency levels");
+
+    // ---- Alg. 1: dual tree traversal from (root, root)
+    std::unordered_map<int64_t, int32_t> dir_memo;
+    auto pair_dir = [&](int l, int64_t kx, int64_t ky, int64_t kz) -> int32_t {
+        if (!lv.hf[l]) return -1;
+        int64_t key = ((((int64_t)l * 4096 + (kx + 2048)) * 4096) + (ky + 2048)) * 4096 + (kz + 2048);
+        auto it = dir_memo.find(key);
+        if (it != dir_memo.end()) return it->second;
+        int32_t u = (int32_t)best_direction(lv.E(l), kx, ky, kz);
+        dir_memo[key] = u;
+        return u;
+    };
+    std::function<void(int32_t, int32_t)> visit = [&](int32_t t, int32_t s) {
+        int l = tt.level[t];
+        int64_t kx = (int64_t)tt.ix[t] - ts.ix[s], ky = (int64_t)tt.iy[t] - ts.iy[s],
+                kz = (int64_t)tt.iz[t] - ts.iz[s];
+        if (lv.mac(l, kx, ky, kz)) {
+            hp.m2l.push_back({t, s, pair_dir(l, kx, ky, kz)});
+            return;
+        }
+        if (tt.leaf(t) || ts.leaf(s)) {
+            hp.p2p.push_back({t, s});
+            return;
+        }
+        for (int32_t a = 0; a < tt.nchild[t]; ++a)
+            for (int32_t b = 0; b < ts.nchild[s]; ++b) visit(tt.first_child[t] + a, ts.first_child[s] + b);
+    };
+    visit(0, 0);
+
+    // ---- Alg. 2 marks + Alg. 3 blank downward pass on both trees
+    hp.marks_t.assign(tt.ncell(), {});
+    hp.marks_s.assign(ts.ncell(), {});
+    for (auto& pr : hp.m2l)
+        if (pr[2] >= 0) {
+            hp.marks_t[pr[0]].push_back(pr[2]);
+            hp.marks_s[pr[1]].push_back(pr[2]);
+        }
+    auto downward = [&](const Tree& tr, std::vector<std::vector<int32_t>>& marks) {
+        for (int32_t c = 0; c < tr.ncell(); ++c) {
+            int l = tr.level[c];
+            if (!lv.hf[l]) {
+                marks[c].assign(1, -1);
+                continue;
+            }
+            sort_unique(marks[c]);
+            if (!lv.hf[l + 1]) continue;
+            for (int32_t a = 0; a < tr.nchild[c]; ++a)
+                for (int32_t u : marks[c])
+                    marks[tr.first_child[c] + a].push_back((int32_t)direction_father(lv.E(l), u));
+        }
+    };
+    downward(tt, hp.marks_t);
+    downward(ts, hp.marks_s);
+
+    // ---- effective expansions
+    auto enumerate = [&](const Tree& tr, const std::vector<std::vector<int32_t>>& marks,
+                         std::vector<int32_t>& cell, std::vector<int32_t>& dir,
+                         std::vector<int32_t>& first, std::vector<int32_t>& count) {
+        first.assign(tr.ncell(), 0);
+        count.assign(tr.ncell(), 0);
+        for (int32_t c = 0; c < tr.ncell(); ++c) {
+            first[c] = (int32_t)cell.size();
+            for (int32_t u : marks[c]) { cell.push_back(c); dir.push_back(u); }
+            count[c] = (int32_t)marks[c].size();
+        }
+    };
+    enumerate(ts, hp.marks_s, hp.m_cell, hp.m_dir, hp.m_first, hp.m_count);
+    enumerate(tt, hp.marks_t, hp.l_cell, hp.l_dir, hp.l_first, hp.l_count);
+    auto find_exp = [](const std::vector<int32_t>& dir, int32_t first, int32_t count, int32_t u) -> int32_t {
+        auto b = dir.begin() + first, e = b + count;
+        auto it = std::lower_bound(b, e, u);
+        if (it == e || *it != u) return -1;
+        return (int32_t)(it - dir.begin());
+    };
+
+    // ---- phase slots per (level, direction) (Sec. 5.2.1 diagonal factors)
+    std::unordered_map<int64_t, int32_t> slot_of;
+    const int p = order;
+    auto get_slot = [&](int l, int32_t u) -> int32_t {
+        if (u < 0) return -1;
+        int64_t key = (int64_t)l * (1LL << 40) + u;
+        auto it = slot_of.find(key);
+        if (it != slot_of.end()) return it->second;
+        int32_t s = (int32_t)hp.slot_level.size();
+        slot_of[key] = s;
+        hp.slot_level.push_back(l);
+        hp.slot_dir.push_back(u);
+        double v[3];
+        direction_vector(lv.E(l), u, v);
+        for (int a = 0; a < 3; ++a) hp.slot_u.push_back(v[a]);
+        double side = lv.side(l);
+        for (int a = 0; a < 3; ++a)
+            for (int m = 0; m < p; ++m) {
+                double arg = kappa * side * ((double)m / (p - 1) - 0.5) * v[a];
+                hp.slot_P.push_back(std::cos(arg));
+                hp.slot_P.push_back(std::sin(arg));
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int o = 0; o < 2; ++o)
+                for (int b = 0; b < p; ++b) {
+                    double arg = kappa * side * ((o + (double)b / (p - 1)) / 2 - 0.5) * v[a];
+                    hp.slot_Q.push_back(std::cos(arg));
+                    hp.slot_Q.push_back(std::sin(arg));
+                }
+        return s;
+    };
+    hp.m_slot.resize(hp.m_cell.size());
+    for (size_t e = 0; e < hp.m_cell.size(); ++e) hp.m_slot[e] = get_slot(ts.level[hp.m_cell[e]], hp.m_dir[e]);
+    hp.l_slot.resize(hp.l_cell.size());
+    for (size_t e = 0; e < hp.l_cell.size(); ++e) hp.l_slot[e] = get_slot(tt.level[hp.l_cell[e]], hp.l_dir[e]);
+
+    // 1-D interpolation matrices M1[o][a][b] = l_a((o + b/(p-1))/2) and twiddles
+    hp.m1.assign(2 * p * p, 0.0);
+    for (int o = 0; o < 2; ++o)
+        for (int a = 0; a < p; ++a)
+            for (int b = 0; b < p; ++b) {
+                double t = (o + (double)b / (p - 1)) / 2;
+                double v = 1.0;
+                for (int m = 0; m < p; ++m)
+                    if (m != a) v *= (t - (double)m / (p - 1)) / ((double)a / (p - 1) - (double)m / (p - 1));
+                hp.m1[(o * p + a) * p + b] = v;
+            }
+    hp.tw.assign(2 * hp.N, 0.0);
+    for (int m = 0; m < hp.N; ++m) {
+        double ang = 2.0 * 3.14159265358979323846 * m / hp.N;
+        hp.tw[2 * m] = std::cos(ang);
+        hp.tw[2 * m + 1] = std::sin(ang);
+    }
+
+    // ---- spectra and M2L tables
+    std::unordered_map<int64_t, int32_t> spec_of;
+    struct PairRec { int32_t tgt, src, spec, code, order; };
+    std::vector<PairRec> recs;
+    recs.reserve(hp.m2l.size());
+    std::vector<int32_t> is_src(hp.m_cell.size(), 0);
+    for (size_t i = 0; i < hp.m2l.size(); ++i) {
+        auto& pr = hp.m2l[i];
+        int32_t t = pr[0], s = pr[1], u = pr[2];
+        int l = tt.level[t];
+        int64_t kx = (int64_t)tt.ix[t] - ts.ix[s], ky = (int64_t)tt.iy[t] - ts.iy[s],
+                kz = (int64_t)tt.iz[t] - ts.iz[s];
+        Canon cn = canonical(kx, ky, kz);
+        int64_t key = (((int64_t)l * 4096 + cn.kbar[0]) * 4096 + cn.kbar[1]) * 4096 + cn.kbar[2];
+        int32_t sid;
+        auto it = spec_of.find(key);
+        if (it == spec_of.end()) {
+            sid = (int32_t)hp.spec_level.size();
+            spec_of[key] = sid;
+            hp.spec_level.push_back(l);
+            hp.spec_kbar.push_back({cn.kbar[0], cn.kbar[1], cn.kbar[2]});
+        } else {
+            sid = it->second;
+        }
+        int32_t te = find_exp(hp.l_dir, hp.l_first[t], hp.l_count[t], u);
+        int32_t se = find_exp(hp.m_dir, hp.m_first[s], hp.m_count[s], u);
+        if (te < 0 || se < 0) throw std::runtime_error("internal: M2L expansion missing");
+        is_src[se] = 1;
+        recs.push_back({te, se, sid, transform_code(cn), (int32_t)i});
+    }
+    hp.mhat_of_m.assign(hp.m_cell.size(), -1);
+    for (size_t e = 0; e < hp.m_cell.size(); ++e)
+        if (is_src[e]) {
+            hp.mhat_of_m[e] = (int32_t)hp.m2f_list.size();
+            hp.m2f_list.push_back((int32_t)e);
+        }
+    std::stable_sort(recs.begin(), recs.end(), [](const PairRec& a, const PairRec& b) { return a.tgt < b.tgt; });
+    hp.m2l_off.push_back(0);
+    for (size_t i = 0; i < recs.size(); ++i) {
+        if (i == 0 || recs[i].tgt != recs[i - 1].tgt) {
+            if (i > 0) hp.m2l_off.push_back((int32_t)i);
+            hp.m2l_tgt.push_back(recs[i].tgt);
+        }
+        hp.m2l_src.push_back(hp.mhat_of_m[recs[i].src]);
+        hp.m2l_spec.push_back(recs[i].spec * 64 + recs[i].code);
+    }
+    if (!recs.empty()) hp.m2l_off.push_back((int32_t)recs.size());
+
+    // ---- M2M per parent level (source tree)
+    int nlev_s = (int)ts.level_range.size();
+    hp.m2m_lvl.assign(nlev_s, {});
+    for (int l = 0; l < nlev_s; ++l) {
+        for (int32_t c = ts.level_range[l].first; c < ts.level_range[l].second; ++c) {
+            if (ts.leaf(c) || hp.m_count[c] == 0) continue;
+            for (int32_t e = hp.m_first[c]; e < hp.m_first[c] + hp.m_count[c]; ++e) {
+                int32_t v = hp.m_dir[e];
+                int32_t u2 = (v < 0 || !lv.hf[l + 1]) ? -1 : (int32_t)direction_father(lv.E(l), v);
+                int32_t ch[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+                for (int32_t a = 0; a < ts.nchild[c]; ++a) {
+                    int32_t c2 = ts.first_child[c] + a;
+                    int32_t ce = find_exp(hp.m_dir, hp.m_first[c2], hp.m_count[c2], u2);
+                    if (ce < 0) throw std::runtime_error("internal: M2M child expansion missing");
+                    ch[octant_of(ts, c2)] = ce;
+                }
+                hp.m2m_lvl[l].push_back(e);
+                for (int o = 0; o < 8; ++o) hp.m2m_lvl[l].push_back(ch[o]);
+            }
+        }
+    }
+
+    // ---- L2L per child level (target tree)
+    int nlev_t = (int)tt.level_range.size();
+    hp.l2l_lvl.assign(nlev_t, {});
+    hp.l2l_par.assign(nlev_t, {});
+    for (int l = 1; l < nlev_t; ++l) {
+        for (int32_t c = tt.level_range[l].first; c < tt.level_range[l].second; ++c) {
+            int32_t par = tt.parent[c];
+            if (hp.l_count[par] == 0) continue;
+            for (int32_t e = hp.l_first[c]; e < hp.l_first[c] + hp.l_count[c]; ++e) {
+                int32_t u = hp.l_dir[e];
+                int32_t first = (int32_t)hp.l2l_par[l].size();
+                for (int32_t pe = hp.l_first[par]; pe < hp.l_first[par] + hp.l_count[par]; ++pe) {
+                    int32_t v = hp.l_dir[pe];
+                    int32_t want = (v < 0 || !lv.hf[l]) ? -1 : (int32_t)direction_father(lv.E(l - 1), v);
+                    if (want == u) hp.l2l_par[l].push_back(pe);
+                }
+                int32_t cnt = (int32_t)hp.l2l_par[l].size() - first;
+                if (cnt == 0) continue;
+                hp.l2l_lvl[l].push_back(e);
+                hp.l2l_lvl[l].push_back(octant_of(tt, c));
+                hp.l2l_lvl[l].push_back(first);
+                hp.l2l_lvl[l].push_back(cnt);
+            }
+        }
+    }
+
+    // ---- leaves for P2M / L2P
+    for (int32_t c = 0; c < ts.ncell(); ++c)
+        if (ts.leaf(c) && hp.m_count[c] > 0) hp.p2m_cells.push_back(c);
+    for (int32_t c = 0; c < tt.ncell(); ++c)
+        if (tt.leaf(c) && hp.l_count[c] > 0) hp.l2p_cells.push_back(c);
+
+    // ---- P2P: per target leaf, the source ranges of its near pairs
+    std::vector<std::vector<int32_t>> near(tt.ncell());
+    std::function<void(int32_t, int32_t)> push_down = [&](int32_t t, int32_t s) {
+        if (tt.leaf(t)) { near[t].push_back(s); return; }
+        for (int32_t a = 0; a < tt.nchild[t]; ++a) push_down(tt.first_child[t] + a, s);
+    };
+    for (auto& pr : hp.p2p) push_down(pr[0], pr[1]);
+    hp.p2p_off.push_back(0);
+    for (int32_t c = 0; c < tt.ncell(); ++c) {
+        if (!tt.leaf(c)) continue;
+        hp.p2p_leaf.push_back(c);
+        auto& v = near[c];
+        std::sort(v.begin(), v.end(), [&](int32_t a, int32_t b) { return ts.begin[a] < ts.begin[b]; });
+        int64_t nt = tt.end[c] - tt.begin[c];
+        for (size_t i = 0; i < v.size(); ++i) {
+            int32_t b = (int32_t)ts.begin[v[i]], e = (int32_t)ts.end[v[i]];
+            hp.p2p_interactions += nt * (int64_t)(e - b);
+            if (!hp.p2p_sbeg.empty() && (int32_t)hp.p2p_sbeg.size() > hp.p2p_off.back() &&
+                hp.p2p_send.back() == b) {
+                hp.p2p_send.back() = e;  // merge contiguous ranges
+            } else {
+                hp.p2p_sbeg.push_back(b);
+                hp.p2p_send.push_back(e);
+            }
+        }
+        hp.p2p_off.push_back((int32_t)hp.p2p_sbeg.size());
+    }
+}
+
+}  // namespace defmm

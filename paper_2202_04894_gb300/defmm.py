@@ -1,0 +1,214 @@
+"""Python binding of libdefmm.so (include/defmm.h): argument marshalling only.
+
+Every step of the application phase runs in the library's CUDA kernels; this
+module allocates tensors with torch, passes raw pointers and the current CUDA
+stream, and converts status codes into exceptions.  There is no fallback:
+if the library is missing, importing it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdefmm.so")
+
+C64, C128 = 0, 1
+PLAN_HOST_ONLY = 1
+_STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
+           5: "ERR_UNSUPPORTED", 6: "ERR_BUSY"}
+
+EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_apply_host",
+            "defmm_destroy", "defmm_plan_info", "defmm_plan_table", "defmm_last_error"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("hf_kw", ctypes.c_double), ("fft_n", ctypes.c_int),
+                ("flags", ctypes.c_int), ("self_eps", ctypes.c_double),
+                ("hbm_budget", ctypes.c_size_t)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("order", ctypes.c_int32),
+                ("fft_n", ctypes.c_int32), ("nlevels", ctypes.c_int32), ("deepest_hf", ctypes.c_int32),
+                ("ncells_t", ctypes.c_int64), ("ncells_s", ctypes.c_int64),
+                ("n_m2l_pairs", ctypes.c_int64), ("n_p2p_pairs", ctypes.c_int64),
+                ("n_multipole", ctypes.c_int64), ("n_local", ctypes.c_int64),
+                ("n_fourier", ctypes.c_int64), ("n_spectra", ctypes.c_int64),
+                ("p2p_interactions", ctypes.c_int64), ("plan_bytes", ctypes.c_size_t),
+                ("workspace_bytes", ctypes.c_size_t), ("launches_per_apply", ctypes.c_int64),
+                ("d_aabb", ctypes.c_double), ("cube_side", ctypes.c_double)]
+
+
+class DefmmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    """Loads libdefmm.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdefmm.so is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        L.defmm_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.defmm_default_options.restype = None
+        L.defmm_plan_create.argtypes = [vp, i64, vp, i64, dbl, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
+        L.defmm_plan_create.restype = ctypes.c_int
+        L.defmm_apply.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+        L.defmm_apply.restype = ctypes.c_int
+        L.defmm_apply_host.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+        L.defmm_apply_host.restype = ctypes.c_int
+        L.defmm_destroy.argtypes = [vp]
+        L.defmm_destroy.restype = ctypes.c_int
+        L.defmm_plan_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.defmm_plan_info.restype = ctypes.c_int
+        L.defmm_plan_table.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(i64), i64, ctypes.POINTER(i64)]
+        L.defmm_plan_table.restype = ctypes.c_int
+        L.defmm_last_error.argtypes = []
+        L.defmm_last_error.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def _check(status):
+    if status != 0:
+        raise DefmmError(status, lib().defmm_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    import torch
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    if stream is None and not torch.cuda.is_available():
+        return None
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().defmm_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """A defmm plan: geometry, traversal tables and transfer spectra on the GPU.
+
+    X (nx, 3) and Y (ny, 3) are float64 arrays (numpy or torch, host or
+    device); Y=None means sources = targets (one tree).
+    """
+
+    def __init__(self, X, Y=None, kappa=1.0, order=4, leaf_size=64, stream=None, **options):
+        Xh = self._points(X)
+        Yh = None if Y is None else self._points(Y)
+        opt = default_options(**options)
+        h = ctypes.c_void_p()
+        self._keep = (Xh, Yh)
+        _check(lib().defmm_plan_create(
+            ctypes.c_void_p(Xh.data_ptr()), Xh.shape[0],
+            None if Yh is None else ctypes.c_void_p(Yh.data_ptr()),
+            Xh.shape[0] if Yh is None else Yh.shape[0],
+            float(kappa), int(order), int(leaf_size), ctypes.byref(opt),
+            None if (opt.flags & PLAN_HOST_ONLY) else _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+        self.nx = Xh.shape[0]
+        self.ny = Xh.shape[0] if Yh is None else Yh.shape[0]
+
+    @staticmethod
+    def _points(P):
+        import torch
+        if not isinstance(P, torch.Tensor):
+            P = torch.from_numpy(np.ascontiguousarray(P, dtype=np.float64))
+        P = P.to(torch.float64).contiguous()
+        if P.dim() != 2 or P.shape[1] != 3:
+            raise ValueError("points must have shape (n, 3)")
+        return P
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().defmm_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check(lib().defmm_destroy(self._h))
+        self._h = None
+
+    def info(self) -> dict:
+        i = Info()
+        _check(lib().defmm_plan_info(self._h, ctypes.byref(i)))
+        return {name: getattr(i, name) for name, _ in Info._fields_}
+
+    def table(self, name: str) -> np.ndarray:
+        n = ctypes.c_int64()
+        _check(lib().defmm_plan_table(self._h, name.encode(), None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, dtype=np.int64)
+        _check(lib().defmm_plan_table(self._h, name.encode(),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      n.value, ctypes.byref(n)))
+        return out
+
+    def apply(self, q, out=None, stream=None):
+        """p = A q on the GPU.  q: complex64/complex128 CUDA tensor (ny,) or (ny, R).
+
+        Returns p with the same shape convention (nx,) or (nx, R).
+        """
+        import torch
+        squeeze = q.dim() == 1
+        qm = q.reshape(-1, 1) if squeeze else q
+        if qm.shape[0] != self.ny:
+            raise ValueError("q has %d rows, plan has %d sources" % (qm.shape[0], self.ny))
+        if qm.dtype not in (torch.complex64, torch.complex128):
+            raise TypeError("q must be complex64 or complex128")
+        R = qm.shape[1]
+        qc = qm.t().contiguous()                      # (R, ny): column-major (ny, R)
+        if out is None:
+            pc = torch.empty((R, self.nx), dtype=qm.dtype, device=qm.device)
+        else:
+            pc = out
+        _check(lib().defmm_apply(self._h, ctypes.c_void_p(qc.data_ptr()), ctypes.c_void_p(pc.data_ptr()),
+                                 R, C64 if qm.dtype == torch.complex64 else C128, _stream_handle(stream)))
+        self._last_q = qc
+        res = pc.t()
+        return res[:, 0] if squeeze else res
+
+    def apply_raw(self, q_ptr: int, p_ptr: int, nrhs: int, dtype: int, stream=None):
+        """defmm_apply on raw device pointers (column-major (n, nrhs) buffers)."""
+        _check(lib().defmm_apply(self._h, ctypes.c_void_p(q_ptr), ctypes.c_void_p(p_ptr), int(nrhs),
+                                 int(dtype), _stream_handle(stream)))
+
+    def apply_host(self, q, out=None, stream=None):
+        """defmm_apply_host: q and p in host memory (numpy or pinned torch CPU tensors)."""
+        import torch
+        if isinstance(q, np.ndarray):
+            q = torch.from_numpy(q)
+        squeeze = q.dim() == 1
+        qm = q.reshape(-1, 1) if squeeze else q
+        R = qm.shape[1]
+        qc = qm.t().contiguous() if not (R == 1 and qm.is_contiguous()) else qm.reshape(1, -1)
+        pc = out if out is not None else torch.empty((R, self.nx), dtype=qm.dtype)
+        _check(lib().defmm_apply_host(self._h, ctypes.c_void_p(qc.data_ptr()), ctypes.c_void_p(pc.data_ptr()),
+                                      R, C64 if qm.dtype == torch.complex64 else C128, _stream_handle(stream)))
+        res = pc.t()
+        return res[:, 0] if squeeze else res

@@ -1,0 +1,105 @@
+"""CPU tests of the C ABI: the library loads, exports what include/defmm.h
+declares, validates arguments, and its host plan tables equal the oracle's."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import fmm as oracle_fmm
+from paper_2202_04894_gb300 import build as pkg_build
+from paper_2202_04894_gb300 import defmm, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    pkg_build.build()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "defmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(defmm_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    L = defmm.lib()
+    names = _declared()
+    assert len(names) >= 8
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(defmm.EXPORTED) <= set(names)
+
+
+def _host_plan(X, Y=None, **kw):
+    return defmm.Plan(X, Y, flags=defmm.PLAN_HOST_ONLY, **kw)
+
+
+def test_argument_errors():
+    X = W.points("sphere", 100, 1)
+    for kw, frag in [(dict(order=1), "order"), (dict(order=9), "order"), (dict(leaf_size=0), "leaf"),
+                     (dict(kappa=-1.0), "kappa"), (dict(fft_n=5, order=4), "fft_n")]:
+        args = dict(kappa=1.0, order=4, leaf_size=8)
+        args.update(kw)
+        with pytest.raises(defmm.DefmmError) as e:
+            _host_plan(X, **args)
+        assert e.value.status == 1 and frag in str(e.value)
+    bad = X.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(defmm.DefmmError):
+        _host_plan(bad, kappa=1.0, order=4, leaf_size=8)
+    pl = _host_plan(X, kappa=1.0, order=4, leaf_size=8)
+    with pytest.raises(defmm.DefmmError) as e:
+        pl.apply_raw(1, 1, 1, defmm.C64)
+    assert e.value.status == 5
+
+
+def _oracle_tables(op):
+    cells = np.stack([op.tt.level, op.tt.coords[:, 0], op.tt.coords[:, 1], op.tt.coords[:, 2],
+                      op.tt.begin, op.tt.end, op.tt.parent], 1)
+    m2l = sorted((t, s, u) for (t, s), u in zip(op.m2l_pairs, op.pair_dir))
+    mult = [(c, u) for c in range(op.ts.ncell) for u in op.marks_s[c]]
+    loc = [(c, u) for c in range(op.tt.ncell) for u in op.marks_t[c]]
+    return cells, m2l, sorted(op.p2p_pairs), mult, loc
+
+
+CASES = [
+    ("sphere", 2000, None, 4.0, 4, 64),
+    ("box", 4000, None, 16.0, 4, 20),
+    ("ellipsoid", 3000, ("sphere", 2500), 30.0, 3, 16),
+    ("cube", 2500, None, 0.0, 5, 10),
+    ("sphere", 1500, None, 60.0, 6, 8),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_plan_tables_equal_oracle(case):
+    """Tree, DTT pairs with best directions, and effective expansions are bit-identical."""
+    kind, n, other, kappa, order, leaf = case
+    X = W.points(kind, n, 3)
+    Y = None if other is None else 0.5 * W.points(other[0], other[1], 4)
+    pl = _host_plan(X, Y, kappa=kappa, order=order, leaf_size=leaf)
+    op = oracle_fmm.make_plan(X, Y, kappa=kappa, order=order, leaf=leaf)
+    cells, m2l, p2p, mult, loc = _oracle_tables(op)
+    assert np.array_equal(pl.table("perm_t"), op.tt.perm)
+    assert np.array_equal(pl.table("perm_s"), op.ts.perm)
+    assert np.array_equal(pl.table("cells_t").reshape(-1, 7), cells)
+    assert sorted(map(tuple, pl.table("m2l").reshape(-1, 3).tolist())) == [tuple(map(int, r)) for r in m2l]
+    assert sorted(map(tuple, pl.table("p2p").reshape(-1, 2).tolist())) == [tuple(map(int, r)) for r in p2p]
+    assert list(map(tuple, pl.table("mult").reshape(-1, 2).tolist())) == mult
+    assert list(map(tuple, pl.table("local").reshape(-1, 2).tolist())) == loc
+    info = pl.info()
+    assert info["n_m2l_pairs"] == len(m2l) and info["n_p2p_pairs"] == len(p2p)
+    assert info["deepest_hf"] == op.levels.l_hf
+    assert info["n_spectra"] == len(op.spectra)
+
+
+def test_degenerate_inputs_host_plan():
+    one = np.array([[0.1, 0.2, 0.3]])
+    pl = _host_plan(one, kappa=3.0, order=4, leaf_size=4)
+    assert pl.info()["ncells_t"] == 1 and pl.info()["n_p2p_pairs"] == 1
+    dup = np.repeat(np.array([[1.0, 2.0, 3.0]]), 10, axis=0)
+    pl = _host_plan(dup, kappa=3.0, order=4, leaf_size=3)
+    assert pl.info()["nlevels"] == 22
