@@ -1,0 +1,321 @@
+"""Benchmark of the defmm application phase on GB300.
+
+Default workload: 10^6 points on the unit sphere, kappa*D = 128, order 4,
+leaf <= 64, one complex64 right-hand side (the high-frequency configuration
+with directional levels active).  A step is one defmm_apply: gather, P2P,
+P2M, M2M, M2F, Hadamard M2L + F2L, L2L, L2P, scatter.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One JSON line on rank 0.  value = Mpoints*RHS/s over all ranks (replicas:
+each rank applies its own copy of the workload; there is no data-path
+collective).  Inputs are resident in HBM for `value`; `e2e` times the
+host-buffer entry point (defmm_apply_host) with both copies inside.  L2 is
+flushed (a 512 MB write) before every timed step, outside the step's events.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "sphere1M_kD128_p4"
+METRIC = "Mpoints·RHS/s at rel-L2 err≤1e-4 vs FP64 oracle; M2L HBM GB/s; p50/p99 ms"
+UNIT = "Mpoints·RHS/s"
+# CPU sample of the same workload: same distribution, order and leaf size, and
+# kappa*D scaled with sqrt(N) so that the points per wavelength^2 stay those of
+# the 10^6-point case.
+SAMPLE_N = 16000          # cpu_baseline: ~10-20 s of single-core oracle work
+ORACLE_S_PER_POINT = 6e-4  # measured oracle cost on this recipe, used to size samples
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = (bus_id or "").lower()
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 10:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for r in self.rows if not self.bus_id or self.bus_id.endswith(r[1].lower()[-12:])
+                or r[1].lower().endswith(self.bus_id[-12:])]
+        rows = rows or self.rows
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_sample(n=SAMPLE_N):
+    """The oracle on a bounded sample of the workload (same recipe, n points)."""
+    from paper_2202_04894_gb300 import workloads as W
+    w = W.WORKLOADS[WORKLOAD]
+    kd = w["kappa_d"] * (n / w["n"]) ** 0.5
+    X = W.points(w["kind"], n, w["seed"])
+    kappa = kd / float(np.max(X.max(0) - X.min(0)))
+    q = W.charges(n, w["seed"], w["nrhs"])
+    desc = ("sphere, %d points, kappa*D=%.2f (10^6-point density per wavelength^2), order %d, leaf %d, "
+            "%d RHS, float64 oracle" % (n, kd, w["order"], w["leaf"], w["nrhs"]))
+    return X, q, kappa, w["order"], w["leaf"], desc
+
+
+def time_oracle(steps, warmup, n=SAMPLE_N):
+    from oracle import fmm
+    X, q, kappa, order, leaf, desc = cpu_sample(n)
+    plan = fmm.make_plan(X, kappa=kappa, order=order, leaf=leaf)
+    for _ in range(warmup):
+        fmm.apply(plan, X, q)
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        fmm.apply(plan, X, q)
+        ts.append(time.perf_counter() - t0)
+    sec = sum(ts) / len(ts)
+    return len(X) * q.shape[1] / sec / 1e6, sec, desc
+
+
+def oracle_subprocess(steps, warmup, n, timeout=1800):
+    """Runs time_oracle in a fresh single-threaded interpreter (BLAS pinned to 1 thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.time_oracle(%d, %d, %d)))" % (ROOT, steps, warmup, n))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-400:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    # each step is a bounded sample sized so that the whole run takes ~2.5 minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n = int(min(SAMPLE_N, max(1000, budget / ORACLE_S_PER_POINT)))
+    value, sec, desc = oracle_subprocess(args.steps, args.warmup, n)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="defmm", choices=["defmm", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    import __graft_entry__
+    from paper_2202_04894_gb300 import defmm, workloads as W
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    W_ = W.WORKLOADS[args.workload]
+    X, q, kappa, order, leaf, dtype = W.make(args.workload)
+    cdt = torch.complex64 if dtype == "c64" else torch.complex128
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plan = defmm.Plan(X, kappa=kappa, order=order, leaf_size=leaf)
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    R = q.shape[1]
+    qd = torch.from_numpy(np.ascontiguousarray(q)).to("cuda").to(cdt)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # accuracy of the timed (complex64) form against the float64 path
+    p_lo = plan.apply(qd)
+    p_hi = plan.apply(qd.to(torch.complex128))
+    torch.cuda.synchronize()
+    rel = float(torch.linalg.norm(p_lo.to(torch.complex128) - p_hi) / torch.linalg.norm(p_hi))
+
+    for _ in range(args.warmup):
+        plan.apply(qd)
+    plan.profile(True)
+    phase_sum = {}
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    bus = None
+    try:
+        props = torch.cuda.get_device_properties(local)
+        bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except Exception:
+        pass
+    clocks = ClockSampler(bus)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        plan.apply(qd)
+        ends[k].record(stream)
+        ends[k].synchronize()
+        step_ms.append(starts[k].elapsed_time(ends[k]))
+        for name, ms in plan.phase_ms().items():
+            phase_sum[name] = phase_sum.get(name, 0.0) + ms
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    plan.profile(False)
+    launches_per_apply = int(plan.info()["launches_per_apply"])
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    units = world * len(X) * R
+    value = units / (ms_per_step * 1e-3) / 1e6
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    qh = torch.from_numpy(np.ascontiguousarray(q.T)).to(cdt).pin_memory()
+    ph = torch.empty((R, len(X)), dtype=cdt).pin_memory()
+    for _ in range(3):
+        plan.apply_host(qh.t(), out=ph)
+    e2e_ms = []
+    for k in range(max(5, args.steps // 5)):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.apply_host(qh.t(), out=ph)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = units / (statistics.mean(e2e_ms) * 1e-3) / 1e6
+    csz = 8 if cdt == torch.complex64 else 16
+
+    # dominant phase and its roofline
+    phase_avg = {k: v / args.steps for k, v in phase_sum.items()}
+    NF = info["fft_n"] ** 3
+    P3 = order ** 3
+    m2l_bytes = (info["n_m2l_pairs"] * R * csz * NF + info["n_spectra"] * csz * NF)
+    m2l_gbs = m2l_bytes / (phase_avg["m2l"] * 1e-3) / 1e9
+    peak_gbs, peak_kind = _peaks()
+    dominant = max(phase_avg, key=phase_avg.get)
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    if dominant == "p2p":
+        # P2P: 3 SFU operations (rsqrt, sin, cos) per interaction; 16 SFU results
+        # per clock per SM on 152 SMs
+        inter = info["p2p_interactions"] * R
+        achieved = inter / (phase_avg["p2p"] * 1e-3) / 1e9
+        peak = 152 * 16 / 3 * sm_max * 1e6 / 1e9
+        roof = {"kernel": "p2p", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginteractions/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "SFU: 152 SMs x 16/clk / 3 per interaction at %.0f MHz" % sm_max}
+    else:
+        roof = {"kernel": "m2l", "bound": "hbm", "achieved": m2l_gbs, "peak": peak_gbs, "unit": "GB/s",
+                "frac": m2l_gbs / peak_gbs, "traffic": None, "peak_source": peak_kind}
+    m2l_roof = {"bound": "hbm", "achieved": m2l_gbs, "peak": peak_gbs, "unit": "GB/s", "frac": m2l_gbs / peak_gbs,
+                "algorithmic_bytes": m2l_bytes, "ms": phase_avg["m2l"], "peak_source": peak_kind}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v, s, d = oracle_subprocess(1, 0, SAMPLE_N)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": d, "seconds": s}
+        except Exception as ex:  # reported, never fatal
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(ex)[:200]}
+
+    if rank == 0:
+        srt = sorted(step_ms)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": {"workload": args.workload, "points": len(X), "kappa_d": W_["kappa_d"], "order": order,
+                           "leaf": leaf, "nrhs": R, "distribution": W_["kind"], "l2": "flushed (512 MB write) before each step",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roof, "m2l_roofline": m2l_roof,
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(X) * R * csz,
+                        "d2h_bytes_per_step": len(X) * R * csz, "ms_per_step": statistics.mean(e2e_ms)},
+                "clocks": clk, "gpu_launches": launches_per_apply * args.steps,
+                "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                "rel_l2_c64_vs_c128": rel, "phase_ms": phase_avg, "plan_s": plan_s,
+                "plan": {k: info[k] for k in ("n_m2l_pairs", "n_p2p_pairs", "n_multipole", "n_local", "n_fourier",
+                                              "n_spectra", "p2p_interactions", "nlevels", "deepest_hf")}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,16 @@ defmm_status defmm_plan_info(defmm_plan plan, defmm_info* out);
 defmm_status defmm_plan_table(defmm_plan plan, const char* name, int64_t* out,
                               int64_t capacity, int64_t* count);
 
+/* Per-phase timing of the application phase, with CUDA events recorded on the
+ * apply's own stream between its kernel groups.  enable = 1 turns recording on
+ * for later defmm_apply calls on this plan (0 turns it off).  Phases, in
+ * order: gather, p2p, p2m, m2m, m2f, m2l (Hadamard + F2L), l2l, l2p, scatter.
+ * defmm_profile_read waits for the last profiled apply and writes up to
+ * capacity phase durations in milliseconds to ms (host) and their number to
+ * *nphase.  Errors: DEFMM_ERR_ARG (no profiled apply yet), DEFMM_ERR_CUDA.   */
+defmm_status defmm_profile_enable(defmm_plan plan, int enable);
+defmm_status defmm_profile_read(defmm_plan plan, double* ms, int capacity, int* nphase);
+
 const char* defmm_last_error(void);
 
 #ifdef __cplusplus

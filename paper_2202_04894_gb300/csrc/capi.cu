@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/defmm.h"
+#include "defmm.h"
 #include "kernels.cuh"
 #include "plan.h"
 
@@ -83,6 +83,9 @@ struct defmm_plan_s {
     size_t hbm_budget = 0;
     int64_t launches = 0;
     bool host_only = false;
+    bool profiling = false;
+    bool profiled = false;
+    cudaEvent_t events[kNumPhases + 1] = {};
     std::mutex busy;
 };
 
@@ -276,8 +279,10 @@ template <typename T> defmm_status apply_impl(defmm_plan_s* pl, Workspace<T>& w,
     const DevTyped<T>& typed = typed_tables(pl, (T*)nullptr);
     int launches = 0;
     cudaError_t e = launch_apply<T>(pl->common, typed, dw, pl->m2m.data(), (int)pl->m2m.size(), pl->l2l.data(),
-                                    pl->l2l_par.data(), (int)pl->l2l.size(), q, p, stream, &launches);
+                                    pl->l2l_par.data(), (int)pl->l2l.size(), q, p, stream, &launches,
+                                    pl->profiling ? pl->events : nullptr);
     pl->launches = launches;
+    if (pl->profiling && e == cudaSuccess) pl->profiled = true;
     if (e != cudaSuccess) return cuda_fail(e, "apply launch");
     return DEFMM_OK;
 }
@@ -388,6 +393,28 @@ defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host,
     return DEFMM_OK;
 }
 
+defmm_status defmm_profile_enable(defmm_plan plan, int enable) {
+    if (!plan) return fail(DEFMM_ERR_ARG, "plan is NULL");
+    if (plan->host_only) return fail(DEFMM_ERR_UNSUPPORTED, "plan was built with DEFMM_PLAN_HOST_ONLY");
+    if (enable && !plan->events[0])
+        for (int i = 0; i <= kNumPhases; ++i) CK(cudaEventCreate(&plan->events[i]), "event create");
+    plan->profiling = enable != 0;
+    return DEFMM_OK;
+}
+
+defmm_status defmm_profile_read(defmm_plan plan, double* ms, int capacity, int* nphase) {
+    if (!plan || !nphase) return fail(DEFMM_ERR_ARG, "null argument");
+    if (!plan->profiled) return fail(DEFMM_ERR_ARG, "no profiled apply yet");
+    CK(cudaEventSynchronize(plan->events[kNumPhases]), "profile wait");
+    *nphase = kNumPhases;
+    for (int i = 0; i < kNumPhases && i < capacity; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, plan->events[i], plan->events[i + 1]), "profile elapsed");
+        if (ms) ms[i] = (double)t;
+    }
+    return DEFMM_OK;
+}
+
 defmm_status defmm_destroy(defmm_plan plan) {
     if (!plan) return DEFMM_OK;
     if (plan->host_only) {
@@ -395,6 +422,8 @@ defmm_status defmm_destroy(defmm_plan plan) {
         return DEFMM_OK;
     }
     cudaError_t e = cudaDeviceSynchronize();
+    for (int i = 0; i <= kNumPhases; ++i)
+        if (plan->events[i]) cudaEventDestroy(plan->events[i]);
     plan->wf.release();
     plan->wd.release();
     cudaFree(plan->arena);

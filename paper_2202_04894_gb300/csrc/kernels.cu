@@ -79,19 +79,21 @@ __global__ void k_scatter(const C* __restrict__ ps, C* __restrict__ p, const int
 
 // ------------------------------------------------------------------ P2P
 // Kernel value G(x, y) for a difference d, zero when |d|^2 <= eps2 (Sec. 5.3).
+// Single precision: 1/r from rsqrt, the phase kappa r / (2 pi) reduced exactly
+// to [-1/2, 1/2] turns (round-to-nearest by adding and subtracting 1.5 * 2^23),
+// then the hardware sine and cosine on [-pi, pi].
 __device__ __forceinline__ float2 helmholtz(float dx, float dy, float dz, float kap2pi, float eps2) {
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     float rinv = rsqrtf(r2);
-    float r = r2 * rinv;
-    // exp(i kappa r) with the phase reduced exactly to [-1/2, 1/2] turns
+    rinv = r2 > eps2 ? rinv : 0.f;      // coincident points contribute nothing
+    const float r = r2 * rinv;
     float t = r * kap2pi;
-    t -= rintf(t);
+    const float rt = (t + 12582912.f) - 12582912.f;
+    t -= rt;
     float s, c;
     __sincosf(6.28318530717958647692f * t, &s, &c);
-    float g = rinv * (float)kInv4Pi;
-    float2 out = make_float2(c * g, s * g);
-    if (!(r2 > eps2)) out = make_float2(0.f, 0.f);
-    return out;
+    const float g = rinv * (float)kInv4Pi;
+    return make_float2(c * g, s * g);
 }
 __device__ __forceinline__ double2 helmholtz(double dx, double dy, double dz, double kappa, double eps2) {
     double r2 = dx * dx + dy * dy + dz * dz;
@@ -104,11 +106,28 @@ __device__ __forceinline__ double2 helmholtz(double dx, double dy, double dz, do
     return out;
 }
 
+// Coordinates relative to the target leaf centre are kept as unevaluated sums
+// hi + lo of two values of type T (lo = 0 in double precision), so that the
+// difference of two nearby points is accurate to the precision of the
+// difference itself, not of the coordinates: random clouds hold pairs far
+// closer than the mean spacing, whose 1/r dominates the near field.
+template <typename T> struct Split {
+    T hi, lo;
+};
+template <typename T> __device__ __forceinline__ Split<T> split(double d) {
+    Split<T> o;
+    o.hi = (T)d;
+    o.lo = sizeof(T) == 4 ? (T)(d - (double)o.hi) : (T)0;
+    return o;
+}
+
 template <typename T, int RB>
 __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>::type* __restrict__ qs,
                                              typename Cplx<T>::type* __restrict__ ps, int R, int rb0) {
     using C = typename Cplx<T>::type;
+    constexpr bool kSplit = sizeof(T) == 4;
     __shared__ T sx[128], sy[128], sz[128];
+    __shared__ T lx[kSplit ? 128 : 1], ly[kSplit ? 128 : 1], lz[kSplit ? 128 : 1];
     __shared__ C sq[RB][128];
     __shared__ C red[4][64][RB];
     const int li = blockIdx.x;
@@ -120,17 +139,19 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
     const double cz = c.ct_corner[3 * cell + 2] + 0.5 * side;
     const int nr = min(RB, R - rb0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const T kpar = sizeof(T) == 4 ? (T)(c.kappa * kInv2Pi) : (T)c.kappa;
+    const T kpar = kSplit ? (T)(c.kappa * kInv2Pi) : (T)c.kappa;
     const T eps2 = (T)(c.eps_self * c.eps_self);
     const int r0 = c.p2p_off[li], r1 = c.p2p_off[li + 1];
     for (int t0 = tb; t0 < te; t0 += 64) {
         const int ia = t0 + lane, ib = t0 + lane + 32;
-        T xa = 0, ya = 0, za = 0, xb = 0, yb = 0, zb = 0;
+        Split<T> xa{0, 0}, ya{0, 0}, za{0, 0}, xb{0, 0}, yb{0, 0}, zb{0, 0};
         if (ia < te) {
-            xa = (T)(c.Xs[3 * (int64_t)ia] - cx); ya = (T)(c.Xs[3 * (int64_t)ia + 1] - cy); za = (T)(c.Xs[3 * (int64_t)ia + 2] - cz);
+            xa = split<T>(c.Xs[3 * (int64_t)ia] - cx); ya = split<T>(c.Xs[3 * (int64_t)ia + 1] - cy);
+            za = split<T>(c.Xs[3 * (int64_t)ia + 2] - cz);
         }
         if (ib < te) {
-            xb = (T)(c.Xs[3 * (int64_t)ib] - cx); yb = (T)(c.Xs[3 * (int64_t)ib + 1] - cy); zb = (T)(c.Xs[3 * (int64_t)ib + 2] - cz);
+            xb = split<T>(c.Xs[3 * (int64_t)ib] - cx); yb = split<T>(c.Xs[3 * (int64_t)ib + 1] - cy);
+            zb = split<T>(c.Xs[3 * (int64_t)ib + 2] - cz);
         }
         C acca[RB], accb[RB];
 #pragma unroll
@@ -142,17 +163,25 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
                 __syncthreads();
                 if (threadIdx.x < ns) {
                     const int64_t j = s0 + threadIdx.x;
-                    sx[threadIdx.x] = (T)(c.Ys[3 * j] - cx);
-                    sy[threadIdx.x] = (T)(c.Ys[3 * j + 1] - cy);
-                    sz[threadIdx.x] = (T)(c.Ys[3 * j + 2] - cz);
+                    const Split<T> ux = split<T>(c.Ys[3 * j] - cx), uy = split<T>(c.Ys[3 * j + 1] - cy),
+                                   uz = split<T>(c.Ys[3 * j + 2] - cz);
+                    sx[threadIdx.x] = ux.hi; sy[threadIdx.x] = uy.hi; sz[threadIdx.x] = uz.hi;
+                    if (kSplit) { lx[threadIdx.x] = ux.lo; ly[threadIdx.x] = uy.lo; lz[threadIdx.x] = uz.lo; }
 #pragma unroll
                     for (int r = 0; r < RB; ++r)
                         sq[r][threadIdx.x] = r < nr ? qs[(int64_t)(rb0 + r) * c.ny + j] : czero<C>();
                 }
                 __syncthreads();
                 for (int k = warp; k < ns; k += 4) {
-                    const C ga = helmholtz(xa - sx[k], ya - sy[k], za - sz[k], kpar, eps2);
-                    const C gb = helmholtz(xb - sx[k], yb - sy[k], zb - sz[k], kpar, eps2);
+                    T dxa = xa.hi - sx[k], dya = ya.hi - sy[k], dza = za.hi - sz[k];
+                    T dxb = xb.hi - sx[k], dyb = yb.hi - sy[k], dzb = zb.hi - sz[k];
+                    if (kSplit) {
+                        const T ex = lx[k], ey = ly[k], ez = lz[k];
+                        dxa += xa.lo - ex; dya += ya.lo - ey; dza += za.lo - ez;
+                        dxb += xb.lo - ex; dyb += yb.lo - ey; dzb += zb.lo - ez;
+                    }
+                    const C ga = helmholtz(dxa, dya, dza, kpar, eps2);
+                    const C gb = helmholtz(dxb, dyb, dzb, kpar, eps2);
 #pragma unroll
                     for (int r = 0; r < RB; ++r) {
                         const C qv = sq[r][k];
@@ -671,11 +700,21 @@ template <typename T>
 cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w,
                          const LevelList* m2m, int n_m2m_levels, const LevelList* l2l,
                          const int32_t* const* l2l_par, int n_l2l_levels, const void* q, void* p,
-                         cudaStream_t stream, int* launches) {
+                         cudaStream_t stream, int* launches, cudaEvent_t* phase_events) {
     using C = typename Cplx<T>::type;
     const int R = w.R;
     int nl = 0;
+    int phase = 0;
     cudaError_t err;
+    auto mark = [&]() -> cudaError_t {
+        if (!phase_events) return cudaSuccess;
+        return cudaEventRecord(phase_events[phase++], stream);
+    };
+#define DEFMM_MARK()                        \
+    do {                                    \
+        err = mark();                       \
+        if (err != cudaSuccess) return err; \
+    } while (0)
 #define DEFMM_CHECK_LAUNCH()                      \
     do {                                          \
         ++nl;                                     \
@@ -686,9 +725,11 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         }                                         \
     } while (0)
     const int sms = 152 * 8;
+    DEFMM_MARK();
     // gather charges into Morton order
     k_gather<C><<<sms, 256, 0, stream>>>(reinterpret_cast<const C*>(q), w.qs, c.perm_s, c.ny, R);
     DEFMM_CHECK_LAUNCH();
+    DEFMM_MARK();
     // near field (writes every target potential)
     for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
         if (c.n_p2p_leaf == 0) break;
@@ -696,6 +737,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         else k_p2p<T, 4><<<(unsigned)c.n_p2p_leaf, 128, 0, stream>>>(c, w.qs, w.ps, R, rb0);
         DEFMM_CHECK_LAUNCH();
     }
+    DEFMM_MARK();
     // upward pass
     for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
         if (c.n_p2m == 0) break;
@@ -703,17 +745,20 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         else k_p2m<T, 4><<<(unsigned)c.n_p2m, 128, 0, stream>>>(c, t, w.qs, w.M, R, rb0);
         DEFMM_CHECK_LAUNCH();
     }
+    DEFMM_MARK();
     const size_t sm_m2m = 2 * (size_t)c.P3 * sizeof(C);
     for (int l = n_m2m_levels - 1; l >= 0; --l) {
         if (m2m[l].n == 0) continue;
         k_m2m<T><<<(unsigned)m2m[l].n, 128, sm_m2m, stream>>>(c, t, m2m[l].data, w.M, R);
         DEFMM_CHECK_LAUNCH();
     }
+    DEFMM_MARK();
     if (c.n_m2f > 0) {
         const size_t sm = ((size_t)c.P3 + (size_t)c.p * c.p * c.N + (size_t)c.p * c.N * c.N) * sizeof(C);
         k_m2f<T><<<(unsigned)c.n_m2f, 128, sm, stream>>>(c, t, w.M, w.Mhat, R);
         DEFMM_CHECK_LAUNCH();
     }
+    DEFMM_MARK();
     // transfer
     err = cudaMemsetAsync(w.L, 0, (size_t)w.nL * R * c.P3 * sizeof(C), stream);
     if (err != cudaSuccess) return err;
@@ -723,12 +768,14 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         k_m2l<T, 4><<<(unsigned)c.n_m2l_tgt, threads, sm, stream>>>(c, t, w.Mhat, w.L, R);
         DEFMM_CHECK_LAUNCH();
     }
+    DEFMM_MARK();
     // downward pass
     for (int l = 1; l < n_l2l_levels; ++l) {
         if (l2l[l].n == 0) continue;
         k_l2l<T><<<(unsigned)l2l[l].n, 128, sm_m2m, stream>>>(c, t, l2l[l].data, l2l_par[l], w.L, R);
         DEFMM_CHECK_LAUNCH();
     }
+    DEFMM_MARK();
     for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
         if (c.n_l2p == 0) break;
         const int rb = R == 1 ? 1 : 4;
@@ -737,9 +784,12 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         else k_l2p<T, 4><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0);
         DEFMM_CHECK_LAUNCH();
     }
+    DEFMM_MARK();
     k_scatter<C><<<sms, 256, 0, stream>>>(w.ps, reinterpret_cast<C*>(p), c.perm_t, c.nx, R);
     DEFMM_CHECK_LAUNCH();
+    DEFMM_MARK();
 #undef DEFMM_CHECK_LAUNCH
+#undef DEFMM_MARK
     if (launches) *launches = nl;
     return cudaSuccess;
 }
@@ -757,10 +807,10 @@ cudaError_t configure_kernels() {
 
 template cudaError_t launch_apply<float>(const DevCommon&, const DevTyped<float>&, const DevWork<float>&,
                                          const LevelList*, int, const LevelList*, const int32_t* const*, int,
-                                         const void*, void*, cudaStream_t, int*);
+                                         const void*, void*, cudaStream_t, int*, cudaEvent_t*);
 template cudaError_t launch_apply<double>(const DevCommon&, const DevTyped<double>&, const DevWork<double>&,
                                           const LevelList*, int, const LevelList*, const int32_t* const*, int,
-                                          const void*, void*, cudaStream_t, int*);
+                                          const void*, void*, cudaStream_t, int*, cudaEvent_t*);
 template cudaError_t configure_kernels<float>();
 template cudaError_t configure_kernels<double>();
 

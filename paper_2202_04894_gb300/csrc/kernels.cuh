@@ -73,7 +73,9 @@ template <typename T>
 cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w,
                          const LevelList* m2m, int n_m2m_levels, const LevelList* l2l,
                          const int32_t* const* l2l_par, int n_l2l_levels, const void* q, void* p,
-                         cudaStream_t stream, int* launches);
+                         cudaStream_t stream, int* launches, cudaEvent_t* phase_events);
+
+constexpr int kNumPhases = 9;  // gather p2p p2m m2m m2f m2l l2l l2p scatter
 
 // Forms the canonical transfer spectra in float64 (Sec. 2.3 Eq. FourierDiagonal).
 cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,

@@ -21,7 +21,9 @@ _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
            5: "ERR_UNSUPPORTED", 6: "ERR_BUSY"}
 
 EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_apply_host",
-            "defmm_destroy", "defmm_plan_info", "defmm_plan_table", "defmm_last_error"]
+            "defmm_destroy", "defmm_plan_info", "defmm_plan_table", "defmm_profile_enable",
+            "defmm_profile_read", "defmm_last_error"]
+PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 
 
 class Options(ctypes.Structure):
@@ -74,6 +76,11 @@ def lib():
         L.defmm_plan_info.restype = ctypes.c_int
         L.defmm_plan_table.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(i64), i64, ctypes.POINTER(i64)]
         L.defmm_plan_table.restype = ctypes.c_int
+        L.defmm_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.defmm_profile_enable.restype = ctypes.c_int
+        L.defmm_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]
+        L.defmm_profile_read.restype = ctypes.c_int
         L.defmm_last_error.argtypes = []
         L.defmm_last_error.restype = ctypes.c_char_p
         _LIB = L
@@ -159,6 +166,17 @@ class Plan:
         i = Info()
         _check(lib().defmm_plan_info(self._h, ctypes.byref(i)))
         return {name: getattr(i, name) for name, _ in Info._fields_}
+
+    def profile(self, enable: bool = True):
+        """Turns per-phase event timing of later applies on or off."""
+        _check(lib().defmm_profile_enable(self._h, 1 if enable else 0))
+
+    def phase_ms(self) -> dict:
+        """Phase durations (ms) of the last profiled apply (waits for it)."""
+        buf = (ctypes.c_double * len(PHASES))()
+        n = ctypes.c_int()
+        _check(lib().defmm_profile_read(self._h, buf, len(PHASES), ctypes.byref(n)))
+        return {PHASES[i]: buf[i] for i in range(n.value)}
 
     def table(self, name: str) -> np.ndarray:
         n = ctypes.c_int64()
