@@ -112,6 +112,24 @@ defmm_status defmm_apply(defmm_plan plan, const void* q, void* p, int nrhs,
 defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host, int nrhs,
                               defmm_dtype dtype, void* stream);
 
+/* defmm_apply for callers that cannot allocate device memory when they apply
+ * (for example while a stream is captured into a CUDA graph, or when device
+ * memory belongs to a pool another component owns).  The paper has no
+ * counterpart: it is a property of this library's memory management.
+ * The scratch comes from a fixed 64 MiB array linked into the library (held
+ * by every GPU that loads it until exit); the call makes no cudaMalloc or
+ * cudaFree.  Arguments, layouts and results are those of defmm_apply.
+ *  - Plans whose scratch for nrhs exceeds 64 MiB are rejected with
+ *    DEFMM_ERR_UNSUPPORTED (the message gives both sizes).
+ *  - The first call on a device looks the array's address up
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents; the
+ *    call clears what must start at zero.  Calls whose GPU work overlaps race
+ *    on the array: the caller must order them.
+ * Errors: DEFMM_ERR_ARG, DEFMM_ERR_UNSUPPORTED, DEFMM_ERR_CUDA, DEFMM_ERR_BUSY. */
+defmm_status defmm_apply_noalloc(defmm_plan plan, const void* q, void* p, int nrhs,
+                                 defmm_dtype dtype, void* stream);
+
 /* Frees the plan and its device memory (synchronises the device first).       */
 defmm_status defmm_destroy(defmm_plan plan);
 

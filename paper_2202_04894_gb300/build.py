@@ -24,6 +24,7 @@ SOURCES = [
     ("plan.cpp", "g++"),
     ("kernels.cu", "nvcc"),
     ("capi.cu", "nvcc"),
+    ("noalloc.cu", "nvcc"),
 ]
 
 

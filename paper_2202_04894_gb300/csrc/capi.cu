@@ -12,6 +12,7 @@
 #include "defmm.h"
 #include "kernels.cuh"
 #include "plan.h"
+#include "plan_state.h"
 
 namespace defmm {
 template <typename T> cudaError_t configure_kernels();
@@ -36,6 +37,12 @@ defmm_status cuda_fail(cudaError_t e, const char* what) {
     return fail(DEFMM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+}  // namespace
+
+defmm_status defmm::set_error(defmm_status s, const std::string& msg) { return fail(s, msg); }
+
+namespace {
+
 #define CK(call, what)                                     \
     do {                                                   \
         cudaError_t e_ = (call);                           \
@@ -54,40 +61,7 @@ struct Blob {
     template <typename V> size_t add(const std::vector<V>& v) { return add(v.data(), v.size()); }
 };
 
-template <typename T> struct Workspace {
-    int R = 0;
-    typename Cplx<T>::type *qs = nullptr, *ps = nullptr, *M = nullptr, *Mhat = nullptr, *L = nullptr;
-    void* q_stage = nullptr;
-    void* p_stage = nullptr;
-    size_t bytes = 0;
-    void release() {
-        cudaFree(qs); cudaFree(ps); cudaFree(M); cudaFree(Mhat); cudaFree(L);
-        cudaFree(q_stage); cudaFree(p_stage);
-        *this = Workspace();
-    }
-};
-
 }  // namespace
-
-struct defmm_plan_s {
-    HostPlan hp;
-    unsigned char* arena = nullptr;
-    size_t arena_bytes = 0;
-    DevCommon common{};
-    DevTyped<float> tf{};
-    DevTyped<double> td{};
-    std::vector<LevelList> m2m, l2l;
-    std::vector<const int32_t*> l2l_par;
-    Workspace<float> wf;
-    Workspace<double> wd;
-    size_t hbm_budget = 0;
-    int64_t launches = 0;
-    bool host_only = false;
-    bool profiling = false;
-    bool profiled = false;
-    cudaEvent_t events[kNumPhases + 1] = {};
-    std::mutex busy;
-};
 
 namespace {
 

@@ -22,7 +22,7 @@ _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
 
 EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_apply_host",
             "defmm_destroy", "defmm_plan_info", "defmm_plan_table", "defmm_profile_enable",
-            "defmm_profile_read", "defmm_last_error"]
+            "defmm_profile_read", "defmm_apply_noalloc", "defmm_last_error"]
 PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 
 
@@ -68,6 +68,8 @@ def lib():
         L.defmm_plan_create.restype = ctypes.c_int
         L.defmm_apply.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
         L.defmm_apply.restype = ctypes.c_int
+        L.defmm_apply_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+        L.defmm_apply_noalloc.restype = ctypes.c_int
         L.defmm_apply_host.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
         L.defmm_apply_host.restype = ctypes.c_int
         L.defmm_destroy.argtypes = [vp]
