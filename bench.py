@@ -166,6 +166,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="defmm", choices=["defmm", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--n", type=int, default=None, help="point count (same recipe; for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -187,7 +188,7 @@ def main():
     if dist:
         dist.barrier()
     W_ = W.WORKLOADS[args.workload]
-    X, q, kappa, order, leaf, dtype = W.make(args.workload)
+    X, q, kappa, order, leaf, dtype = W.make(args.workload, n=args.n)
     cdt = torch.complex64 if dtype == "c64" else torch.complex128
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()

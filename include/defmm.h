@@ -108,7 +108,8 @@ defmm_status defmm_apply(defmm_plan plan, const void* q, void* p, int nrhs,
 
 /* defmm_apply with host arrays: copies q to the device, applies, copies p back
  * and synchronises the stream before returning.  Page-locked host memory
- * gives asynchronous copies; pageable memory works but is slower.            */
+ * gives asynchronous copies; pageable memory works but is slower.  Returns
+ * DEFMM_ERR_TIMEOUT if a bounded device-side wait of the apply gave up.      */
 defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host, int nrhs,
                               defmm_dtype dtype, void* stream);
 
@@ -147,6 +148,9 @@ typedef struct {
     size_t plan_bytes;                /* device bytes held by the plan tables */
     size_t workspace_bytes;           /* device bytes of the current workspace */
     int64_t launches_per_apply;       /* kernels launched by the last apply (0 before any) */
+    int64_t device_error;             /* 1 if a bounded device-side wait of an apply gave up
+                                         (that apply's results are invalid); this call
+                                         synchronises with the device to read it */
     double d_aabb;                    /* side of the smallest box holding X, Y */
     double cube_side;                 /* side of the octree root */
 } defmm_info;

@@ -87,7 +87,7 @@ defmm_status read_points(const double* P, int64_t n, std::vector<double>& out, b
 template <typename T> size_t workspace_bytes(const HostPlan& hp, int R) {
     size_t c = sizeof(typename Cplx<T>::type);
     return c * R * ((size_t)hp.ny + hp.nx + (size_t)hp.nM() * hp.P3 + hp.m2f_list.size() * (size_t)hp.NFpad +
-                    (size_t)hp.nL() * hp.P3);
+                    (size_t)hp.nL() * hp.P3 + (size_t)hp.p2p_parts);
 }
 
 template <typename T> defmm_status ensure_workspace(defmm_plan_s* pl, Workspace<T>& w, int R, bool host) {
@@ -103,6 +103,7 @@ template <typename T> defmm_status ensure_workspace(defmm_plan_s* pl, Workspace<
         CK(cudaMalloc(&w.M, sizeof(C) * R * (size_t)std::max<int64_t>(1, hp.nM()) * hp.P3), "workspace M");
         CK(cudaMalloc(&w.Mhat, sizeof(C) * R * std::max<size_t>(1, hp.m2f_list.size()) * hp.NFpad), "workspace Mhat");
         CK(cudaMalloc(&w.L, sizeof(C) * R * (size_t)std::max<int64_t>(1, hp.nL()) * hp.P3), "workspace L");
+        CK(cudaMalloc(&w.part, sizeof(C) * R * (size_t)std::max<int64_t>(1, hp.p2p_parts)), "workspace near-field partials");
         w.R = R;
         w.bytes = need;
     }
@@ -134,6 +135,27 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
         o_Ys = b.add(Ys);
     }
     size_t o_pt = b.add(tt.perm), o_ps = hp.same ? o_pt : b.add(ts.perm);
+    // single-precision coordinates as hi + lo pairs relative to the cube centre
+    auto split4 = [&](const std::vector<double>& src, int64_t n, const Tree& tr, size_t& oh, size_t& ol) {
+        std::vector<float4> hi(n), lo(n);
+        const double c0[3] = {hp.corner[0] + hp.side / 2, hp.corner[1] + hp.side / 2, hp.corner[2] + hp.side / 2};
+        for (int64_t i = 0; i < n; ++i) {
+            float h[3], l[3];
+            for (int a = 0; a < 3; ++a) {
+                double d = src[3 * tr.perm[i] + a] - c0[a];
+                h[a] = (float)d;
+                l[a] = (float)(d - (double)h[a]);
+            }
+            hi[i] = make_float4(h[0], h[1], h[2], 0.f);
+            lo[i] = make_float4(l[0], l[1], l[2], 0.f);
+        }
+        oh = b.add(hi);
+        ol = b.add(lo);
+    };
+    size_t o_Xh, o_Xl, o_Yh, o_Yl;
+    split4(X, hp.nx, tt, o_Xh, o_Xl);
+    if (hp.same) { o_Yh = o_Xh; o_Yl = o_Xl; }
+    else split4(Y, hp.ny, ts, o_Yh, o_Yl);
 
     auto cells = [&](const Tree& tr, size_t& ob, size_t& oe, size_t& ol, size_t& oc) {
         std::vector<int32_t> beg(tr.ncell()), end(tr.ncell());
@@ -155,6 +177,8 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     std::vector<double> lside(kNumLevels);
     for (int l = 0; l < kNumLevels; ++l) lside[l] = hp.lv.side(l);
     size_t o_lside = b.add(lside);
+    const int32_t zero_flag[4] = {0, 0, 0, 0};
+    size_t o_err = b.add(zero_flag, 4);
 
     size_t o_mf = b.add(hp.m_first), o_mc = b.add(hp.m_count), o_ms = b.add(hp.m_slot);
     size_t o_lf = b.add(hp.l_first), o_lc = b.add(hp.l_count), o_ls = b.add(hp.l_slot);
@@ -162,7 +186,9 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     size_t o_m2f = b.add(hp.m2f_list);
     size_t o_mt = b.add(hp.m2l_tgt), o_mo = b.add(hp.m2l_off), o_msrc = b.add(hp.m2l_src), o_mspec = b.add(hp.m2l_spec);
     size_t o_p2m = b.add(hp.p2m_cells), o_l2p = b.add(hp.l2p_cells);
-    size_t o_pl = b.add(hp.p2p_leaf), o_po = b.add(hp.p2p_off), o_psb = b.add(hp.p2p_sbeg), o_pse = b.add(hp.p2p_send);
+    size_t o_pul = b.add(hp.p2p_unit_leaf), o_puo = b.add(hp.p2p_unit_off), o_psb = b.add(hp.p2p_sbeg),
+           o_pse = b.add(hp.p2p_send), o_pso = b.add(hp.p2p_soff), o_ppt = b.add(hp.p2p_part);
+    size_t o_pl = b.add(hp.p2p_leaf), o_plo = b.add(hp.p2p_leaf_off), o_plu = b.add(hp.p2p_leaf_units);
     std::vector<size_t> o_m2m(hp.m2m_lvl.size()), o_l2l(hp.l2l_lvl.size()), o_l2lp(hp.l2l_par.size());
     for (size_t l = 0; l < hp.m2m_lvl.size(); ++l) o_m2m[l] = b.add(hp.m2m_lvl[l]);
     for (size_t l = 0; l < hp.l2l_lvl.size(); ++l) { o_l2l[l] = b.add(hp.l2l_lvl[l]); o_l2lp[l] = b.add(hp.l2l_par[l]); }
@@ -196,11 +222,14 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.nx = hp.nx; c.ny = hp.ny; c.kappa = hp.kappa; c.eps_self = hp.eps_self;
     c.Xs = (const double*)P(o_Xs); c.Ys = (const double*)P(o_Ys);
     c.perm_t = (const int64_t*)P(o_pt); c.perm_s = (const int64_t*)P(o_ps);
+    c.Xh = (const float4*)P(o_Xh); c.Xl = (const float4*)P(o_Xl);
+    c.Yh = (const float4*)P(o_Yh); c.Yl = (const float4*)P(o_Yl);
     c.ct_beg = (const int32_t*)P(o_ctb); c.ct_end = (const int32_t*)P(o_cte);
     c.ct_level = (const int32_t*)P(o_ctl); c.ct_corner = (const double*)P(o_ctc);
     c.cs_beg = (const int32_t*)P(o_csb); c.cs_end = (const int32_t*)P(o_cse);
     c.cs_level = (const int32_t*)P(o_csl); c.cs_corner = (const double*)P(o_csc);
     c.level_side = (const double*)P(o_lside);
+    c.err_flag = (int*)P(o_err);
     c.m_first = (const int32_t*)P(o_mf); c.m_count = (const int32_t*)P(o_mc); c.m_slot = (const int32_t*)P(o_ms);
     c.l_first = (const int32_t*)P(o_lf); c.l_count = (const int32_t*)P(o_lc); c.l_slot = (const int32_t*)P(o_ls);
     c.slot_u = (const double*)P(o_su);
@@ -210,8 +239,12 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.n_m2l_tgt = (int64_t)hp.m2l_tgt.size();
     c.p2m_cells = (const int32_t*)P(o_p2m); c.n_p2m = (int64_t)hp.p2m_cells.size();
     c.l2p_cells = (const int32_t*)P(o_l2p); c.n_l2p = (int64_t)hp.l2p_cells.size();
-    c.p2p_leaf = (const int32_t*)P(o_pl); c.p2p_off = (const int32_t*)P(o_po);
+    c.p2p_unit_leaf = (const int32_t*)P(o_pul); c.p2p_unit_off = (const int32_t*)P(o_puo);
     c.p2p_sbeg = (const int32_t*)P(o_psb); c.p2p_send = (const int32_t*)P(o_pse);
+    c.p2p_soff = (const int32_t*)P(o_pso); c.p2p_part = (const int32_t*)P(o_ppt);
+    c.n_p2p_units = (int64_t)hp.p2p_unit_leaf.size(); c.p2p_parts = hp.p2p_parts;
+    c.p2p_leaf = (const int32_t*)P(o_pl); c.p2p_leaf_off = (const int32_t*)P(o_plo);
+    c.p2p_leaf_units = (const int32_t*)P(o_plu);
     c.n_p2p_leaf = (int64_t)hp.p2p_leaf.size();
 
     pl->m2m.resize(hp.m2m_lvl.size());
@@ -250,6 +283,7 @@ template <typename T> defmm_status apply_impl(defmm_plan_s* pl, Workspace<T>& w,
     if (s != DEFMM_OK) return s;
     DevWork<T> dw;
     dw.R = nrhs; dw.qs = w.qs; dw.ps = w.ps; dw.M = w.M; dw.Mhat = w.Mhat; dw.L = w.L; dw.nL = pl->hp.nL();
+    dw.part = w.part;
     const DevTyped<T>& typed = typed_tables(pl, (T*)nullptr);
     int launches = 0;
     cudaError_t e = launch_apply<T>(pl->common, typed, dw, pl->m2m.data(), (int)pl->m2m.size(), pl->l2l.data(),
@@ -364,6 +398,9 @@ defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host,
     if (s != DEFMM_OK) return s;
     CK(cudaMemcpyAsync(p_host, pd, pb, cudaMemcpyDeviceToHost, st), "copy p to host");
     CK(cudaStreamSynchronize(st), "apply");
+    int flag = 0;
+    CK(cudaMemcpy(&flag, plan->common.err_flag, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+    if (flag) return fail(DEFMM_ERR_TIMEOUT, "a bounded device wait gave up (results invalid)");
     return DEFMM_OK;
 }
 
@@ -422,6 +459,11 @@ defmm_status defmm_plan_info(defmm_plan plan, defmm_info* out) {
     out->plan_bytes = plan->arena_bytes;
     out->workspace_bytes = plan->wf.bytes + plan->wd.bytes;
     out->launches_per_apply = plan->launches;
+    if (!plan->host_only) {
+        int flag = 0;
+        CK(cudaMemcpy(&flag, plan->common.err_flag, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+        out->device_error = flag;
+    }
     out->d_aabb = hp.d_aabb;
     out->cube_side = hp.side;
     return DEFMM_OK;

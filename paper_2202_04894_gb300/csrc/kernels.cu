@@ -17,8 +17,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels.cuh"
+#include "plan.h"
 #include "symmetry.h"
 
 namespace defmm {
@@ -121,18 +123,22 @@ template <typename T> __device__ __forceinline__ Split<T> split(double d) {
     return o;
 }
 
+// Near field in the arithmetic type T (used for float64): one block per work
+// unit (a target leaf and at most kP2PUnitSources of its near sources); the
+// unit's partial sums go to part[] and are reduced per target by k_p2p_reduce.
 template <typename T, int RB>
 __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>::type* __restrict__ qs,
-                                             typename Cplx<T>::type* __restrict__ ps, int R, int rb0) {
+                                             typename Cplx<T>::type* __restrict__ part, int R, int rb0) {
     using C = typename Cplx<T>::type;
     constexpr bool kSplit = sizeof(T) == 4;
     __shared__ T sx[128], sy[128], sz[128];
     __shared__ T lx[kSplit ? 128 : 1], ly[kSplit ? 128 : 1], lz[kSplit ? 128 : 1];
     __shared__ C sq[RB][128];
     __shared__ C red[4][64][RB];
-    const int li = blockIdx.x;
-    const int cell = c.p2p_leaf[li];
+    const int u = blockIdx.x;
+    const int cell = c.p2p_leaf[c.p2p_unit_leaf[u]];
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
+    const int64_t pbase = c.p2p_part[u];
     const double side = c.level_side[c.ct_level[cell]];
     const double cx = c.ct_corner[3 * cell] + 0.5 * side;
     const double cy = c.ct_corner[3 * cell + 1] + 0.5 * side;
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const T kpar = kSplit ? (T)(c.kappa * kInv2Pi) : (T)c.kappa;
     const T eps2 = (T)(c.eps_self * c.eps_self);
-    const int r0 = c.p2p_off[li], r1 = c.p2p_off[li + 1];
+    const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];
     for (int t0 = tb; t0 < te; t0 += 64) {
         const int ia = t0 + lane, ib = t0 + lane + 32;
         Split<T> xa{0, 0}, ya{0, 0}, za{0, 0}, xb{0, 0}, yb{0, 0}, zb{0, 0};
@@ -202,12 +208,161 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
                     s = cadd(s, red[1][threadIdx.x][r]);
                     s = cadd(s, red[2][threadIdx.x][r]);
                     s = cadd(s, red[3][threadIdx.x][r]);
-                    ps[(int64_t)(rb0 + r) * c.nx + i] = s;
+                    part[(int64_t)(rb0 + r) * c.p2p_parts + pbase + (i - tb)] = s;
                 }
             }
         }
         __syncthreads();
     }
+}
+
+// Single-precision near field.  One block per target leaf (heaviest first);
+// the leaf's n_t targets are spread over the 128 threads as target x
+// source-split (splits = 128 / n_t), so small leaves do not leave lanes idle.
+// The leaf's source ranges are read as one concatenated sequence cut into
+// full tiles of 128 (a thread finds its source by binary search in the
+// ranges' prefix offsets), and the next tile is loaded into registers while
+// the current one is consumed.  Coordinates are hi + lo float pairs relative
+// to the cube centre; charges are pre-scaled by 1/(4 pi) when staged; partial
+// sums are reduced over the splits in a fixed order.
+constexpr int kP2PRanges = kP2PUnitRanges;   // ranges of a work unit, held in shared memory
+
+template <int RB>
+__global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __restrict__ qs,
+                                                 float2* __restrict__ part, int R, int rb0) {
+    __shared__ float4 sa[128];   // hi x, y, z and Re q / (4 pi)   (RB == 1)
+    __shared__ float4 sb[128];   // lo x, y, z and Im q / (4 pi)
+    __shared__ float2 sq[RB][128];
+    __shared__ float2 red[RB][128];
+    __shared__ int rbeg[kP2PRanges], roff[kP2PRanges + 1];
+    const int u = blockIdx.x;
+    const int cell = c.p2p_leaf[c.p2p_unit_leaf[u]];
+    const int tb = c.ct_beg[cell], te = c.ct_end[cell];
+    const int64_t pbase = c.p2p_part[u];
+    const int nr = min(RB, R - rb0);
+    const float kap2pi = (float)(c.kappa * kInv2Pi);
+    const float eps2 = (float)(c.eps_self * c.eps_self);
+    const float inv4pi = (float)kInv4Pi;
+    const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];
+    for (int t0 = tb; t0 < te; t0 += 128) {
+        const int nt = min(128, te - t0);
+        const int splits = 128 / nt;
+        const int ti = threadIdx.x % nt, sj = threadIdx.x / nt;
+        const bool active = sj < splits;
+        float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh;
+        if (active) { xh = c.Xh[t0 + ti]; xl = c.Xl[t0 + ti]; }
+        float2 acc[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) acc[r] = make_float2(0.f, 0.f);
+        for (int g0 = r0; g0 < r1; g0 += kP2PRanges) {          // batches of ranges
+            const int ng = min(kP2PRanges, r1 - g0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < ng; k += blockDim.x) {
+                rbeg[k] = c.p2p_sbeg[g0 + k];
+                roff[k] = c.p2p_soff[g0 + k] - c.p2p_soff[g0];
+            }
+            if (threadIdx.x == 0) roff[ng] = c.p2p_soff[g0 + ng - 1] - c.p2p_soff[g0] + c.p2p_send[g0 + ng - 1] - c.p2p_sbeg[g0 + ng - 1];
+            __syncthreads();
+            const int total = roff[ng];
+            // source of concatenated position f: binary search in roff
+            auto source_of = [&](int f) {
+                int lo = 0, hi = ng - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (roff[mid] <= f) lo = mid; else hi = mid - 1;
+                }
+                return rbeg[lo] + (f - roff[lo]);
+            };
+            float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+            float2 nq[RB];
+            auto fetch = [&](int f0) {
+                if (f0 + (int)threadIdx.x < total) {
+                    const int64_t j = source_of(f0 + threadIdx.x);
+                    na = c.Yh[j];
+                    nb = c.Yl[j];
+#pragma unroll
+                    for (int r = 0; r < RB; ++r)
+                        nq[r] = r < nr ? qs[(int64_t)(rb0 + r) * c.ny + j] : make_float2(0.f, 0.f);
+                }
+            };
+            fetch(0);
+            for (int f0 = 0; f0 < total; f0 += 128) {
+                const int ns = min(128, total - f0);
+                __syncthreads();                 // previous tile consumed
+                if (threadIdx.x < ns) {
+                    float4 a = na, b = nb;
+                    if (RB == 1) {
+                        a.w = nq[0].x * inv4pi;
+                        b.w = nq[0].y * inv4pi;
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < RB; ++r) sq[r][threadIdx.x] = make_float2(nq[r].x * inv4pi, nq[r].y * inv4pi);
+                    }
+                    sa[threadIdx.x] = a;
+                    sb[threadIdx.x] = b;
+                }
+                __syncthreads();
+                if (f0 + 128 < total) fetch(f0 + 128);   // in flight during the compute below
+                if (active) {
+                    for (int k = sj; k < ns; k += splits) {
+                        const float4 a = sa[k], b = sb[k];
+                        const float dx = (xh.x - a.x) + (xl.x - b.x);
+                        const float dy = (xh.y - a.y) + (xl.y - b.y);
+                        const float dz = (xh.z - a.z) + (xl.z - b.z);
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        float rinv = rsqrtf(r2);
+                        rinv = r2 > eps2 ? rinv : 0.f;
+                        float tt = r2 * rinv * kap2pi;
+                        tt -= __fadd_rn(__fadd_rn(tt, 12582912.f), -12582912.f);
+                        float sn, cs;
+                        __sincosf(6.28318530717958647692f * tt, &sn, &cs);
+                        const float gr = cs * rinv, gi = sn * rinv;
+                        if (RB == 1) {
+                            acc[0].x = fmaf(gr, a.w, fmaf(-gi, b.w, acc[0].x));
+                            acc[0].y = fmaf(gr, b.w, fmaf(gi, a.w, acc[0].y));
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < RB; ++r) {
+                                const float2 q = sq[r][k];
+                                acc[r].x = fmaf(gr, q.x, fmaf(-gi, q.y, acc[r].x));
+                                acc[r].y = fmaf(gr, q.y, fmaf(gi, q.x, acc[r].y));
+                            }
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r) red[r][threadIdx.x] = acc[r];
+        __syncthreads();
+        if (active && sj == 0) {
+            for (int r = 0; r < nr; ++r) {
+                float2 s = red[r][ti];
+                for (int q = 1; q < splits; ++q) {
+                    s.x += red[r][ti + q * nt].x;
+                    s.y += red[r][ti + q * nt].y;
+                }
+                part[(int64_t)(rb0 + r) * c.p2p_parts + pbase + (t0 + ti - tb)] = s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Sums each target's partial near-field sums over its leaf's work units, in
+// the units' source order, into the potentials.
+template <typename C>
+__global__ void __launch_bounds__(128) k_p2p_reduce(DevCommon c, const C* __restrict__ part, C* __restrict__ ps, int R) {
+    const int li = blockIdx.x;
+    const int cell = c.p2p_leaf[li];
+    const int tb = c.ct_beg[cell], te = c.ct_end[cell];
+    const int u0 = c.p2p_leaf_off[li], u1 = c.p2p_leaf_off[li + 1];
+    for (int r = 0; r < R; ++r)
+        for (int j = tb + threadIdx.x; j < te; j += blockDim.x) {
+            C s = czero<C>();
+            for (int k = u0; k < u1; ++k) s = cadd(s, part[(int64_t)r * c.p2p_parts + c.p2p_part[c.p2p_leaf_units[k]] + (j - tb)]);
+            ps[(int64_t)r * c.nx + j] = s;
+        }
 }
 
 // ------------------------------------------------------------------ P2M
@@ -396,59 +551,151 @@ __global__ void __launch_bounds__(128) k_m2f(DevCommon c, DevTyped<T> t, const t
 }
 
 // ------------------------------------------------------------------ M2L (+F2L)
-// One block per target expansion with a non-empty list.  Thread i owns the
-// Fourier samples xi = i + v*blockDim (v < VPT); for each source it reads the
-// canonical spectrum at the symmetry-permuted index xi' (xi'_{sigma(a)} =
-// s_a xi_a mod N) and accumulates spectrum(xi') * Mhat_s(xi).  The inverse DFT
-// and the crop to the p^3 grid follow in shared memory.
+// Asynchronous bulk copies (TMA, cp.async.bulk) into shared memory, completed
+// on mbarriers.  Every wait is bounded; a wait that gives up raises the plan's
+// error flag and the block stops.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+constexpr int kMaxSpin = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (int it = 0; it < kMaxSpin; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+constexpr int kM2LMaxStages = 3;  // ring depth (runtime S <= this)
+constexpr size_t kSmemLimit = 227 * 1024 - 2048;   // dynamic shared memory per block, with room for static
+
+// One block per target expansion with a non-empty list.  The list is cut into
+// chunks of P pairs; a chunk's canonical spectra and source Fourier multipoles
+// (one contiguous NFpad block each) are brought into a ring of S
+// shared-memory stages by TMA bulk copies issued by thread 0, while the block
+// computes an earlier chunk.  Thread i owns the Fourier samples
+// xi = i + v*blockDim (v < VPT) and accumulates, for each pair,
+// spectrum(xi') * Mhat(xi) with xi'_{sigma(a)} = s_a xi_a mod N: the symmetry
+// of the pair is applied as a gather from shared memory.  The inverse DFT and
+// the crop to the p^3 grid follow in shared memory.
 template <typename T, int VPT>
 __global__ void __launch_bounds__(1024) k_m2l(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
-                                              typename Cplx<T>::type* __restrict__ L, int R) {
+                                              typename Cplx<T>::type* __restrict__ L, int R, int P, int S) {
     using C = typename Cplx<T>::type;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int p = c.p, N = c.N, NF = c.NF, NFpad = c.NFpad, P3 = c.P3;
-    C* Lh = reinterpret_cast<C*>(smem_raw);   // NF
-    C* T1 = Lh + NF;                          // [az][xi_y][xi_x]  p*N*N
-    C* T2 = T1 + p * N * N;                   // [az][ay][xi_x]    p*p*N
+    const uint32_t blk_bytes = (uint32_t)(NFpad * sizeof(C));
+    // ring of stages: stage s holds P spectra then P Fourier multipoles
+    C* ring = reinterpret_cast<C*>(smem_raw);
+    const int stage_elems = 2 * P * NFpad;
+    // F2L work arrays reuse the ring once every copy has landed
+    C* Lh = ring;                              // NF
+    C* T1 = Lh + NF;                           // [az][xi_y][xi_x]  p*N*N
+    C* T2 = T1 + p * N * N;                    // [az][ay][xi_x]    p*p*N
+    __shared__ __align__(8) uint64_t bars[kM2LMaxStages];
     __shared__ C tws[16];
+    __shared__ int stride[6][3];               // N^sigma(a) for each axis permutation
     const int i = blockIdx.x;
     const int te = c.m2l_tgt[i];
     const int j0 = c.m2l_off[i], j1 = c.m2l_off[i + 1];
+    const int npairs = j1 - j0;
+    const int nchunks = (npairs + P - 1) / P;
     if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
-    int xi[VPT], cx[VPT], cy[VPT], cz[VPT];
+    if (threadIdx.x < 18) {
+        const int q = kPermDev[threadIdx.x / 3][threadIdx.x % 3];
+        stride[threadIdx.x / 3][threadIdx.x % 3] = q == 0 ? 1 : (q == 1 ? N : N * N);
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
+    }
+    int xi[VPT], cp[VPT][3], cn[VPT][3];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
         xi[v] = threadIdx.x + v * blockDim.x;
         const int f = xi[v] < NF ? xi[v] : 0;
-        cx[v] = f % N; cy[v] = (f / N) % N; cz[v] = f / (N * N);
+        cp[v][0] = f % N; cp[v][1] = (f / N) % N; cp[v][2] = f / (N * N);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) cn[v][a] = cp[v][a] == 0 ? 0 : N - cp[v][a];
     }
+    __syncthreads();
+    uint32_t use = 0;  // chunks consumed so far (all right-hand sides): stage = use % S, parity = (use / S) & 1
     const T scale = (T)1 / (T)NF;
+    // producer: copies of chunk ch (right-hand side r) into stage st
+    auto issue = [&](int ch, int r, int st) {
+        const int q0 = j0 + ch * P;
+        const int nq = min(P, j1 - q0);
+        C* base = ring + (size_t)st * stage_elems;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bars[st], 2u * nq * blk_bytes);
+        for (int q = 0; q < nq; ++q) {
+            const int sid = c.m2l_spec[q0 + q] >> 6;
+            const int src = c.m2l_src[q0 + q];
+            tma_bulk_load(base + (size_t)q * NFpad, t.spec + (int64_t)sid * NFpad, blk_bytes, &bars[st]);
+            tma_bulk_load(base + (size_t)(P + q) * NFpad, Mhat + ((int64_t)src * R + r) * NFpad, blk_bytes, &bars[st]);
+        }
+    };
     for (int r = 0; r < R; ++r) {
+        if (threadIdx.x == 0)
+            for (int k = 0; k < S - 1 && k < nchunks; ++k) issue(k, r, (use + k) % S);
         C acc[VPT];
 #pragma unroll
         for (int v = 0; v < VPT; ++v) acc[v] = czero<C>();
-        for (int j = j0; j < j1; ++j) {
-            const int src = c.m2l_src[j];
-            const int sc = c.m2l_spec[j];
-            const int sid = sc >> 6, code = sc & 63, pid = code >> 3;
-            const int st[3] = {kPermDev[pid][0] == 0 ? 1 : (kPermDev[pid][0] == 1 ? N : N * N),
-                               kPermDev[pid][1] == 0 ? 1 : (kPermDev[pid][1] == 1 ? N : N * N),
-                               kPermDev[pid][2] == 0 ? 1 : (kPermDev[pid][2] == 1 ? N : N * N)};
-            const bool n0 = code & 1, n1 = code & 2, n2 = code & 4;
-            const C* __restrict__ g = t.spec + (int64_t)sid * NFpad;
-            const C* __restrict__ mh = Mhat + ((int64_t)src * R + r) * NFpad;
+        for (int ch = 0; ch < nchunks; ++ch, ++use) {
+            const int st = use % S;
+            const bool ok = mbar_wait(&bars[st], (use / S) & 1);
+            // one barrier per chunk: every thread has finished the previous chunk
+            // (so its stage may be refilled) and the decision to stop is uniform
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    atomicExch(c.err_flag, 1);
+                    // give copies already issued a bounded chance to land before the block exits
+                    const int last = min(nchunks - 1, ch + S - 2);
+                    for (int k = ch; k <= last; ++k)
+                        (void)mbar_wait(&bars[(use + k - ch) % S], ((use + k - ch) / S) & 1);
+                }
+                return;
+            }
+            if (threadIdx.x == 0 && ch + S - 1 < nchunks)
+                issue(ch + S - 1, r, (use + S - 1) % S);
+            const C* sg = ring + (size_t)st * stage_elems;
+            const C* sm = sg + (size_t)P * NFpad;
+            const int q0 = j0 + ch * P;
+            const int nq = min(P, j1 - q0);
+            for (int q = 0; q < nq; ++q) {
+                const int code = c.m2l_spec[q0 + q] & 63;
+                const int pid = code >> 3;
+                const int s0 = stride[pid][0], s1 = stride[pid][1], s2 = stride[pid][2];
+                const C* g = sg + (size_t)q * NFpad;
+                const C* m = sm + (size_t)q * NFpad;
 #pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                if (xi[v] < NF) {
-                    const int x0 = n0 ? (N - cx[v]) % N : cx[v];
-                    const int x1 = n1 ? (N - cy[v]) % N : cy[v];
-                    const int x2 = n2 ? (N - cz[v]) % N : cz[v];
-                    const int idx = x0 * st[0] + x1 * st[1] + x2 * st[2];
-                    cfma(acc[v], __ldg(&g[idx]), __ldg(&mh[xi[v]]));
+                for (int v = 0; v < VPT; ++v) {
+                    if (xi[v] < NF) {
+                        const int idx = ((code & 1) ? cn[v][0] : cp[v][0]) * s0 +
+                                        ((code & 2) ? cn[v][1] : cp[v][1]) * s1 +
+                                        ((code & 4) ? cn[v][2] : cp[v][2]) * s2;
+                        cfma(acc[v], g[idx], m[xi[v]]);
+                    }
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();   // every chunk read: the ring may now hold the F2L arrays
 #pragma unroll
         for (int v = 0; v < VPT; ++v)
             if (xi[v] < NF) Lh[xi[v]] = acc[v];
@@ -473,7 +720,24 @@ __global__ void __launch_bounds__(1024) k_m2l(DevCommon c, DevTyped<T> t, const 
             for (int k = 0; k < N; ++k) cfma(s, T2[rest * N + k], tws[(k * ax) % N]);
             L[((int64_t)te * R + r) * P3 + a] = cscale(s, scale);
         }
+        __syncthreads();   // F2L arrays alias the ring: done before the next prologue
     }
+}
+
+// Ring depth S, pairs per stage P and the dynamic shared memory of k_m2l:
+// three stages of up to 24 KB when they fit, else two stages of one pair.
+template <typename T> __host__ void m2l_shape(const DevCommon& c, int* P, int* S, size_t* smem) {
+    const size_t blk = (size_t)c.NFpad * sizeof(typename Cplx<T>::type);
+    int pp = (int)(24576 / (2 * blk));
+    if (pp < 1) pp = 1;
+    if (pp > 8) pp = 8;
+    int ss = kM2LMaxStages;
+    while (ss > 2 && (size_t)ss * 2 * pp * blk > kSmemLimit) --ss;
+    const size_t ring = (size_t)ss * 2 * pp * blk;
+    const size_t f2l = ((size_t)c.NF + (size_t)c.p * c.N * c.N + (size_t)c.p * c.p * c.N) * sizeof(typename Cplx<T>::type);
+    *P = pp;
+    *S = ss;
+    *smem = ring > f2l ? ring : f2l;
 }
 
 // ------------------------------------------------------------------ L2L
@@ -730,11 +994,20 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     k_gather<C><<<sms, 256, 0, stream>>>(reinterpret_cast<const C*>(q), w.qs, c.perm_s, c.ny, R);
     DEFMM_CHECK_LAUNCH();
     DEFMM_MARK();
-    // near field (writes every target potential)
+    // near field: work units write partial sums, reduced per target in fixed order
     for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
-        if (c.n_p2p_leaf == 0) break;
-        if (R == 1) k_p2p<T, 1><<<(unsigned)c.n_p2p_leaf, 128, 0, stream>>>(c, w.qs, w.ps, R, rb0);
-        else k_p2p<T, 4><<<(unsigned)c.n_p2p_leaf, 128, 0, stream>>>(c, w.qs, w.ps, R, rb0);
+        if (c.n_p2p_units == 0) break;
+        if constexpr (std::is_same<T, float>::value) {
+            if (R == 1) k_p2p_f32<1><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+            else k_p2p_f32<4><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+        } else {
+            if (R == 1) k_p2p<T, 1><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+            else k_p2p<T, 4><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+        }
+        DEFMM_CHECK_LAUNCH();
+    }
+    if (c.n_p2p_leaf > 0) {
+        k_p2p_reduce<C><<<(unsigned)c.n_p2p_leaf, 128, 0, stream>>>(c, w.part, w.ps, R);
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -763,9 +1036,17 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     err = cudaMemsetAsync(w.L, 0, (size_t)w.nL * R * c.P3 * sizeof(C), stream);
     if (err != cudaSuccess) return err;
     if (c.n_m2l_tgt > 0) {
-        const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
-        const size_t sm = ((size_t)c.NF + (size_t)c.p * c.N * c.N + (size_t)c.p * c.p * c.N) * sizeof(C);
-        k_m2l<T, 4><<<(unsigned)c.n_m2l_tgt, threads, sm, stream>>>(c, t, w.Mhat, w.L, R);
+        int P, S;
+        size_t sm;
+        m2l_shape<T>(c, &P, &S, &sm);
+        if (sm > kSmemLimit) return cudaErrorInvalidConfiguration;
+        if (c.NF <= 2048) {  // two samples per thread, at most 1024 threads
+            const int threads = ((c.NF + 1) / 2 + 31) / 32 * 32;
+            k_m2l<T, 2><<<(unsigned)c.n_m2l_tgt, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, P, S);
+        } else {
+            const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
+            k_m2l<T, 4><<<(unsigned)c.n_m2l_tgt, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, P, S);
+        }
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -798,8 +1079,9 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
 // than 48 KB (large orders / FFT lengths, float64).
 template <typename T>
 cudaError_t configure_kernels() {
-    const int big = 200 * 1024;
+    const int big = (int)kSmemLimit;
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_m2l<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     return cudaSuccess;

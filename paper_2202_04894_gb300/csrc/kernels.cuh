@@ -19,6 +19,10 @@ struct DevCommon {
     double kappa, eps_self;
     const double* Xs;        // nx*3 targets, Morton order
     const double* Ys;        // ny*3 sources, Morton order
+    const float4* Xh;        // targets minus the cube centre, float hi part (w unused)
+    const float4* Xl;        // the float remainder (x - c) - hi
+    const float4* Yh;        // same for sources
+    const float4* Yl;
     const int64_t* perm_t;   // sorted -> input
     const int64_t* perm_s;
     // target / source cells
@@ -36,7 +40,12 @@ struct DevCommon {
     const int32_t *m2l_tgt, *m2l_off, *m2l_src, *m2l_spec;  int64_t n_m2l_tgt;
     const int32_t* p2m_cells;  int64_t n_p2m;
     const int32_t* l2p_cells;  int64_t n_l2p;
-    const int32_t *p2p_leaf, *p2p_off, *p2p_sbeg, *p2p_send;  int64_t n_p2p_leaf;
+    // near field: work units (leaf x bounded source ranges) and leaves
+    const int32_t *p2p_unit_leaf, *p2p_unit_off, *p2p_sbeg, *p2p_send, *p2p_soff, *p2p_part;
+    int64_t n_p2p_units, p2p_parts;
+    const int32_t *p2p_leaf, *p2p_leaf_off, *p2p_leaf_units;
+    int64_t n_p2p_leaf;
+    int* err_flag;           // set by a kernel whose bounded wait gave up (read by defmm_check)
 };
 
 // Tables in the arithmetic precision T.
@@ -57,6 +66,7 @@ struct DevWork {
     int R;
     C* qs;     // [R][ny]
     C* ps;     // [R][nx]
+    C* part;   // [R][p2p_parts] near-field partial sums of the work units
     C* M;      // [nM][R][P3]
     C* Mhat;   // [nMhat][R][NFpad]
     C* L;      // [nL][R][P3]

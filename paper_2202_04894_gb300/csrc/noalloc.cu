@@ -5,7 +5,8 @@
 // whose device memory is owned by a pool or allocator that another component
 // controls, or solvers that have reserved all device memory up front.  For
 // them this entry point takes the application phase's scratch (Morton-ordered
-// charges and potentials, multipole, Fourier-domain and local expansions)
+// charges and potentials, multipole, Fourier-domain and local expansions,
+// near-field partial sums)
 // from a fixed array linked into the library instead of from cudaMalloc.
 //
 // Limits and rules:
@@ -77,6 +78,7 @@ defmm_status apply_static(defmm_plan_s* pl, const void* q, void* p, int R, cudaS
     const size_t o_M = carve(off, (size_t)R * hp.nM() * hp.P3);
     const size_t o_Mh = carve(off, (size_t)R * hp.m2f_list.size() * hp.NFpad);
     const size_t o_L = carve(off, (size_t)R * hp.nL() * hp.P3);
+    const size_t o_part = carve(off, (size_t)R * hp.p2p_parts);
     if (off > kScratchBytes)
         return defmm::set_error(DEFMM_ERR_UNSUPPORTED,
                                 "defmm_apply_noalloc: this plan needs " + std::to_string(off) +
@@ -94,6 +96,7 @@ defmm_status apply_static(defmm_plan_s* pl, const void* q, void* p, int R, cudaS
     w.M = reinterpret_cast<C*>(b + o_M);
     w.Mhat = reinterpret_cast<C*>(b + o_Mh);
     w.L = reinterpret_cast<C*>(b + o_L);
+    w.part = reinterpret_cast<C*>(b + o_part);
     w.nL = hp.nL();
     const defmm::DevTyped<T>& typed = typed_tables(pl, (T*)nullptr);
     int launches = 0;

@@ -205,6 +205,10 @@ static void sort_unique(std::vector<int32_t>& v) {
 }
 
 // ---------------------------------------------------------------- plan
+template <typename U> static bool units_for_leaf_empty(const std::vector<U>& units, int32_t li) {
+    return units.empty() || units.back().leaf != li;
+}
+
 void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa,
                      int order, int leaf, double eta, double hf_kw, int fft_n, double self_eps,
                      HostPlan& hp) {
@@ -428,16 +432,27 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
             hp.m2f_list.push_back((int32_t)e);
         }
     std::stable_sort(recs.begin(), recs.end(), [](const PairRec& a, const PairRec& b) { return a.tgt < b.tgt; });
-    hp.m2l_off.push_back(0);
-    for (size_t i = 0; i < recs.size(); ++i) {
-        if (i == 0 || recs[i].tgt != recs[i - 1].tgt) {
-            if (i > 0) hp.m2l_off.push_back((int32_t)i);
-            hp.m2l_tgt.push_back(recs[i].tgt);
+    {
+        // group by target expansion, then order the groups longest first
+        std::vector<std::pair<size_t, size_t>> groups;  // [begin, end) in recs
+        for (size_t i = 0; i < recs.size(); ++i)
+            if (i == 0 || recs[i].tgt != recs[i - 1].tgt) groups.push_back({i, i});
+        for (size_t g = 0; g < groups.size(); ++g)
+            groups[g].second = g + 1 < groups.size() ? groups[g + 1].first : recs.size();
+        std::stable_sort(groups.begin(), groups.end(), [](const std::pair<size_t, size_t>& a,
+                                                          const std::pair<size_t, size_t>& b) {
+            return a.second - a.first > b.second - b.first;
+        });
+        hp.m2l_off.push_back(0);
+        for (auto& g : groups) {
+            hp.m2l_tgt.push_back(recs[g.first].tgt);
+            for (size_t i = g.first; i < g.second; ++i) {
+                hp.m2l_src.push_back(hp.mhat_of_m[recs[i].src]);
+                hp.m2l_spec.push_back(recs[i].spec * 64 + recs[i].code);
+            }
+            hp.m2l_off.push_back((int32_t)hp.m2l_src.size());
         }
-        hp.m2l_src.push_back(hp.mhat_of_m[recs[i].src]);
-        hp.m2l_spec.push_back(recs[i].spec * 64 + recs[i].code);
     }
-    if (!recs.empty()) hp.m2l_off.push_back((int32_t)recs.size());
 
     // ---- M2M per parent level (source tree)
     int nlev_s = (int)ts.level_range.size();
@@ -500,25 +515,83 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         for (int32_t a = 0; a < tt.nchild[t]; ++a) push_down(tt.first_child[t] + a, s);
     };
     for (auto& pr : hp.p2p) push_down(pr[0], pr[1]);
-    hp.p2p_off.push_back(0);
+    struct Unit { int32_t leaf; int64_t work; std::vector<int32_t> b, e; };
+    std::vector<Unit> units;
     for (int32_t c = 0; c < tt.ncell(); ++c) {
         if (!tt.leaf(c)) continue;
+        const int32_t li = (int32_t)hp.p2p_leaf.size();
         hp.p2p_leaf.push_back(c);
         auto& v = near[c];
         std::sort(v.begin(), v.end(), [&](int32_t a, int32_t b) { return ts.begin[a] < ts.begin[b]; });
-        int64_t nt = tt.end[c] - tt.begin[c];
+        const int64_t nt = tt.end[c] - tt.begin[c];
+        // merged ranges of the leaf, then cut into units of bounded size
+        std::vector<int32_t> rb, re;
         for (size_t i = 0; i < v.size(); ++i) {
-            int32_t b = (int32_t)ts.begin[v[i]], e = (int32_t)ts.end[v[i]];
+            const int32_t b = (int32_t)ts.begin[v[i]], e = (int32_t)ts.end[v[i]];
             hp.p2p_interactions += nt * (int64_t)(e - b);
-            if (!hp.p2p_sbeg.empty() && (int32_t)hp.p2p_sbeg.size() > hp.p2p_off.back() &&
-                hp.p2p_send.back() == b) {
-                hp.p2p_send.back() = e;  // merge contiguous ranges
-            } else {
-                hp.p2p_sbeg.push_back(b);
-                hp.p2p_send.push_back(e);
+            if (!re.empty() && re.back() == b) re.back() = e;
+            else { rb.push_back(b); re.push_back(e); }
+        }
+        Unit u{li, 0, {}, {}};
+        int32_t have = 0;
+        auto flush = [&]() {
+            if (!u.b.empty()) { u.work = nt * (int64_t)have; units.push_back(u); }
+            u = Unit{li, 0, {}, {}};
+            have = 0;
+        };
+        for (size_t k = 0; k < rb.size(); ++k) {
+            int32_t b = rb[k];
+            while (b < re[k]) {
+                if (have == kP2PUnitSources || (int)u.b.size() == kP2PUnitRanges) flush();
+                const int32_t take = std::min(re[k] - b, kP2PUnitSources - have);
+                u.b.push_back(b);
+                u.e.push_back(b + take);
+                have += take;
+                b += take;
             }
         }
-        hp.p2p_off.push_back((int32_t)hp.p2p_sbeg.size());
+        if (u.b.empty() && units_for_leaf_empty(units, li)) {
+            // a leaf without near sources still owns one (empty) unit: its sums are zero
+            units.push_back(Unit{li, 0, {}, {}});
+        } else {
+            flush();
+        }
+    }
+    // heaviest units first, so that the last blocks to start are short ones
+    std::stable_sort(units.begin(), units.end(), [](const Unit& a, const Unit& b) { return a.work > b.work; });
+    hp.p2p_unit_off.push_back(0);
+    std::vector<std::vector<int32_t>> leaf_units(hp.p2p_leaf.size());
+    int64_t parts = 0;
+    for (size_t ui = 0; ui < units.size(); ++ui) {
+        const Unit& u = units[ui];
+        hp.p2p_unit_leaf.push_back(u.leaf);
+        int32_t acc = 0;
+        for (size_t k = 0; k < u.b.size(); ++k) {
+            hp.p2p_sbeg.push_back(u.b[k]);
+            hp.p2p_send.push_back(u.e[k]);
+            hp.p2p_soff.push_back(acc);
+            acc += u.e[k] - u.b[k];
+        }
+        hp.p2p_unit_off.push_back((int32_t)hp.p2p_sbeg.size());
+        hp.p2p_part.push_back((int32_t)parts);
+        const int32_t c = hp.p2p_leaf[u.leaf];
+        parts += tt.end[c] - tt.begin[c];
+        leaf_units[u.leaf].push_back((int32_t)ui);
+    }
+    if (parts > (1LL << 31) - 1) throw std::runtime_error("too many near-field partial sums");
+    hp.p2p_parts = parts;
+    hp.p2p_leaf_off.push_back(0);
+    for (size_t li = 0; li < leaf_units.size(); ++li) {
+        // units of a leaf in the order of their sources, so the reduction order is fixed
+        auto& lu = leaf_units[li];
+        std::sort(lu.begin(), lu.end(), [&](int32_t a, int32_t b) {
+            const int32_t ra = hp.p2p_unit_off[a], rb2 = hp.p2p_unit_off[b];
+            const int32_t na = hp.p2p_unit_off[a + 1] - ra, nb = hp.p2p_unit_off[b + 1] - rb2;
+            const int32_t ka = na ? hp.p2p_sbeg[ra] : -1, kb = nb ? hp.p2p_sbeg[rb2] : -1;
+            return ka < kb;
+        });
+        hp.p2p_leaf_units.insert(hp.p2p_leaf_units.end(), lu.begin(), lu.end());
+        hp.p2p_leaf_off.push_back((int32_t)hp.p2p_leaf_units.size());
     }
 }
 

@@ -17,6 +17,8 @@ namespace defmm {
 constexpr int kMaxLevel = 21;
 constexpr int kNumLevels = kMaxLevel + 1;
 constexpr int kMaxOrder = 8;
+constexpr int kP2PUnitSources = 4096;
+constexpr int kP2PUnitRanges = 256;
 
 struct Tree {
     std::vector<int64_t> perm;  // sorted position -> input index
@@ -107,9 +109,17 @@ struct HostPlan {
     std::vector<std::vector<int32_t>> l2l_par;  // parent local exp ids per level
     // leaves
     std::vector<int32_t> p2m_cells, l2p_cells;  // cells (source / target tree)
-    // P2P CSR over target leaves: source ranges
-    std::vector<int32_t> p2p_leaf, p2p_off;
-    std::vector<int32_t> p2p_sbeg, p2p_send;
+    // P2P work units: a unit is one target leaf against at most kP2PUnitSources
+    // of its near sources (its ranges in Morton order); units are ordered by
+    // work, heaviest first.  Each unit writes partial sums for its leaf's
+    // targets at p2p_part[unit]; the leaf's units are reduced in order.
+    std::vector<int32_t> p2p_unit_leaf;              // unit -> index into p2p_leaf
+    std::vector<int32_t> p2p_unit_off;               // CSR into the unit ranges below
+    std::vector<int32_t> p2p_sbeg, p2p_send, p2p_soff;  // ranges, prefix within the unit
+    std::vector<int32_t> p2p_part;                   // unit -> first partial-sum slot
+    std::vector<int32_t> p2p_leaf;                   // target leaf cells
+    std::vector<int32_t> p2p_leaf_off, p2p_leaf_units;  // leaf -> its units, in source order
+    int64_t p2p_parts = 0;                           // partial-sum slots per right-hand side
     int64_t p2p_interactions = 0;
 
     int64_t nM() const { return (int64_t)m_cell.size(); }

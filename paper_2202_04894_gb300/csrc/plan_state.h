@@ -15,12 +15,12 @@ namespace defmm {
 
 template <typename T> struct Workspace {
     int R = 0;
-    typename Cplx<T>::type *qs = nullptr, *ps = nullptr, *M = nullptr, *Mhat = nullptr, *L = nullptr;
+    typename Cplx<T>::type *qs = nullptr, *ps = nullptr, *M = nullptr, *Mhat = nullptr, *L = nullptr, *part = nullptr;
     void* q_stage = nullptr;
     void* p_stage = nullptr;
     size_t bytes = 0;
     void release() {
-        cudaFree(qs); cudaFree(ps); cudaFree(M); cudaFree(Mhat); cudaFree(L);
+        cudaFree(qs); cudaFree(ps); cudaFree(M); cudaFree(Mhat); cudaFree(L); cudaFree(part);
         cudaFree(q_stage); cudaFree(p_stage);
         *this = Workspace();
     }

@@ -41,6 +41,7 @@ class Info(ctypes.Structure):
                 ("n_fourier", ctypes.c_int64), ("n_spectra", ctypes.c_int64),
                 ("p2p_interactions", ctypes.c_int64), ("plan_bytes", ctypes.c_size_t),
                 ("workspace_bytes", ctypes.c_size_t), ("launches_per_apply", ctypes.c_int64),
+                ("device_error", ctypes.c_int64),
                 ("d_aabb", ctypes.c_double), ("cube_side", ctypes.c_double)]
 
 

@@ -61,6 +61,8 @@ CASES = [
     ("sphere", 3000, None, 24.0, 3, 150, 8),      # leaves of >64 targets, >128 sources, N > 2p-1
     ("box", 1200, None, 40.0, 2, 12, 0),
     ("ellipsoid", 4000, None, 64.0, 4, 40, 0),
+    ("sphere", 1500, None, 10.0, 3, 30, 13),       # N^3 = 2197 samples: four per M2L thread
+    ("box", 2500, None, 20.0, 4, 200, 0),          # leaves of 129..200 targets: two P2P passes
 ]
 
 
