@@ -184,7 +184,9 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     size_t o_lf = b.add(hp.l_first), o_lc = b.add(hp.l_count), o_ls = b.add(hp.l_slot);
     size_t o_su = b.add(hp.slot_u);
     size_t o_m2f = b.add(hp.m2f_list);
-    size_t o_mt = b.add(hp.m2l_tgt), o_mo = b.add(hp.m2l_off), o_msrc = b.add(hp.m2l_src), o_mspec = b.add(hp.m2l_spec);
+    size_t o_gmo = b.add(hp.grp_member_off), o_gm = b.add(hp.grp_members), o_gco = b.add(hp.grp_chunk_off);
+    size_t o_cbo = b.add(hp.chk_blk_off), o_cns = b.add(hp.chk_nspec), o_cb = b.add(hp.chk_blk);
+    size_t o_coo = b.add(hp.chk_op_off), o_co = b.add(hp.chk_op);
     size_t o_p2m = b.add(hp.p2m_cells), o_l2p = b.add(hp.l2p_cells);
     size_t o_pul = b.add(hp.p2p_unit_leaf), o_puo = b.add(hp.p2p_unit_off), o_psb = b.add(hp.p2p_sbeg),
            o_pse = b.add(hp.p2p_send), o_pso = b.add(hp.p2p_soff), o_ppt = b.add(hp.p2p_part);
@@ -234,9 +236,12 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.l_first = (const int32_t*)P(o_lf); c.l_count = (const int32_t*)P(o_lc); c.l_slot = (const int32_t*)P(o_ls);
     c.slot_u = (const double*)P(o_su);
     c.m2f_list = (const int32_t*)P(o_m2f); c.n_m2f = (int64_t)hp.m2f_list.size();
-    c.m2l_tgt = (const int32_t*)P(o_mt); c.m2l_off = (const int32_t*)P(o_mo);
-    c.m2l_src = (const int32_t*)P(o_msrc); c.m2l_spec = (const int32_t*)P(o_mspec);
-    c.n_m2l_tgt = (int64_t)hp.m2l_tgt.size();
+    c.grp_member_off = (const int32_t*)P(o_gmo); c.grp_members = (const int32_t*)P(o_gm);
+    c.grp_chunk_off = (const int32_t*)P(o_gco);
+    c.n_grp = (int64_t)hp.grp_member_off.size() - 1;
+    c.chk_blk_off = (const int32_t*)P(o_cbo); c.chk_nspec = (const int32_t*)P(o_cns); c.chk_blk = (const int32_t*)P(o_cb);
+    c.chk_op_off = (const int32_t*)P(o_coo); c.chk_op = (const int32_t*)P(o_co);
+    c.chk_max_blocks = hp.chk_max_blocks;
     c.p2m_cells = (const int32_t*)P(o_p2m); c.n_p2m = (int64_t)hp.p2m_cells.size();
     c.l2p_cells = (const int32_t*)P(o_l2p); c.n_l2p = (int64_t)hp.l2p_cells.size();
     c.p2p_unit_leaf = (const int32_t*)P(o_pul); c.p2p_unit_off = (const int32_t*)P(o_puo);

@@ -585,25 +585,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 constexpr int kM2LMaxStages = 3;  // ring depth (runtime S <= this)
 constexpr size_t kSmemLimit = 227 * 1024 - 2048;   // dynamic shared memory per block, with room for static
 
-// One block per target expansion with a non-empty list.  The list is cut into
-// chunks of P pairs; a chunk's canonical spectra and source Fourier multipoles
-// (one contiguous NFpad block each) are brought into a ring of S
-// shared-memory stages by TMA bulk copies issued by thread 0, while the block
-// computes an earlier chunk.  Thread i owns the Fourier samples
-// xi = i + v*blockDim (v < VPT) and accumulates, for each pair,
-// spectrum(xi') * Mhat(xi) with xi'_{sigma(a)} = s_a xi_a mod N: the symmetry
-// of the pair is applied as a gather from shared memory.  The inverse DFT and
-// the crop to the p^3 grid follow in shared memory.
-template <typename T, int VPT>
-__global__ void __launch_bounds__(1024) k_m2l(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
-                                              typename Cplx<T>::type* __restrict__ L, int R, int P, int S) {
+// One block per M2L group: up to 8 sibling target expansions sharing a father
+// cell and a direction.  The group's pairs come in chunks; a chunk's blocks
+// (the distinct canonical spectra and source Fourier multipoles it uses, one
+// contiguous NFpad block each) are brought into a ring of S shared-memory
+// stages by TMA bulk copies (cp.async.bulk) issued by thread 0 and completed
+// on mbarriers, while the block computes an earlier chunk; every staged block
+// serves all pairs of the chunk that use it.  Thread i owns the Fourier
+// samples xi = i + v*blockDim (v < VPT) and accumulates, for each pair of
+// member m, spectrum(xi') * Mhat(xi), xi'_{sigma(a)} = s_a xi_a mod N: the
+// pair's symmetry is applied as a gather from shared memory.  The inverse DFT
+// and the crop to the p^3 grid of each member follow in shared memory.
+template <typename T, int VPT, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_m2l(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
+                                              typename Cplx<T>::type* __restrict__ L, int R, int S) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int p = c.p, N = c.N, NF = c.NF, NFpad = c.NFpad, P3 = c.P3;
     const uint32_t blk_bytes = (uint32_t)(NFpad * sizeof(C));
-    // ring of stages: stage s holds P spectra then P Fourier multipoles
     C* ring = reinterpret_cast<C*>(smem_raw);
-    const int stage_elems = 2 * P * NFpad;
+    const int stage_elems = c.chk_max_blocks * NFpad;
     // F2L work arrays reuse the ring once every copy has landed
     C* Lh = ring;                              // NF
     C* T1 = Lh + NF;                           // [az][xi_y][xi_x]  p*N*N
@@ -611,11 +612,9 @@ __global__ void __launch_bounds__(1024) k_m2l(DevCommon c, DevTyped<T> t, const 
     __shared__ __align__(8) uint64_t bars[kM2LMaxStages];
     __shared__ C tws[16];
     __shared__ int stride[6][3];               // N^sigma(a) for each axis permutation
-    const int i = blockIdx.x;
-    const int te = c.m2l_tgt[i];
-    const int j0 = c.m2l_off[i], j1 = c.m2l_off[i + 1];
-    const int npairs = j1 - j0;
-    const int nchunks = (npairs + P - 1) / P;
+    const int g = blockIdx.x;
+    const int mem0 = c.grp_member_off[g], nm = c.grp_member_off[g + 1] - mem0;
+    const int ch0 = c.grp_chunk_off[g], nchunks = c.grp_chunk_off[g + 1] - ch0;
     if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
     if (threadIdx.x < 18) {
         const int q = kPermDev[threadIdx.x / 3][threadIdx.x % 3];
@@ -635,28 +634,29 @@ __global__ void __launch_bounds__(1024) k_m2l(DevCommon c, DevTyped<T> t, const 
         for (int a = 0; a < 3; ++a) cn[v][a] = cp[v][a] == 0 ? 0 : N - cp[v][a];
     }
     __syncthreads();
-    uint32_t use = 0;  // chunks consumed so far (all right-hand sides): stage = use % S, parity = (use / S) & 1
+    uint32_t use = 0;  // chunks consumed so far: stage = use % S, parity = (use / S) & 1
     const T scale = (T)1 / (T)NF;
-    // producer: copies of chunk ch (right-hand side r) into stage st
+    // producer: the blocks of chunk ch (right-hand side r) into stage st
     auto issue = [&](int ch, int r, int st) {
-        const int q0 = j0 + ch * P;
-        const int nq = min(P, j1 - q0);
+        const int cc = ch0 + ch;
+        const int b0 = c.chk_blk_off[cc], nb = c.chk_blk_off[cc + 1] - b0, nsp = c.chk_nspec[cc];
         C* base = ring + (size_t)st * stage_elems;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&bars[st], 2u * nq * blk_bytes);
-        for (int q = 0; q < nq; ++q) {
-            const int sid = c.m2l_spec[q0 + q] >> 6;
-            const int src = c.m2l_src[q0 + q];
-            tma_bulk_load(base + (size_t)q * NFpad, t.spec + (int64_t)sid * NFpad, blk_bytes, &bars[st]);
-            tma_bulk_load(base + (size_t)(P + q) * NFpad, Mhat + ((int64_t)src * R + r) * NFpad, blk_bytes, &bars[st]);
+        mbar_expect_tx(&bars[st], (uint32_t)nb * blk_bytes);
+        for (int b = 0; b < nb; ++b) {
+            const int id = c.chk_blk[b0 + b];
+            const C* src = b < nsp ? t.spec + (int64_t)id * NFpad : Mhat + ((int64_t)id * R + r) * NFpad;
+            tma_bulk_load(base + (size_t)b * NFpad, src, blk_bytes, &bars[st]);
         }
     };
     for (int r = 0; r < R; ++r) {
         if (threadIdx.x == 0)
             for (int k = 0; k < S - 1 && k < nchunks; ++k) issue(k, r, (use + k) % S);
-        C acc[VPT];
+        C acc[8][VPT];
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) acc[v] = czero<C>();
+        for (int m = 0; m < 8; ++m)
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) acc[m][v] = czero<C>();
         for (int ch = 0; ch < nchunks; ++ch, ++use) {
             const int st = use % S;
             const bool ok = mbar_wait(&bars[st], (use / S) & 1);
@@ -672,70 +672,248 @@ __global__ void __launch_bounds__(1024) k_m2l(DevCommon c, DevTyped<T> t, const 
                 }
                 return;
             }
-            if (threadIdx.x == 0 && ch + S - 1 < nchunks)
-                issue(ch + S - 1, r, (use + S - 1) % S);
-            const C* sg = ring + (size_t)st * stage_elems;
-            const C* sm = sg + (size_t)P * NFpad;
-            const int q0 = j0 + ch * P;
-            const int nq = min(P, j1 - q0);
-            for (int q = 0; q < nq; ++q) {
-                const int code = c.m2l_spec[q0 + q] & 63;
-                const int pid = code >> 3;
-                const int s0 = stride[pid][0], s1 = stride[pid][1], s2 = stride[pid][2];
-                const C* g = sg + (size_t)q * NFpad;
-                const C* m = sm + (size_t)q * NFpad;
+            if (threadIdx.x == 0 && ch + S - 1 < nchunks) issue(ch + S - 1, r, (use + S - 1) % S);
+            const C* base = ring + (size_t)st * stage_elems;
+            const int* opoff = c.chk_op_off + 9 * (ch0 + ch);
 #pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    if (xi[v] < NF) {
-                        const int idx = ((code & 1) ? cn[v][0] : cp[v][0]) * s0 +
-                                        ((code & 2) ? cn[v][1] : cp[v][1]) * s1 +
-                                        ((code & 4) ? cn[v][2] : cp[v][2]) * s2;
-                        cfma(acc[v], g[idx], m[xi[v]]);
+            for (int m = 0; m < 8; ++m) {
+                const int o1 = opoff[m + 1];
+                for (int o = opoff[m]; o < o1; ++o) {
+                    const int op = c.chk_op[o];
+                    const int code = op >> 16, pid = code >> 3;
+                    const int s0 = stride[pid][0], s1 = stride[pid][1], s2 = stride[pid][2];
+                    const C* gs = base + (size_t)(op & 255) * NFpad;
+                    const C* ms = base + (size_t)((op >> 8) & 255) * NFpad;
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        if (xi[v] < NF) {
+                            const int idx = ((code & 1) ? cn[v][0] : cp[v][0]) * s0 +
+                                            ((code & 2) ? cn[v][1] : cp[v][1]) * s1 +
+                                            ((code & 4) ? cn[v][2] : cp[v][2]) * s2;
+                            cfma(acc[m][v], gs[idx], ms[xi[v]]);
+                        }
                     }
                 }
             }
         }
         __syncthreads();   // every chunk read: the ring may now hold the F2L arrays
 #pragma unroll
-        for (int v = 0; v < VPT; ++v)
-            if (xi[v] < NF) Lh[xi[v]] = acc[v];
-        __syncthreads();
-        for (int q = threadIdx.x; q < p * N * N; q += blockDim.x) {  // z
-            const int xy = q % (N * N), az = q / (N * N);
-            C s = czero<C>();
-            for (int k = 0; k < N; ++k) cfma(s, Lh[k * N * N + xy], tws[(k * az) % N]);
-            T1[q] = s;
+        for (int m = 0; m < 8; ++m) {
+            if (m >= nm) break;
+#pragma unroll
+            for (int v = 0; v < VPT; ++v)
+                if (xi[v] < NF) Lh[xi[v]] = acc[m][v];
+            __syncthreads();
+            for (int q = threadIdx.x; q < p * N * N; q += blockDim.x) {  // z
+                const int xy = q % (N * N), az = q / (N * N);
+                C s = czero<C>();
+                for (int k = 0; k < N; ++k) cfma(s, Lh[k * N * N + xy], tws[(k * az) % N]);
+                T1[q] = s;
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < p * p * N; q += blockDim.x) {  // y
+                const int xx = q % N, ay = (q / N) % p, az = q / (N * p);
+                C s = czero<C>();
+                for (int k = 0; k < N; ++k) cfma(s, T1[(az * N + k) * N + xx], tws[(k * ay) % N]);
+                T2[q] = s;
+            }
+            __syncthreads();
+            const int te = c.grp_members[mem0 + m];
+            for (int a = threadIdx.x; a < P3; a += blockDim.x) {  // x, crop, 1/N^3
+                const int ax = a % p, rest = a / p;  // rest = az*p + ay
+                C s = czero<C>();
+                for (int k = 0; k < N; ++k) cfma(s, T2[rest * N + k], tws[(k * ax) % N]);
+                L[((int64_t)te * R + r) * P3 + a] = cscale(s, scale);
+            }
+            __syncthreads();   // Lh, T1, T2 reused by the next member / the next prologue
         }
-        __syncthreads();
-        for (int q = threadIdx.x; q < p * p * N; q += blockDim.x) {  // y
-            const int xx = q % N, ay = (q / N) % p, az = q / (N * p);
-            C s = czero<C>();
-            for (int k = 0; k < N; ++k) cfma(s, T1[(az * N + k) * N + xx], tws[(k * ay) % N]);
-            T2[q] = s;
-        }
-        __syncthreads();
-        for (int a = threadIdx.x; a < P3; a += blockDim.x) {  // x, crop, 1/N^3
-            const int ax = a % p, rest = a / p;  // rest = az*p + ay
-            C s = czero<C>();
-            for (int k = 0; k < N; ++k) cfma(s, T2[rest * N + k], tws[(k * ax) % N]);
-            L[((int64_t)te * R + r) * P3 + a] = cscale(s, scale);
-        }
-        __syncthreads();   // F2L arrays alias the ring: done before the next prologue
     }
 }
 
-// Ring depth S, pairs per stage P and the dynamic shared memory of k_m2l:
-// three stages of up to 24 KB when they fit, else two stages of one pair.
-template <typename T> __host__ void m2l_shape(const DevCommon& c, int* P, int* S, size_t* smem) {
-    const size_t blk = (size_t)c.NFpad * sizeof(typename Cplx<T>::type);
-    int pp = (int)(24576 / (2 * blk));
-    if (pp < 1) pp = 1;
-    if (pp > 8) pp = 8;
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The same group schedule with rows of samples and a warp-specialised
+// pipeline.  Consumer thread (member m, lane l) of the first 8*TPM threads
+// owns the x-row (y, z) = (l mod N, l div N) of member m (l < N^2), i.e. the
+// N samples xi = x + N*l: under a pair's symmetry (sigma, s) the row's
+// permuted indices are base(y, z) + x*step (with a wrap for a negated x), so
+// the permutation costs one row base per pair.  The last warp is the
+// producer: it keeps every stage of the ring loaded with TMA bulk copies,
+// waiting on per-stage "empty" mbarriers that the consumer warps arrive on
+// after reading a stage; consumers wait on per-stage "full" mbarriers that
+// the copies complete.  There is no block-wide barrier in the main loop.
+// Every wait is bounded; a wait that gives up raises the plan's error flag
+// and the block stops after its copies in flight have had a bounded chance to
+// land.  Needs N <= NX and N^2 <= TPM.
+template <typename T, int NX, int TPM>
+__global__ void __launch_bounds__(8 * TPM + 32) k_m2l_rows(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
+                                                          typename Cplx<T>::type* __restrict__ L, int R, int S) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int p = c.p, N = c.N, NF = c.NF, NFpad = c.NFpad, P3 = c.P3;
+    const int NN = N * N;
+    const uint32_t blk_bytes = (uint32_t)(NFpad * sizeof(C));
+    C* ring = reinterpret_cast<C*>(smem_raw);
+    const int stage_elems = c.chk_max_blocks * NFpad;
+    __shared__ __align__(8) uint64_t full[kM2LMaxStages], empty[kM2LMaxStages];
+    __shared__ C tws[16];
+    __shared__ int stride[6][3];
+    __shared__ int abort_store, issued_sh, abort_at;
+    volatile int& abort_sh = abort_store;   // written and polled by different warps
+    const int g = blockIdx.x;
+    const int mem0 = c.grp_member_off[g], nm = c.grp_member_off[g + 1] - mem0;
+    const int ch0 = c.grp_chunk_off[g], nchunks = c.grp_chunk_off[g + 1] - ch0;
+    const bool producer = threadIdx.x >= 8 * TPM;
+    const int lane = threadIdx.x & 31;
+    const int m = threadIdx.x / TPM, l = threadIdx.x % TPM;
+    const bool member = !producer && m < nm;     // warp belongs to a member of the group
+    const bool active = member && l < NN;        // lane owns a row
+    const int y = l % N, z = l / N;
+    const int yn = y == 0 ? 0 : N - y, zn = z == 0 ? 0 : N - z;
+    const int consumer_warps = nm * (TPM / 32);
+    if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
+    if (threadIdx.x < 18) {
+        const int q = kPermDev[threadIdx.x / 3][threadIdx.x % 3];
+        stride[threadIdx.x / 3][threadIdx.x % 3] = q == 0 ? 1 : (q == 1 ? N : N * N);
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], consumer_warps);
+        }
+        abort_sh = 0;
+        issued_sh = 0;
+        abort_at = 1 << 30;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t use0 = 0;   // chunks of earlier right-hand sides
+    const T scale = (T)1 / (T)NF;
+    for (int r = 0; r < R; ++r) {
+        C acc[NX];
+#pragma unroll
+        for (int x = 0; x < NX; ++x) acc[x] = czero<C>();
+        if (producer) {
+            if (lane == 0) {
+                for (int k = 0; k < nchunks; ++k) {
+                    const uint32_t u = use0 + k;
+                    const int st = u % S;
+                    if (u >= (uint32_t)S && !mbar_wait(&empty[st], ((u / S) - 1) & 1)) {
+                        abort_sh = 1;
+                        atomicExch(c.err_flag, 1);
+                        break;
+                    }
+                    if (abort_sh) break;
+                    const int cc = ch0 + k;
+                    const int b0 = c.chk_blk_off[cc], nb = c.chk_blk_off[cc + 1] - b0, nsp = c.chk_nspec[cc];
+                    C* base = ring + (size_t)st * stage_elems;
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(&full[st], (uint32_t)nb * blk_bytes);
+                    for (int b = 0; b < nb; ++b) {
+                        const int id = c.chk_blk[b0 + b];
+                        const C* src = b < nsp ? t.spec + (int64_t)id * NFpad : Mhat + ((int64_t)id * R + r) * NFpad;
+                        tma_bulk_load(base + (size_t)b * NFpad, src, blk_bytes, &full[st]);
+                    }
+                    issued_sh = k + 1;
+                }
+            }
+        } else if (member) {
+            for (int k = 0; k < nchunks; ++k) {
+                const uint32_t u = use0 + k;
+                const int st = u % S;
+                if (!mbar_wait(&full[st], (u / S) & 1) || abort_sh) {
+                    abort_sh = 1;
+                    atomicMin(&abort_at, k);
+                    atomicExch(c.err_flag, 1);
+                    break;
+                }
+                if (active) {
+                    const C* base = ring + (size_t)st * stage_elems;
+                    const int* opoff = c.chk_op_off + 9 * (ch0 + k);
+                    const int o1 = opoff[m + 1];
+                    for (int o = opoff[m]; o < o1; ++o) {
+                        const int op = c.chk_op[o];
+                        const int code = op >> 16, pid = code >> 3;
+                        const int s0 = stride[pid][0], s1 = stride[pid][1], s2 = stride[pid][2];
+                        const C* gs = base + (size_t)(op & 255) * NFpad;
+                        const C* ms = base + (size_t)((op >> 8) & 255) * NFpad + (size_t)l * N;
+                        // permuted index of sample (x, y, z): f0(x) s0 + f1(y) s1 + f2(z) s2
+                        const int rowb = ((code & 2) ? yn : y) * s1 + ((code & 4) ? zn : z) * s2;
+                        const int xneg = code & 1;
+                        const int b1 = xneg ? rowb + N * s0 : rowb;   // x >= 1: b1 + x * dx
+                        const int dx = xneg ? -s0 : s0;
+                        cfma(acc[0], gs[rowb], ms[0]);
+#pragma unroll
+                        for (int x = 1; x < NX; ++x)
+                            if (x < N) cfma(acc[x], gs[b1 + x * dx], ms[x]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[st]);
+            }
+        }
+        __syncthreads();   // every chunk of this right-hand side consumed (or the block gave up)
+        if (abort_sh) {
+            if (threadIdx.x == 0) {   // bounded drain of copies issued but never waited for
+                const int first = abort_at < nchunks ? abort_at : 0;
+                for (int k = first; k < issued_sh; ++k)
+                    (void)mbar_wait(&full[(use0 + k) % S], ((use0 + k) / S) & 1);
+            }
+            __syncthreads();
+            return;
+        }
+        use0 += nchunks;
+        // F2L of every member in parallel: member m uses its own arrays and its TPM threads
+        C* Lh = ring + (size_t)(member ? m : 0) * (NF + p * NN + p * p * N);
+        C* T1 = Lh + NF;
+        C* T2 = T1 + p * NN;
+        if (active) {
+#pragma unroll
+            for (int x = 0; x < NX; ++x)
+                if (x < N) Lh[l * N + x] = acc[x];
+        }
+        __syncthreads();
+        if (member)
+            for (int q = l; q < p * NN; q += TPM) {  // z
+                const int xy = q % NN, az = q / NN;
+                C s = czero<C>();
+                for (int k = 0; k < N; ++k) cfma(s, Lh[k * NN + xy], tws[(k * az) % N]);
+                T1[q] = s;
+            }
+        __syncthreads();
+        if (member)
+            for (int q = l; q < p * p * N; q += TPM) {  // y
+                const int xx = q % N, ay = (q / N) % p, az = q / (N * p);
+                C s = czero<C>();
+                for (int k = 0; k < N; ++k) cfma(s, T1[(az * N + k) * N + xx], tws[(k * ay) % N]);
+                T2[q] = s;
+            }
+        __syncthreads();
+        if (member) {
+            const int te = c.grp_members[mem0 + m];
+            for (int a = l; a < P3; a += TPM) {  // x, crop, 1/N^3
+                const int ax = a % p, rest = a / p;
+                C s = czero<C>();
+                for (int k = 0; k < N; ++k) cfma(s, T2[rest * N + k], tws[(k * ax) % N]);
+                L[((int64_t)te * R + r) * P3 + a] = cscale(s, scale);
+            }
+        }
+        __syncthreads();   // the F2L arrays alias the ring: done before the next right-hand side
+    }
+}
+
+// Ring depth S and the dynamic shared memory of the M2L kernels: three stages
+// of chk_max_blocks blocks when they fit, else two; the F2L arrays (of one
+// member, or of all 8 for the row kernel) reuse the same memory.
+template <typename T> __host__ void m2l_shape(const DevCommon& c, int members, int* S, size_t* smem) {
+    const size_t stage = (size_t)c.chk_max_blocks * c.NFpad * sizeof(typename Cplx<T>::type);
     int ss = kM2LMaxStages;
-    while (ss > 2 && (size_t)ss * 2 * pp * blk > kSmemLimit) --ss;
-    const size_t ring = (size_t)ss * 2 * pp * blk;
-    const size_t f2l = ((size_t)c.NF + (size_t)c.p * c.N * c.N + (size_t)c.p * c.p * c.N) * sizeof(typename Cplx<T>::type);
-    *P = pp;
+    while (ss > 2 && (size_t)ss * stage > kSmemLimit) --ss;
+    const size_t ring = (size_t)ss * stage;
+    const size_t f2l = (size_t)members * ((size_t)c.NF + (size_t)c.p * c.N * c.N + (size_t)c.p * c.p * c.N) *
+                       sizeof(typename Cplx<T>::type);
     *S = ss;
     *smem = ring > f2l ? ring : f2l;
 }
@@ -1035,17 +1213,25 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     // transfer
     err = cudaMemsetAsync(w.L, 0, (size_t)w.nL * R * c.P3 * sizeof(C), stream);
     if (err != cudaSuccess) return err;
-    if (c.n_m2l_tgt > 0) {
-        int P, S;
-        size_t sm;
-        m2l_shape<T>(c, &P, &S, &sm);
-        if (sm > kSmemLimit) return cudaErrorInvalidConfiguration;
-        if (c.NF <= 2048) {  // two samples per thread, at most 1024 threads
-            const int threads = ((c.NF + 1) / 2 + 31) / 32 * 32;
-            k_m2l<T, 2><<<(unsigned)c.n_m2l_tgt, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, P, S);
+    if (c.n_grp > 0) {
+        int S, S8;
+        size_t sm, sm8;
+        m2l_shape<T>(c, 1, &S, &sm);
+        m2l_shape<T>(c, 8, &S8, &sm8);
+        if (c.N <= 8 && sm8 <= kSmemLimit) {         // rows of N <= 8 samples (N^2 <= 64), 64 threads per member
+            k_m2l_rows<T, 8, 64><<<(unsigned)c.n_grp, 512 + 32, sm8, stream>>>(c, t, w.Mhat, w.L, R, S8);
         } else {
-            const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
-            k_m2l<T, 4><<<(unsigned)c.n_m2l_tgt, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, P, S);
+            if (sm > kSmemLimit) return cudaErrorInvalidConfiguration;
+            if (c.NF <= 512) {          // two samples per thread, at most 256 threads
+                const int threads = ((c.NF + 1) / 2 + 31) / 32 * 32;
+                k_m2l<T, 2, 256><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, S);
+            } else if (c.NF <= 1024) {  // four samples per thread, at most 256 threads
+                const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
+                k_m2l<T, 4, 256><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, S);
+            } else {                    // four samples per thread, up to 1024 threads
+                const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
+                k_m2l<T, 4, 1024><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, S);
+            }
         }
         DEFMM_CHECK_LAUNCH();
     }
@@ -1081,8 +1267,10 @@ template <typename T>
 cudaError_t configure_kernels() {
     const int big = (int)kSmemLimit;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_m2l<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_m2l<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l<T, 2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l<T, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l<T, 4, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     return cudaSuccess;
 }

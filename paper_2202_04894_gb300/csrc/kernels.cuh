@@ -37,7 +37,10 @@ struct DevCommon {
     const double* slot_u;                       // 3 per slot
     // tables
     const int32_t* m2f_list;  int64_t n_m2f;
-    const int32_t *m2l_tgt, *m2l_off, *m2l_src, *m2l_spec;  int64_t n_m2l_tgt;
+    // M2L schedule: groups of sibling targets, chunks of staged blocks and pair ops
+    const int32_t *grp_member_off, *grp_members, *grp_chunk_off;  int64_t n_grp;
+    const int32_t *chk_blk_off, *chk_nspec, *chk_blk, *chk_op_off, *chk_op;
+    int chk_max_blocks;
     const int32_t* p2m_cells;  int64_t n_p2m;
     const int32_t* l2p_cells;  int64_t n_l2p;
     // near field: work units (leaf x bounded source ranges) and leaves

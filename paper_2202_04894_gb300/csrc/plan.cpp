@@ -432,25 +432,91 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
             hp.m2f_list.push_back((int32_t)e);
         }
     std::stable_sort(recs.begin(), recs.end(), [](const PairRec& a, const PairRec& b) { return a.tgt < b.tgt; });
+
+    // ---- M2L groups and chunks (sibling targets sharing a father and a direction)
     {
-        // group by target expansion, then order the groups longest first
-        std::vector<std::pair<size_t, size_t>> groups;  // [begin, end) in recs
-        for (size_t i = 0; i < recs.size(); ++i)
-            if (i == 0 || recs[i].tgt != recs[i - 1].tgt) groups.push_back({i, i});
-        for (size_t g = 0; g < groups.size(); ++g)
-            groups[g].second = g + 1 < groups.size() ? groups[g + 1].first : recs.size();
-        std::stable_sort(groups.begin(), groups.end(), [](const std::pair<size_t, size_t>& a,
-                                                          const std::pair<size_t, size_t>& b) {
-            return a.second - a.first > b.second - b.first;
-        });
-        hp.m2l_off.push_back(0);
-        for (auto& g : groups) {
-            hp.m2l_tgt.push_back(recs[g.first].tgt);
-            for (size_t i = g.first; i < g.second; ++i) {
-                hp.m2l_src.push_back(hp.mhat_of_m[recs[i].src]);
-                hp.m2l_spec.push_back(recs[i].spec * 64 + recs[i].code);
+        const int max_blocks = std::max(2, std::min(31, 22528 / (hp.NFpad * 8)));
+        hp.chk_max_blocks = max_blocks;
+        struct Op { int32_t member, src_parent, src, spec, code; };
+        std::unordered_map<int64_t, int32_t> group_of;   // (father cell, direction) -> group
+        std::vector<std::vector<int32_t>> members;        // local expansion ids
+        std::vector<std::vector<Op>> gops;
+        for (size_t i = 0; i < recs.size(); ++i) {
+            const int32_t te = recs[i].tgt;
+            const int32_t t = hp.l_cell[te], u = hp.l_dir[te];
+            const int64_t key = (int64_t)tt.parent[t] * (1LL << 32) + (int64_t)(u + 1);
+            auto it = group_of.find(key);
+            int32_t g;
+            if (it == group_of.end()) {
+                g = (int32_t)members.size();
+                group_of[key] = g;
+                members.push_back({});
+                gops.push_back({});
+            } else {
+                g = it->second;
             }
-            hp.m2l_off.push_back((int32_t)hp.m2l_src.size());
+            auto& mem = members[g];
+            int32_t m = -1;
+            for (size_t q = 0; q < mem.size(); ++q)
+                if (mem[q] == te) m = (int32_t)q;
+            if (m < 0) { m = (int32_t)mem.size(); mem.push_back(te); }
+            if (m >= 8) throw std::runtime_error("internal: more than 8 siblings in an M2L group");
+            const int32_t s_cell = hp.m_cell[recs[i].src];
+            gops[g].push_back({m, ts.parent[s_cell], hp.mhat_of_m[recs[i].src], recs[i].spec, recs[i].code});
+        }
+        // heaviest groups first
+        std::vector<int32_t> gorder(members.size());
+        std::iota(gorder.begin(), gorder.end(), 0);
+        std::stable_sort(gorder.begin(), gorder.end(), [&](int32_t a, int32_t b) { return gops[a].size() > gops[b].size(); });
+        hp.grp_member_off.push_back(0);
+        hp.grp_chunk_off.push_back(0);
+        hp.chk_blk_off.push_back(0);
+        for (int32_t g : gorder) {
+            for (int32_t te : members[g]) hp.grp_members.push_back(te);
+            hp.grp_member_off.push_back((int32_t)hp.grp_members.size());
+            auto& ops = gops[g];
+            // sources grouped by their father: a chunk then covers about one father's sons
+            std::stable_sort(ops.begin(), ops.end(), [](const Op& a, const Op& b) {
+                if (a.src_parent != b.src_parent) return a.src_parent < b.src_parent;
+                if (a.src != b.src) return a.src < b.src;
+                return a.member < b.member;
+            });
+            size_t i = 0;
+            while (i < ops.size()) {
+                std::vector<int32_t> specs, srcs;
+                std::vector<Op> chunk;
+                while (i < ops.size()) {
+                    const Op& o = ops[i];
+                    const bool new_sp = std::find(specs.begin(), specs.end(), o.spec) == specs.end();
+                    const bool new_src = std::find(srcs.begin(), srcs.end(), o.src) == srcs.end();
+                    const int need = (int)specs.size() + (int)srcs.size() + (new_sp ? 1 : 0) + (new_src ? 1 : 0);
+                    if (!chunk.empty() && need > max_blocks) break;
+                    if (new_sp) specs.push_back(o.spec);
+                    if (new_src) srcs.push_back(o.src);
+                    chunk.push_back(o);
+                    ++i;
+                }
+                const int32_t nsp = (int32_t)specs.size();
+                hp.chk_nspec.push_back(nsp);
+                hp.chk_blk.insert(hp.chk_blk.end(), specs.begin(), specs.end());
+                hp.chk_blk.insert(hp.chk_blk.end(), srcs.begin(), srcs.end());
+                hp.chk_blk_off.push_back((int32_t)hp.chk_blk.size());
+                std::stable_sort(chunk.begin(), chunk.end(), [](const Op& a, const Op& b) { return a.member < b.member; });
+                int32_t base = (int32_t)hp.chk_op.size();
+                size_t k = 0;
+                for (int m = 0; m < 8; ++m) {
+                    hp.chk_op_off.push_back(base + (int32_t)k);
+                    while (k < chunk.size() && chunk[k].member == m) {
+                        const Op& o = chunk[k];
+                        const int32_t sb = (int32_t)(std::find(specs.begin(), specs.end(), o.spec) - specs.begin());
+                        const int32_t mb = nsp + (int32_t)(std::find(srcs.begin(), srcs.end(), o.src) - srcs.begin());
+                        hp.chk_op.push_back(sb | (mb << 8) | (o.code << 16));
+                        ++k;
+                    }
+                }
+                hp.chk_op_off.push_back(base + (int32_t)k);
+            }
+            hp.grp_chunk_off.push_back((int32_t)hp.chk_nspec.size());
         }
     }
 

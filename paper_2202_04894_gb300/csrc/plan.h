@@ -99,8 +99,18 @@ struct HostPlan {
     // M2F: multipole ids that are M2L sources, and inverse map
     std::vector<int32_t> m2f_list, mhat_of_m;
 
-    // M2L CSR over target local expansions
-    std::vector<int32_t> m2l_tgt, m2l_off, m2l_src, m2l_spec;
+    // M2L work schedule.  A group is the set of sibling target expansions that
+    // share a father cell and a direction (at most 8 members).  Its pairs are
+    // cut into chunks; a chunk names the distinct blocks it needs (canonical
+    // spectra, then Fourier multipoles: one TMA stage) and its pair operations,
+    // sorted by member.  Groups are ordered by work, heaviest first.
+    std::vector<int32_t> grp_member_off, grp_members;   // CSR: group -> local expansion ids
+    std::vector<int32_t> grp_chunk_off;                 // CSR: group -> chunks
+    std::vector<int32_t> chk_blk_off, chk_nspec;        // CSR: chunk -> blocks; spectra first
+    std::vector<int32_t> chk_blk;                       // spectrum id or Fourier-multipole slot
+    std::vector<int32_t> chk_op_off;                    // 9 per chunk: op ranges of members 0..7, end
+    std::vector<int32_t> chk_op;                        // spec_blk | mhat_blk << 8 | code << 16
+    int32_t chk_max_blocks = 0;
 
     // M2M per level (parent level l): entries of 9 ints: parent exp, 8 child exps (-1)
     std::vector<std::vector<int32_t>> m2m_lvl;
