@@ -748,7 +748,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // and the block stops after its copies in flight have had a bounded chance to
 // land.  Needs N <= NX and N^2 <= TPM.
 template <typename T, int NX, int TPM>
-__global__ void __launch_bounds__(8 * TPM + 32) k_m2l_rows(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
+__global__ void __launch_bounds__(8 * TPM + 32, (sizeof(T) == 4 ? 3 : 1)) k_m2l_rows(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
                                                           typename Cplx<T>::type* __restrict__ L, int R, int S) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -832,9 +832,11 @@ __global__ void __launch_bounds__(8 * TPM + 32) k_m2l_rows(DevCommon c, DevTyped
                 if (active) {
                     const C* base = ring + (size_t)st * stage_elems;
                     const int* opoff = c.chk_op_off + 9 * (ch0 + k);
-                    const int o1 = opoff[m + 1];
-                    for (int o = opoff[m]; o < o1; ++o) {
-                        const int op = c.chk_op[o];
+                    const int o0 = opoff[m], o1 = opoff[m + 1];
+                    int op_next = o0 < o1 ? __ldg(&c.chk_op[o0]) : 0;
+                    for (int o = o0; o < o1; ++o) {
+                        const int op = op_next;
+                        if (o + 1 < o1) op_next = __ldg(&c.chk_op[o + 1]);   // in flight during this pair
                         const int code = op >> 16, pid = code >> 3;
                         const int s0 = stride[pid][0], s1 = stride[pid][1], s2 = stride[pid][2];
                         const C* gs = base + (size_t)(op & 255) * NFpad;
@@ -1271,6 +1273,8 @@ cudaError_t configure_kernels() {
     if ((e = cudaFuncSetAttribute(k_m2l<T, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<T, 4, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    // the row kernel's occupancy is set by shared memory: ask for the largest carveout
+    if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     return cudaSuccess;
 }
