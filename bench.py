@@ -39,6 +39,25 @@ SAMPLE_N = 16000          # cpu_baseline: ~10-20 s of single-core oracle work
 ORACLE_S_PER_POINT = 6e-4  # measured oracle cost on this recipe, used to size samples
 
 
+def _recorded_traffic_per_pair():
+    """DRAM bytes per M2L pair from the committed ncu summary, or None when the
+    kernels have changed since those counters were taken."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "m2l_rows_sphere300k_kD128_p4.md")
+    src = os.path.join(ROOT, "paper_2202_04894_gb300", "csrc", "kernels.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_pair:\s*([0-9.]+)", text)
+    h = re.search(r"kernels.cu sha256 \(first 16 hex\):\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != sha:
+        return None
+    return float(m.group(1))
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -273,20 +292,21 @@ def main():
     peak_gbs, peak_kind = _peaks()
     dominant = max(phase_avg, key=phase_avg.get)
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    if dominant == "p2p":
-        # P2P: 3 SFU operations (rsqrt, sin, cos) per interaction; 16 SFU results
-        # per clock per SM on 152 SMs
-        inter = info["p2p_interactions"] * R
-        achieved = inter / (phase_avg["p2p"] * 1e-3) / 1e9
-        peak = 152 * 16 / 3 * sm_max * 1e6 / 1e9
-        roof = {"kernel": "p2p", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginteractions/s",
-                "frac": achieved / peak, "traffic": None,
+    # P2P: 3 SFU operations (rsqrt, sin, cos) per interaction; 16 SFU results
+    # per clock per SM on 152 SMs
+    inter = info["p2p_interactions"] * R
+    p2p_achieved = inter / (phase_avg["p2p"] * 1e-3) / 1e9
+    p2p_peak = 152 * 16 / 3 * sm_max * 1e6 / 1e9
+    p2p_roof = {"kernel": "p2p", "bound": "alu", "achieved": p2p_achieved, "peak": p2p_peak,
+                "unit": "Ginteractions/s", "frac": p2p_achieved / p2p_peak, "traffic": None,
                 "peak_source": "SFU: 152 SMs x 16/clk / 3 per interaction at %.0f MHz" % sm_max}
-    else:
-        roof = {"kernel": "m2l", "bound": "hbm", "achieved": m2l_gbs, "peak": peak_gbs, "unit": "GB/s",
-                "frac": m2l_gbs / peak_gbs, "traffic": None, "peak_source": peak_kind}
-    m2l_roof = {"bound": "hbm", "achieved": m2l_gbs, "peak": peak_gbs, "unit": "GB/s", "frac": m2l_gbs / peak_gbs,
-                "algorithmic_bytes": m2l_bytes, "ms": phase_avg["m2l"], "peak_source": peak_kind}
+    per_pair = _recorded_traffic_per_pair()
+    m2l_traffic = None if per_pair is None or R != 1 else per_pair * info["n_m2l_pairs"]
+    m2l_roof = {"kernel": "m2l", "bound": "hbm", "achieved": m2l_gbs, "peak": peak_gbs, "unit": "GB/s",
+                "frac": m2l_gbs / peak_gbs, "traffic": m2l_traffic, "algorithmic_bytes": m2l_bytes,
+                "ms": phase_avg["m2l"], "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic_source": "profiles/m2l_rows_sphere300k_kD128_p4.md, DRAM bytes per pair x pairs"}
+    roof = p2p_roof if dominant == "p2p" else m2l_roof
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -304,7 +324,7 @@ def main():
                 "config": {"workload": args.workload, "points": len(X), "kappa_d": W_["kappa_d"], "order": order,
                            "leaf": leaf, "nrhs": R, "distribution": W_["kind"], "l2": "flushed (512 MB write) before each step",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roof, "m2l_roofline": m2l_roof,
+                "roofline": roof, "m2l_roofline": m2l_roof, "p2p_roofline": p2p_roof,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(X) * R * csz,
                         "d2h_bytes_per_step": len(X) * R * csz, "ms_per_step": statistics.mean(e2e_ms)},
