@@ -290,7 +290,8 @@ def main():
     m2l_bytes = (info["n_m2l_pairs"] * R * csz * NF + info["n_spectra"] * csz * NF)
     m2l_gbs = m2l_bytes / (phase_avg["m2l"] * 1e-3) / 1e9
     peak_gbs, peak_kind = _peaks()
-    dominant = max(phase_avg, key=phase_avg.get)
+    kernel_phases = {k: v for k, v in phase_avg.items() if k not in ("total", "join_wait")}
+    dominant = max(kernel_phases, key=kernel_phases.get)
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     # P2P: 3 SFU operations (rsqrt, sin, cos) per interaction; 16 SFU results
     # per clock per SM on 152 SMs

@@ -366,69 +366,126 @@ __global__ void __launch_bounds__(128) k_p2p_reduce(DevCommon c, const C* __rest
 }
 
 // ------------------------------------------------------------------ P2M
+// The plane wave of S_a^u separates: exp(i kappa <y_a - y, u>) = P_u(a) conj(E_u(y))
+// with E_u(y) = exp(i kappa <y - c, u>) (c the cell centre) and P_u(a) the
+// tabulated node factors of the direction's slot, so
+//   M_u[a] = P_u(a) * sum_y S_a(y_hat) (q(y) conj(E_u(y))),
+// one phase per (particle, direction) and a real-basis contraction.
+// e^{2 pi i t} for a phase given in turns, reduced exactly to [-1/2, 1/2].
+__device__ __forceinline__ void turns_sincos(float t, float* s, float* c) {
+    t -= __fadd_rn(__fadd_rn(t, 12582912.f), -12582912.f);
+    __sincosf(6.28318530717958647692f * t, s, c);
+}
+__device__ __forceinline__ void turns_sincos(double t, double* s, double* c) {
+    t -= rint(t);
+    sincospi(2.0 * t, s, c);
+}
+
+constexpr int kP2MChunk = 64;     // particles staged at a time
+constexpr int kMaxExp = 32;       // expansions handled per pass
+
 template <typename T, int RB>
 __global__ void __launch_bounds__(128) k_p2m(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ qs,
-                                             typename Cplx<T>::type* __restrict__ M, int R, int rb0) {
+                                             typename Cplx<T>::type* __restrict__ M, int R, int rb0, int epass) {
     using C = typename Cplx<T>::type;
-    __shared__ C phi[32][3][8];
-    __shared__ C sq[RB][32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // [kP2MChunk][3][p] Lagrange values, then [RB][epass][kP2MChunk] modified charges
+    T* lag = reinterpret_cast<T*>(smem_raw);
+    const int p = c.p, P3 = c.P3;
+    C* qm = reinterpret_cast<C*>(smem_raw + (((size_t)kP2MChunk * 3 * p * sizeof(T) + 15) / 16) * 16);
     const int cell = c.p2m_cells[blockIdx.x];
     const int b = c.cs_beg[cell], e = c.cs_end[cell];
     const double side = c.level_side[c.cs_level[cell]];
-    const int p = c.p, P3 = c.P3;
     const double h = side / (p - 1);
     const double cor[3] = {c.cs_corner[3 * cell], c.cs_corner[3 * cell + 1], c.cs_corner[3 * cell + 2]};
     const int nr = min(RB, R - rb0);
-    const T kap = (T)c.kappa;
-    for (int ex = c.m_first[cell]; ex < c.m_first[cell] + c.m_count[cell]; ++ex) {
-        const int slot = c.m_slot[ex];
-        T u[3] = {0, 0, 0};
-        if (slot >= 0) { u[0] = (T)c.slot_u[3 * slot]; u[1] = (T)c.slot_u[3 * slot + 1]; u[2] = (T)c.slot_u[3 * slot + 2]; }
-        C acc[4][RB];
+    const T k2pi = (T)(c.kappa * kInv2Pi);
+    const int ex0 = c.m_first[cell], nex = c.m_count[cell];
+    for (int e0 = 0; e0 < nex; e0 += epass) {
+        const int ne = min(epass, nex - e0);
+        // outputs of this thread: (expansion, node) pairs o = threadIdx.x + 128 v (ne * P3 <= 16 * 128)
+        const int nout = ne * P3;
+        C acc[16][RB];      // up to 16 outputs per thread (ne * P3 <= 2048)
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
+        for (int v = 0; v < 16; ++v)
 #pragma unroll
             for (int r = 0; r < RB; ++r) acc[v][r] = czero<C>();
-        for (int j0 = b; j0 < e; j0 += 32) {
-            const int nj = min(32, e - j0);
+        for (int j0 = b; j0 < e; j0 += kP2MChunk) {
+            const int nj = min(kP2MChunk, e - j0);
             __syncthreads();
             for (int idx = threadIdx.x; idx < nj * 3 * p; idx += blockDim.x) {
                 const int j = idx / (3 * p), rem = idx - j * 3 * p, ax = rem / p, m = rem - ax * p;
                 const double d = c.Ys[3 * (int64_t)(j0 + j) + ax] - cor[ax];
-                const T lag = lagrange<T>(p, m, (T)(d / h));
-                C val = mk(lag, (T)0);
-                if (slot >= 0) {
-                    T sn, cs;
-                    sincos_t(kap * (T)((double)m * h - d) * u[ax], &sn, &cs);
-                    val = mk(lag * cs, lag * sn);
-                }
-                phi[j][ax][m] = val;
+                lag[idx] = lagrange<T>(p, m, (T)(d / h));
+                (void)j;
             }
-            if (threadIdx.x < nj * RB) {
-                const int j = threadIdx.x % nj, r = threadIdx.x / nj;
-                sq[r][j] = r < nr ? qs[(int64_t)(rb0 + r) * c.ny + j0 + j] : czero<C>();
+            for (int idx = threadIdx.x; idx < ne * nj; idx += blockDim.x) {
+                const int ee = idx / nj, j = idx - ee * nj;
+                const int slot = c.m_slot[ex0 + e0 + ee];
+                C ph = mk((T)1, (T)0);
+                if (slot >= 0) {
+                    T arg = 0;
+                    for (int ax = 0; ax < 3; ++ax)
+                        arg += (T)(c.Ys[3 * (int64_t)(j0 + j) + ax] - cor[ax] - 0.5 * side) * (T)c.slot_u[3 * slot + ax];
+                    T sn, cs;
+                    turns_sincos(arg * k2pi, &sn, &cs);
+                    ph = mk(cs, -sn);                                  // conj(E_u(y))
+                }
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const C q = r < nr ? qs[(int64_t)(rb0 + r) * c.ny + j0 + j] : czero<C>();
+                    qm[((size_t)r * epass + ee) * kP2MChunk + j] = cmul(q, ph);
+                }
             }
             __syncthreads();
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int a = threadIdx.x + v * 128;
-                if (a < P3) {
+            for (int v = 0; v < 16; ++v) {
+                const int o = threadIdx.x + v * 128;
+                if (o < nout) {
+                    const int ee = o / P3, a = o - ee * P3;
                     const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
                     for (int j = 0; j < nj; ++j) {
-                        const C f = cmul(cmul(phi[j][0][a0], phi[j][1][a1]), phi[j][2][a2]);
+                        const T* lj = lag + j * 3 * p;
+                        const T w = lj[a0] * lj[p + a1] * lj[2 * p + a2];
 #pragma unroll
-                        for (int r = 0; r < RB; ++r) cfma(acc[v][r], f, sq[r][j]);
+                        for (int r = 0; r < RB; ++r) {
+                            const C q = qm[((size_t)r * epass + ee) * kP2MChunk + j];
+                            acc[v][r].x = fma(w, q.x, acc[v][r].x);
+                            acc[v][r].y = fma(w, q.y, acc[v][r].y);
+                        }
                     }
                 }
             }
         }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int a = threadIdx.x + v * 128;
-            if (a < P3)
-                for (int r = 0; r < nr; ++r) M[((int64_t)ex * R + rb0 + r) * P3 + a] = acc[v][r];
+        for (int v = 0; v < 16; ++v) {
+            const int o = threadIdx.x + v * 128;
+            if (o < nout) {
+                const int ee = o / P3, a = o - ee * P3;
+                const int ex = ex0 + e0 + ee;
+                const int slot = c.m_slot[ex];
+                C ph = mk((T)1, (T)0);
+                if (slot >= 0) {
+                    const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
+                    const C* P = t.slot_P + (int64_t)slot * 3 * p;
+                    ph = cmul(cmul(P[a0], P[p + a1]), P[2 * p + a2]);
+                }
+                for (int r = 0; r < nr; ++r) M[((int64_t)ex * R + rb0 + r) * P3 + a] = cmul(acc[v][r], ph);
+            }
         }
     }
+}
+
+// Expansions per pass of k_p2m: at most 16 outputs per thread and 64 KB of modified charges.
+__host__ int p2m_epass(int P3, int RB, size_t creal) {
+    int ep = kMaxExp;
+    ep = ep < (16 * 128) / P3 ? ep : (16 * 128) / P3;
+    const int by_smem = (int)((64 * 1024) / ((size_t)RB * kP2MChunk * 2 * creal));
+    ep = ep < by_smem ? ep : by_smem;
+    return ep < 1 ? 1 : ep;
+}
+__host__ size_t p2m_smem(int p, int RB, int epass, size_t creal) {
+    return ((size_t)kP2MChunk * 3 * p * creal + 15) / 16 * 16 + (size_t)RB * epass * kP2MChunk * 2 * creal;
 }
 
 // ------------------------------------------------------------------ M2M
@@ -997,12 +1054,18 @@ __global__ void __launch_bounds__(128) k_l2l(DevCommon c, DevTyped<T> t, const i
 }
 
 // ------------------------------------------------------------------ L2P
+// p(x) += sum_u E_u(x) sum_a S_a(x_hat) conj(P_u(a)) L_u[a], E_u(x) = exp(i kappa <x - c, u>):
+// the leaf's expansions are pre-scaled by conj(P_u) into shared memory, each
+// (particle, expansion) then costs one phase and a real-basis contraction.
+// The leaf's n_t targets are spread over 128 threads as targets x
+// expansion-splits; partial sums are reduced over the splits in order.
 template <typename T, int RB>
 __global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ L,
-                                             typename Cplx<T>::type* __restrict__ ps, int R, int rb0) {
+                                             typename Cplx<T>::type* __restrict__ ps, int R, int rb0, int epass) {
     using C = typename Cplx<T>::type;
-    extern __shared__ unsigned char smem_raw[];
-    C* Ls = reinterpret_cast<C*>(smem_raw);  // [RB][P3]
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* Ls = reinterpret_cast<C*>(smem_raw);            // [RB][epass][P3]
+    C* red = Ls + (size_t)RB * epass * c.P3;            // [RB][128]
     const int cell = c.l2p_cells[blockIdx.x];
     const int b = c.ct_beg[cell], e = c.ct_end[cell];
     const double side = c.level_side[c.ct_level[cell]];
@@ -1010,63 +1073,95 @@ __global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const t
     const double h = side / (p - 1);
     const double cor[3] = {c.ct_corner[3 * cell], c.ct_corner[3 * cell + 1], c.ct_corner[3 * cell + 2]};
     const int nr = min(RB, R - rb0);
-    const T kap = (T)c.kappa;
-    for (int j0 = b; j0 < e; j0 += blockDim.x) {
-        const int j = j0 + threadIdx.x;
-        const bool valid = j < e;
-        double d[3] = {0, 0, 0};
-        if (valid)
-            for (int ax = 0; ax < 3; ++ax) d[ax] = c.Xs[3 * (int64_t)j + ax] - cor[ax];
-        T lag[3][8];
-        for (int ax = 0; ax < 3; ++ax)
-            for (int m = 0; m < p; ++m) lag[ax][m] = lagrange<T>(p, m, (T)(d[ax] / h));
+    const T k2pi = (T)(c.kappa * kInv2Pi);
+    const int ex0 = c.l_first[cell], nex = c.l_count[cell];
+    for (int t0 = b; t0 < e; t0 += 128) {
+        const int nt = min(128, e - t0);
+        const int splits = 128 / nt;
+        const int ti = threadIdx.x % nt, sj = threadIdx.x / nt;
+        const bool active = sj < splits;
+        const int j = t0 + ti;
+        T lag[3][8], dc[3];
+        for (int ax = 0; ax < 3; ++ax) {
+            const double d = active ? c.Xs[3 * (int64_t)j + ax] - cor[ax] : 0.0;
+            dc[ax] = (T)(d - 0.5 * side);
+            for (int m = 0; m < p; ++m) lag[ax][m] = lagrange<T>(p, m, (T)(d / h));
+        }
         C acc[RB];
 #pragma unroll
         for (int r = 0; r < RB; ++r) acc[r] = czero<C>();
-        for (int ex = c.l_first[cell]; ex < c.l_first[cell] + c.l_count[cell]; ++ex) {
+        for (int e0 = 0; e0 < nex; e0 += epass) {
+            const int ne = min(epass, nex - e0);
             __syncthreads();
-            for (int i = threadIdx.x; i < nr * P3; i += blockDim.x) {
-                const int r = i / P3, a = i - r * P3;
-                Ls[r * P3 + a] = L[((int64_t)ex * R + rb0 + r) * P3 + a];
-            }
-            __syncthreads();
-            const int slot = c.l_slot[ex];
-            C ph[3][8];
-            for (int ax = 0; ax < 3; ++ax) {
-                const T u = slot >= 0 ? (T)c.slot_u[3 * slot + ax] : (T)0;
-                for (int m = 0; m < p; ++m) {
-                    if (slot >= 0) {
-                        T sn, cs;
-                        sincos_t(kap * (T)(d[ax] - (double)m * h) * u, &sn, &cs);
-                        ph[ax][m] = mk(lag[ax][m] * cs, lag[ax][m] * sn);
-                    } else {
-                        ph[ax][m] = mk(lag[ax][m], (T)0);
-                    }
+            for (int i = threadIdx.x; i < nr * ne * P3; i += blockDim.x) {
+                const int r = i / (ne * P3), rem = i - r * ne * P3, ee = rem / P3, a = rem - ee * P3;
+                const int ex = ex0 + e0 + ee;
+                const int slot = c.l_slot[ex];
+                C v = L[((int64_t)ex * R + rb0 + r) * P3 + a];
+                if (slot >= 0) {
+                    const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
+                    const C* P = t.slot_P + (int64_t)slot * 3 * p;
+                    v = cmulc(v, cmul(cmul(P[a0], P[p + a1]), P[2 * p + a2]));
                 }
+                Ls[((size_t)r * epass + ee) * P3 + a] = v;
             }
-            if (valid) {
-                for (int r = 0; r < nr; ++r) {
-                    const C* Lr = Ls + r * P3;
-                    C sz = czero<C>();
-                    for (int a2 = 0; a2 < p; ++a2) {
-                        C sy = czero<C>();
-                        for (int a1 = 0; a1 < p; ++a1) {
-                            C sx = czero<C>();
-                            for (int a0 = 0; a0 < p; ++a0) cfma(sx, Lr[(a2 * p + a1) * p + a0], ph[0][a0]);
-                            cfma(sy, sx, ph[1][a1]);
-                        }
-                        cfma(sz, sy, ph[2][a2]);
+            __syncthreads();
+            if (active) {
+                for (int ee = sj; ee < ne; ee += splits) {
+                    const int slot = c.l_slot[ex0 + e0 + ee];
+                    C E = mk((T)1, (T)0);
+                    if (slot >= 0) {
+                        const T arg = dc[0] * (T)c.slot_u[3 * slot] + dc[1] * (T)c.slot_u[3 * slot + 1] +
+                                      dc[2] * (T)c.slot_u[3 * slot + 2];
+                        T sn, cs;
+                        turns_sincos(arg * k2pi, &sn, &cs);
+                        E = mk(cs, sn);
                     }
-                    acc[r] = cadd(acc[r], sz);
+                    for (int r = 0; r < nr; ++r) {
+                        const C* Lr = Ls + ((size_t)r * epass + ee) * P3;
+                        C sz = czero<C>();
+                        for (int a2 = 0; a2 < p; ++a2) {
+                            C sy = czero<C>();
+                            for (int a1 = 0; a1 < p; ++a1) {
+                                C sx = czero<C>();
+                                const C* row = Lr + (a2 * p + a1) * p;
+                                for (int a0 = 0; a0 < p; ++a0) {
+                                    sx.x = fma(lag[0][a0], row[a0].x, sx.x);
+                                    sx.y = fma(lag[0][a0], row[a0].y, sx.y);
+                                }
+                                sy.x = fma(lag[1][a1], sx.x, sy.x);
+                                sy.y = fma(lag[1][a1], sx.y, sy.y);
+                            }
+                            sz.x = fma(lag[2][a2], sy.x, sz.x);
+                            sz.y = fma(lag[2][a2], sy.y, sz.y);
+                        }
+                        cfma(acc[r], E, sz);
+                    }
                 }
             }
         }
-        if (valid)
+#pragma unroll
+        for (int r = 0; r < RB; ++r) red[r * 128 + threadIdx.x] = acc[r];
+        __syncthreads();
+        if (active && sj == 0)
             for (int r = 0; r < nr; ++r) {
+                C s = red[r * 128 + ti];
+                for (int q = 1; q < splits; ++q) s = cadd(s, red[r * 128 + ti + q * nt]);
                 C* dst = ps + (int64_t)(rb0 + r) * c.nx + j;
-                *dst = cadd(*dst, acc[r]);
+                *dst = cadd(*dst, s);
             }
+        __syncthreads();
     }
+}
+
+// Expansions per pass of k_l2p: at most 96 KB of pre-scaled local expansions.
+__host__ int l2p_epass(int P3, int RB, size_t ccplx) {
+    const int by_smem = (int)((96 * 1024) / ((size_t)RB * P3 * ccplx));
+    int ep = kMaxExp < by_smem ? kMaxExp : by_smem;
+    return ep < 1 ? 1 : ep;
+}
+__host__ size_t l2p_smem(int P3, int RB, int epass, size_t ccplx) {
+    return ((size_t)RB * epass * P3 + (size_t)RB * 128) * ccplx;
 }
 
 // ------------------------------------------------------------------ spectra (float64)
@@ -1194,8 +1289,11 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     // upward pass
     for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
         if (c.n_p2m == 0) break;
-        if (R == 1) k_p2m<T, 1><<<(unsigned)c.n_p2m, 128, 0, stream>>>(c, t, w.qs, w.M, R, rb0);
-        else k_p2m<T, 4><<<(unsigned)c.n_p2m, 128, 0, stream>>>(c, t, w.qs, w.M, R, rb0);
+        const int rb = R == 1 ? 1 : 4;
+        const int ep = p2m_epass(c.P3, rb, sizeof(T));
+        const size_t sm = p2m_smem(c.p, rb, ep, sizeof(T));
+        if (R == 1) k_p2m<T, 1><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+        else k_p2m<T, 4><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -1248,9 +1346,10 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
         if (c.n_l2p == 0) break;
         const int rb = R == 1 ? 1 : 4;
-        const size_t sm = (size_t)rb * c.P3 * sizeof(C);
-        if (R == 1) k_l2p<T, 1><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0);
-        else k_l2p<T, 4><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0);
+        const int ep = l2p_epass(c.P3, rb, sizeof(C));
+        const size_t sm = l2p_smem(c.P3, rb, ep, sizeof(C));
+        if (R == 1) k_l2p<T, 1><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+        else k_l2p<T, 4><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -1276,6 +1375,10 @@ cudaError_t configure_kernels() {
     // the row kernel's occupancy is set by shared memory: ask for the largest carveout
     if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_p2m<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_p2m<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_l2p<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_l2p<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
