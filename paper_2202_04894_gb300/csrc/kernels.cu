@@ -384,14 +384,14 @@ __device__ __forceinline__ void turns_sincos(double t, double* s, double* c) {
 constexpr int kP2MChunk = 64;     // particles staged at a time
 constexpr int kMaxExp = 32;       // expansions handled per pass
 
-template <typename T, int RB>
+template <typename T, int RB, int PC = 0>
 __global__ void __launch_bounds__(128) k_p2m(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ qs,
                                              typename Cplx<T>::type* __restrict__ M, int R, int rb0, int epass) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // [kP2MChunk][3][p] Lagrange values, then [RB][epass][kP2MChunk] modified charges
     T* lag = reinterpret_cast<T*>(smem_raw);
-    const int p = c.p, P3 = c.P3;
+    const int p = PC ? PC : c.p, P3 = p * p * p;
     C* qm = reinterpret_cast<C*>(smem_raw + (((size_t)kP2MChunk * 3 * p * sizeof(T) + 15) / 16) * 16);
     const int cell = c.p2m_cells[blockIdx.x];
     const int b = c.cs_beg[cell], e = c.cs_end[cell];
@@ -488,31 +488,40 @@ __host__ size_t p2m_smem(int p, int RB, int epass, size_t creal) {
     return ((size_t)kP2MChunk * 3 * p * creal + 15) / 16 * 16 + (size_t)RB * epass * kP2MChunk * 2 * creal;
 }
 
+// ------------------------------------------------------------------ warp-per-item helpers
+// M2M, L2L and M2F work on one small expansion at a time: one warp per item,
+// synchronised with __syncwarp only; blocks hold `wpb` independent warps.
 // ------------------------------------------------------------------ M2M
-// One block per father expansion (entry: father id, 8 son ids or -1).
-template <typename T>
-__global__ void __launch_bounds__(128) k_m2m(DevCommon c, DevTyped<T> t, const int32_t* __restrict__ list,
+// One warp per father expansion (entry: father id, 8 son ids or -1):
+//   M_f^v[a] = P_v(a) sum_sons sum_b T_o[a, b] conj(Q_v,o(b)) M_son[b],
+// T_o the tensor product of the 1-D son->father matrices, applied as three
+// 1-D passes (Sec. 5.2.1).
+template <typename T, int PC = 0>
+__global__ void __launch_bounds__(256) k_m2m(DevCommon c, DevTyped<T> t, const int32_t* __restrict__ list, int64_t n,
                                              typename Cplx<T>::type* __restrict__ M, int R) {
     using C = typename Cplx<T>::type;
-    extern __shared__ unsigned char smem_raw[];
-    C* A = reinterpret_cast<C*>(smem_raw);
-    C* B = A + c.P3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = PC ? PC : c.p, P3 = p * p * p;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ T m1s[2 * 8 * 8];
-    __shared__ C Ps[3 * 8], Qs[3 * 2 * 8];
-    const int32_t* ent = list + 9 * (int64_t)blockIdx.x;
+    for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) m1s[i] = t.m1[i];
+    __syncthreads();
+    const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (item >= n) return;
+    C* A = reinterpret_cast<C*>(smem_raw) + (size_t)warp * (2 * P3 + 72);
+    C* B = A + P3;
+    C* Ps = B + P3;          // [3][p]
+    C* Qs = Ps + 24;         // [3][2][p]
+    const int32_t* ent = list + 9 * item;
     const int ep = ent[0];
     const int slot = c.m_slot[ep];
-    const int p = c.p, P3 = c.P3;
-    for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) m1s[i] = t.m1[i];
-    for (int i = threadIdx.x; i < 3 * p; i += blockDim.x)
-        Ps[i] = slot >= 0 ? t.slot_P[(int64_t)slot * 3 * p + i] : mk((T)1, (T)0);
-    for (int i = threadIdx.x; i < 6 * p; i += blockDim.x)
-        Qs[i] = slot >= 0 ? t.slot_Q[(int64_t)slot * 6 * p + i] : mk((T)1, (T)0);
-    __syncthreads();
+    for (int i = lane; i < 3 * p; i += 32) Ps[i] = slot >= 0 ? t.slot_P[(int64_t)slot * 3 * p + i] : mk((T)1, (T)0);
+    for (int i = lane; i < 6 * p; i += 32) Qs[i] = slot >= 0 ? t.slot_Q[(int64_t)slot * 6 * p + i] : mk((T)1, (T)0);
+    __syncwarp();
     for (int r = 0; r < R; ++r) {
-        C acc[4];
+        C acc[16];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] = czero<C>();
+        for (int v = 0; v < 16; ++v) acc[v] = czero<C>();
         for (int o = 0; o < 8; ++o) {
             const int ce = ent[1 + o];
             if (ce < 0) continue;
@@ -520,29 +529,29 @@ __global__ void __launch_bounds__(128) k_m2m(DevCommon c, DevTyped<T> t, const i
             const T* mx = m1s + ox * p * p;
             const T* my = m1s + oy * p * p;
             const T* mz = m1s + oz * p * p;
-            for (int a = threadIdx.x; a < P3; a += blockDim.x) {
+            for (int a = lane; a < P3; a += 32) {
                 const int b0 = a % p, b1 = (a / p) % p, b2 = a / (p * p);
                 const C q = cmul(cmul(Qs[(0 * 2 + ox) * p + b0], Qs[(1 * 2 + oy) * p + b1]), Qs[(2 * 2 + oz) * p + b2]);
                 A[a] = cmulc(M[((int64_t)ce * R + r) * P3 + a], q);
             }
-            __syncthreads();
-            for (int a = threadIdx.x; a < P3; a += blockDim.x) {  // x: (bz, by, ax)
+            __syncwarp();
+            for (int a = lane; a < P3; a += 32) {  // x: (bz, by, ax)
                 const int a0 = a % p, rest = a - a0;
                 C s = czero<C>();
                 for (int k = 0; k < p; ++k) { C v = A[rest + k]; T m = mx[a0 * p + k]; s.x += m * v.x; s.y += m * v.y; }
                 B[a] = s;
             }
-            __syncthreads();
-            for (int a = threadIdx.x; a < P3; a += blockDim.x) {  // y: (bz, ay, ax)
+            __syncwarp();
+            for (int a = lane; a < P3; a += 32) {  // y: (bz, ay, ax)
                 const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
                 C s = czero<C>();
                 for (int k = 0; k < p; ++k) { C v = B[(a2 * p + k) * p + a0]; T m = my[a1 * p + k]; s.x += m * v.x; s.y += m * v.y; }
                 A[a] = s;
             }
-            __syncthreads();
+            __syncwarp();
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {  // z: (az, ay, ax), accumulate
-                const int a = threadIdx.x + v * 128;
+            for (int v = 0; v < 16; ++v) {  // z: (az, ay, ax), accumulate
+                const int a = lane + v * 32;
                 if (a < P3) {
                     const int a01 = a % (p * p), a2 = a / (p * p);
                     C s = acc[v];
@@ -550,11 +559,11 @@ __global__ void __launch_bounds__(128) k_m2m(DevCommon c, DevTyped<T> t, const i
                     acc[v] = s;
                 }
             }
-            __syncthreads();
+            __syncwarp();
         }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int a = threadIdx.x + v * 128;
+        for (int v = 0; v < 16; ++v) {
+            const int a = lane + v * 32;
             if (a < P3) {
                 const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
                 const C ph = cmul(cmul(Ps[0 * p + a0], Ps[1 * p + a1]), Ps[2 * p + a2]);
@@ -565,46 +574,58 @@ __global__ void __launch_bounds__(128) k_m2m(DevCommon c, DevTyped<T> t, const i
 }
 
 // ------------------------------------------------------------------ M2F
-template <typename T>
-__global__ void __launch_bounds__(128) k_m2f(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ M,
+// One warp per Fourier multipole: zero-pad and forward DFT (F chi, Sec. 4.1.1),
+// pruned to the p non-zero inputs per line.
+template <typename T, int PC = 0, int NC = 0>
+__global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ M,
                                              typename Cplx<T>::type* __restrict__ Mhat, int R) {
     using C = typename Cplx<T>::type;
-    extern __shared__ unsigned char smem_raw[];
-    const int p = c.p, N = c.N, P3 = c.P3, NF = c.NF, NFpad = c.NFpad;
-    C* A = reinterpret_cast<C*>(smem_raw);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = PC ? PC : c.p, N = NC ? NC : c.N, P3 = p * p * p, NF = N * N * N, NFpad = c.NFpad;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ C tws[16];
+    if (threadIdx.x < N) tws[threadIdx.x] = mk(t.tw[threadIdx.x].x, -t.tw[threadIdx.x].y);   // e^{-2 pi i m / N}
+    __syncthreads();
+    const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (item >= c.n_m2f) return;
+    C* A = reinterpret_cast<C*>(smem_raw) + (size_t)warp * (P3 + p * p * N + p * N * N);
     C* B = A + P3;              // [bz][by][xi_x]   p*p*N
     C* D = B + p * p * N;       // [bz][xi_y][xi_x] p*N*N
-    __shared__ C tws[16];
-    const int e = c.m2f_list[blockIdx.x];
-    if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
+    const int e = c.m2f_list[item];
     for (int r = 0; r < R; ++r) {
-        __syncthreads();
-        for (int a = threadIdx.x; a < P3; a += blockDim.x) A[a] = M[((int64_t)e * R + r) * P3 + a];
-        __syncthreads();
-        for (int i = threadIdx.x; i < p * p * N; i += blockDim.x) {
+        for (int a = lane; a < P3; a += 32) A[a] = M[((int64_t)e * R + r) * P3 + a];
+        __syncwarp();
+        for (int i = lane; i < p * p * N; i += 32) {
             const int xx = i % N, rest = i / N;  // rest = bz*p + by
             C s = czero<C>();
-            for (int b = 0; b < p; ++b) cfma(s, A[rest * p + b], mk(tws[(xx * b) % N].x, -tws[(xx * b) % N].y));
+            for (int b = 0; b < p; ++b) cfma(s, A[rest * p + b], tws[(xx * b) % N]);
             B[i] = s;
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < p * N * N; i += blockDim.x) {
+        __syncwarp();
+        for (int i = lane; i < p * N * N; i += 32) {
             const int xx = i % N, yy = (i / N) % N, bz = i / (N * N);
             C s = czero<C>();
-            for (int b = 0; b < p; ++b) cfma(s, B[(bz * p + b) * N + xx], mk(tws[(yy * b) % N].x, -tws[(yy * b) % N].y));
+            for (int b = 0; b < p; ++b) cfma(s, B[(bz * p + b) * N + xx], tws[(yy * b) % N]);
             D[i] = s;
         }
-        __syncthreads();
-        C* out = Mhat + ((int64_t)blockIdx.x * R + r) * NFpad;
-        for (int i = threadIdx.x; i < NFpad; i += blockDim.x) {
+        __syncwarp();
+        C* out = Mhat + ((int64_t)item * R + r) * NFpad;
+        for (int i = lane; i < NFpad; i += 32) {
             C s = czero<C>();
             if (i < NF) {
                 const int xy = i % (N * N), zz = i / (N * N);
-                for (int b = 0; b < p; ++b) cfma(s, D[b * N * N + xy], mk(tws[(zz * b) % N].x, -tws[(zz * b) % N].y));
+                for (int b = 0; b < p; ++b) cfma(s, D[b * N * N + xy], tws[(zz * b) % N]);
             }
             out[i] = s;
         }
+        __syncwarp();
     }
+}
+
+// Warps per block for the warp-per-item kernels, given the shared bytes of one warp.
+__host__ int warps_per_block(size_t per_warp) {
+    int w = (int)((180 * 1024) / (per_warp ? per_warp : 1));
+    return w < 1 ? 1 : (w > 8 ? 8 : w);
 }
 
 // ------------------------------------------------------------------ M2L (+F2L)
@@ -804,12 +825,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // Every wait is bounded; a wait that gives up raises the plan's error flag
 // and the block stops after its copies in flight have had a bounded chance to
 // land.  Needs N <= NX and N^2 <= TPM.
-template <typename T, int NX, int TPM>
+template <typename T, int NX, int TPM, int PC = 0, int NC = 0>
 __global__ void __launch_bounds__(8 * TPM + 32, (sizeof(T) == 4 ? 3 : 1)) k_m2l_rows(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
                                                           typename Cplx<T>::type* __restrict__ L, int R, int S) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int p = c.p, N = c.N, NF = c.NF, NFpad = c.NFpad, P3 = c.P3;
+    const int p = PC ? PC : c.p, N = NC ? NC : c.N, NF = N * N * N, NFpad = c.NFpad, P3 = p * p * p;
     const int NN = N * N;
     const uint32_t blk_bytes = (uint32_t)(NFpad * sizeof(C));
     C* ring = reinterpret_cast<C*>(smem_raw);
@@ -978,61 +999,65 @@ template <typename T> __host__ void m2l_shape(const DevCommon& c, int members, i
 }
 
 // ------------------------------------------------------------------ L2L
-// One block per son expansion (entry: son id, octant, first, count into the
-// list of father expansions feeding it).
-template <typename T>
-__global__ void __launch_bounds__(128) k_l2l(DevCommon c, DevTyped<T> t, const int32_t* __restrict__ list,
+// One warp per son expansion (entry: son id, octant, first, count into the
+// list of father expansions feeding it), the transpose of M2M:
+//   L_son[b] += sum_fathers Q_v,o(b) sum_a T_o[a, b] conj(P_v(a)) L_v[a].
+template <typename T, int PC = 0>
+__global__ void __launch_bounds__(256) k_l2l(DevCommon c, DevTyped<T> t, const int32_t* __restrict__ list, int64_t n,
                                              const int32_t* __restrict__ par, typename Cplx<T>::type* __restrict__ L, int R) {
     using C = typename Cplx<T>::type;
-    extern __shared__ unsigned char smem_raw[];
-    C* A = reinterpret_cast<C*>(smem_raw);
-    C* B = A + c.P3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = PC ? PC : c.p, P3 = p * p * p;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ T m1s[2 * 8 * 8];
-    __shared__ C Ps[3 * 8], Qs[3 * 2 * 8];
-    const int32_t* ent = list + 4 * (int64_t)blockIdx.x;
-    const int ec = ent[0], o = ent[1], first = ent[2], cnt = ent[3];
-    const int p = c.p, P3 = c.P3;
-    const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
     for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) m1s[i] = t.m1[i];
+    __syncthreads();
+    const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (item >= n) return;
+    C* A = reinterpret_cast<C*>(smem_raw) + (size_t)warp * (2 * P3 + 72);
+    C* B = A + P3;
+    C* Ps = B + P3;          // [3][p]
+    C* Qs = Ps + 24;         // [3][2][p]
+    const int32_t* ent = list + 4 * item;
+    const int ec = ent[0], o = ent[1], first = ent[2], cnt = ent[3];
+    const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
     const T* mx = m1s + ox * p * p;
     const T* my = m1s + oy * p * p;
     const T* mz = m1s + oz * p * p;
     for (int r = 0; r < R; ++r) {
-        C acc[4];
+        C acc[16];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] = czero<C>();
+        for (int v = 0; v < 16; ++v) acc[v] = czero<C>();
         for (int k = 0; k < cnt; ++k) {
             const int pe = par[first + k];
             const int slot = c.l_slot[pe];
-            __syncthreads();
-            for (int i = threadIdx.x; i < 3 * p; i += blockDim.x)
-                Ps[i] = slot >= 0 ? t.slot_P[(int64_t)slot * 3 * p + i] : mk((T)1, (T)0);
-            for (int i = threadIdx.x; i < 6 * p; i += blockDim.x)
-                Qs[i] = slot >= 0 ? t.slot_Q[(int64_t)slot * 6 * p + i] : mk((T)1, (T)0);
-            __syncthreads();
-            for (int a = threadIdx.x; a < P3; a += blockDim.x) {
+            __syncwarp();
+            for (int i = lane; i < 3 * p; i += 32) Ps[i] = slot >= 0 ? t.slot_P[(int64_t)slot * 3 * p + i] : mk((T)1, (T)0);
+            for (int i = lane; i < 6 * p; i += 32) Qs[i] = slot >= 0 ? t.slot_Q[(int64_t)slot * 6 * p + i] : mk((T)1, (T)0);
+            __syncwarp();
+            for (int a = lane; a < P3; a += 32) {
                 const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
                 const C ph = cmul(cmul(Ps[a0], Ps[p + a1]), Ps[2 * p + a2]);
                 A[a] = cmulc(L[((int64_t)pe * R + r) * P3 + a], ph);
             }
-            __syncthreads();
-            for (int b = threadIdx.x; b < P3; b += blockDim.x) {  // x: (az, ay, bx)
+            __syncwarp();
+            for (int b = lane; b < P3; b += 32) {  // x: (az, ay, bx)
                 const int b0 = b % p, rest = b - b0;
                 C s = czero<C>();
                 for (int q = 0; q < p; ++q) { C v = A[rest + q]; T m = mx[q * p + b0]; s.x += m * v.x; s.y += m * v.y; }
                 B[b] = s;
             }
-            __syncthreads();
-            for (int b = threadIdx.x; b < P3; b += blockDim.x) {  // y: (az, by, bx)
+            __syncwarp();
+            for (int b = lane; b < P3; b += 32) {  // y: (az, by, bx)
                 const int b0 = b % p, b1 = (b / p) % p, b2 = b / (p * p);
                 C s = czero<C>();
                 for (int q = 0; q < p; ++q) { C v = B[(b2 * p + q) * p + b0]; T m = my[q * p + b1]; s.x += m * v.x; s.y += m * v.y; }
                 A[b] = s;
             }
-            __syncthreads();
+            __syncwarp();
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {  // z: (bz, by, bx), times Q(v, o)
-                const int b = threadIdx.x + v * 128;
+            for (int v = 0; v < 16; ++v) {  // z: (bz, by, bx), times Q(v, o)
+                const int b = lane + v * 32;
                 if (b < P3) {
                     const int b0 = b % p, b1 = (b / p) % p, b01 = b % (p * p), b2 = b / (p * p);
                     C s = czero<C>();
@@ -1043,8 +1068,8 @@ __global__ void __launch_bounds__(128) k_l2l(DevCommon c, DevTyped<T> t, const i
             }
         }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int b = threadIdx.x + v * 128;
+        for (int v = 0; v < 16; ++v) {
+            const int b = lane + v * 32;
             if (b < P3) {
                 C* dst = L + ((int64_t)ec * R + r) * P3 + b;
                 *dst = cadd(*dst, acc[v]);
@@ -1059,7 +1084,7 @@ __global__ void __launch_bounds__(128) k_l2l(DevCommon c, DevTyped<T> t, const i
 // (particle, expansion) then costs one phase and a real-basis contraction.
 // The leaf's n_t targets are spread over 128 threads as targets x
 // expansion-splits; partial sums are reduced over the splits in order.
-template <typename T, int RB>
+template <typename T, int RB, int PC = 0>
 __global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ L,
                                              typename Cplx<T>::type* __restrict__ ps, int R, int rb0, int epass) {
     using C = typename Cplx<T>::type;
@@ -1069,7 +1094,7 @@ __global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const t
     const int cell = c.l2p_cells[blockIdx.x];
     const int b = c.ct_beg[cell], e = c.ct_end[cell];
     const double side = c.level_side[c.ct_level[cell]];
-    const int p = c.p, P3 = c.P3;
+    const int p = PC ? PC : c.p, P3 = p * p * p;
     const double h = side / (p - 1);
     const double cor[3] = {c.ct_corner[3 * cell], c.ct_corner[3 * cell + 1], c.ct_corner[3 * cell + 2]};
     const int nr = min(RB, R - rb0);
@@ -1292,21 +1317,30 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         const int rb = R == 1 ? 1 : 4;
         const int ep = p2m_epass(c.P3, rb, sizeof(T));
         const size_t sm = p2m_smem(c.p, rb, ep, sizeof(T));
-        if (R == 1) k_p2m<T, 1><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+        if (R == 1 && c.p == 4) k_p2m<T, 1, 4><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+        else if (R == 1) k_p2m<T, 1><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
         else k_p2m<T, 4><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
-    const size_t sm_m2m = 2 * (size_t)c.P3 * sizeof(C);
+    const size_t per_warp_mm = (2 * (size_t)c.P3 + 72) * sizeof(C);
+    const int wpb_mm = warps_per_block(per_warp_mm);
     for (int l = n_m2m_levels - 1; l >= 0; --l) {
         if (m2m[l].n == 0) continue;
-        k_m2m<T><<<(unsigned)m2m[l].n, 128, sm_m2m, stream>>>(c, t, m2m[l].data, w.M, R);
+        const unsigned blocks = (unsigned)((m2m[l].n + wpb_mm - 1) / wpb_mm);
+        if (c.p == 4) k_m2m<T, 4><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
+        else if (c.p == 5) k_m2m<T, 5><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
+        else k_m2m<T><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
     if (c.n_m2f > 0) {
-        const size_t sm = ((size_t)c.P3 + (size_t)c.p * c.p * c.N + (size_t)c.p * c.N * c.N) * sizeof(C);
-        k_m2f<T><<<(unsigned)c.n_m2f, 128, sm, stream>>>(c, t, w.M, w.Mhat, R);
+        const size_t per_warp = ((size_t)c.P3 + (size_t)c.p * c.p * c.N + (size_t)c.p * c.N * c.N) * sizeof(C);
+        const int wpb = warps_per_block(per_warp);
+        const unsigned blocks = (unsigned)((c.n_m2f + wpb - 1) / wpb);
+        if (c.p == 4 && c.N == 7) k_m2f<T, 4, 7><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
+        else if (c.p == 5 && c.N == 9) k_m2f<T, 5, 9><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
+        else k_m2f<T><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -1319,7 +1353,8 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         m2l_shape<T>(c, 1, &S, &sm);
         m2l_shape<T>(c, 8, &S8, &sm8);
         if (c.N <= 8 && sm8 <= kSmemLimit) {         // rows of N <= 8 samples (N^2 <= 64), 64 threads per member
-            k_m2l_rows<T, 8, 64><<<(unsigned)c.n_grp, 512 + 32, sm8, stream>>>(c, t, w.Mhat, w.L, R, S8);
+            if (c.p == 4 && c.N == 7) k_m2l_rows<T, 8, 64, 4, 7><<<(unsigned)c.n_grp, 512 + 32, sm8, stream>>>(c, t, w.Mhat, w.L, R, S8);
+            else k_m2l_rows<T, 8, 64><<<(unsigned)c.n_grp, 512 + 32, sm8, stream>>>(c, t, w.Mhat, w.L, R, S8);
         } else {
             if (sm > kSmemLimit) return cudaErrorInvalidConfiguration;
             if (c.NF <= 512) {          // two samples per thread, at most 256 threads
@@ -1339,7 +1374,10 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     // downward pass
     for (int l = 1; l < n_l2l_levels; ++l) {
         if (l2l[l].n == 0) continue;
-        k_l2l<T><<<(unsigned)l2l[l].n, 128, sm_m2m, stream>>>(c, t, l2l[l].data, l2l_par[l], w.L, R);
+        const unsigned blocks = (unsigned)((l2l[l].n + wpb_mm - 1) / wpb_mm);
+        if (c.p == 4) k_l2l<T, 4><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);
+        else if (c.p == 5) k_l2l<T, 5><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);
+        else k_l2l<T><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -1348,7 +1386,8 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         const int rb = R == 1 ? 1 : 4;
         const int ep = l2p_epass(c.P3, rb, sizeof(C));
         const size_t sm = l2p_smem(c.P3, rb, ep, sizeof(C));
-        if (R == 1) k_l2p<T, 1><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+        if (R == 1 && c.p == 4) k_l2p<T, 1, 4><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+        else if (R == 1) k_l2p<T, 1><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
         else k_l2p<T, 4><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
         DEFMM_CHECK_LAUNCH();
     }
@@ -1374,7 +1413,19 @@ cudaError_t configure_kernels() {
     if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     // the row kernel's occupancy is set by shared memory: ask for the largest carveout
     if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64, 4, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64, 4, 7>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2f<T, 4, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2f<T, 5, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2m<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2m<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_l2l<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_l2l<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_p2m<T, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_l2p<T, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_l2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_p2m<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_p2m<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_l2p<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
