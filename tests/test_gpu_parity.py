@@ -138,3 +138,20 @@ def test_sphere1M_sampled_against_direct():
     err = _rel(p64[idx], exact)
     print("sphere1M: rel-L2 vs direct on 2000 targets %.3e, c64 vs c128 %.3e" % (err, _rel(p64, p128)))
     assert err <= 5e-3
+
+
+@pytest.mark.slow
+def test_box500k_order5_32rhs_sampled_against_direct():
+    """5*10^5 points on a 1 x 1 x 0.25 box surface (edge-refined), kappa*D = 64,
+    order 5, 32 complex64 right-hand sides in one apply: every column against
+    the direct sum on 400 sampled targets (order-5 accuracy)."""
+    X, q, kappa, order, leaf, _ = W.make("box500k_kD64_p5_r32")
+    plan = defmm.Plan(X, kappa=kappa, order=order, leaf_size=leaf)
+    p64 = _gpu(plan, q, torch.complex64)
+    idx = np.sort(np.random.default_rng(11).choice(len(X), 400, replace=False))
+    exact = direct.direct_sum_c(X, X, q, kappa, direct.eps_self(X), targets=idx)
+    errs = [_rel(p64[idx, r], exact[:, r]) for r in range(q.shape[1])]
+    print("box500k p5 x32: rel-L2 vs direct, worst column %.3e, mean %.3e" % (max(errs), np.mean(errs)))
+    assert max(errs) <= 2e-3
+    one = _gpu(plan, q[:, 17], torch.complex64)
+    assert _rel(one, p64[:, 17]) <= TOL64          # a column alone equals the column in the batch
