@@ -108,6 +108,16 @@ __device__ __forceinline__ double2 helmholtz(double dx, double dy, double dz, do
     return out;
 }
 
+// e^{2 pi i t} for a phase given in turns, reduced exactly to [-1/2, 1/2].
+__device__ __forceinline__ void turns_sincos(float t, float* s, float* c) {
+    t -= __fadd_rn(__fadd_rn(t, 12582912.f), -12582912.f);
+    __sincosf(6.28318530717958647692f * t, s, c);
+}
+__device__ __forceinline__ void turns_sincos(double t, double* s, double* c) {
+    t -= rint(t);
+    sincospi(2.0 * t, s, c);
+}
+
 // Coordinates relative to the target leaf centre are kept as unevaluated sums
 // hi + lo of two values of type T (lo = 0 in double precision), so that the
 // difference of two nearby points is accurate to the precision of the
@@ -244,16 +254,24 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
     const float eps2 = (float)(c.eps_self * c.eps_self);
     const float inv4pi = (float)kInv4Pi;
     const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];
-    for (int t0 = tb; t0 < te; t0 += 128) {
-        const int nt = min(128, te - t0);
-        const int splits = 128 / nt;
-        const int ti = threadIdx.x % nt, sj = threadIdx.x / nt;
+    for (int t0 = tb; t0 < te; t0 += 256) {
+        // two targets per thread: target pairs (2i, 2i+1) x source splits
+        const int nt = min(256, te - t0);
+        const int np = (nt + 1) >> 1;
+        const int splits = 128 / np;
+        const int ti = threadIdx.x % np, sj = threadIdx.x / np;
         const bool active = sj < splits;
-        float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh;
-        if (active) { xh = c.Xh[t0 + ti]; xl = c.Xl[t0 + ti]; }
-        float2 acc[RB];
+        const int ia = 2 * ti, ib = 2 * ti + 1;
+        const bool has_b = ib < nt;
+        float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh, yh = xh, yl = xh;
+        if (active) {
+            xh = c.Xh[t0 + ia]; xl = c.Xl[t0 + ia];
+            if (has_b) { yh = c.Xh[t0 + ib]; yl = c.Xl[t0 + ib]; }
+            else { yh = xh; yl = xl; }
+        }
+        float2 acc[RB], bcc[RB];
 #pragma unroll
-        for (int r = 0; r < RB; ++r) acc[r] = make_float2(0.f, 0.f);
+        for (int r = 0; r < RB; ++r) { acc[r] = make_float2(0.f, 0.f); bcc[r] = make_float2(0.f, 0.f); }
         for (int g0 = r0; g0 < r1; g0 += kP2PRanges) {          // batches of ranges
             const int ng = min(kP2PRanges, r1 - g0);
             __syncthreads();
@@ -264,7 +282,6 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
             if (threadIdx.x == 0) roff[ng] = c.p2p_soff[g0 + ng - 1] - c.p2p_soff[g0] + c.p2p_send[g0 + ng - 1] - c.p2p_sbeg[g0 + ng - 1];
             __syncthreads();
             const int total = roff[ng];
-            // source of concatenated position f: binary search in roff
             auto source_of = [&](int f) {
                 int lo = 0, hi = ng - 1;
                 while (lo < hi) {
@@ -306,45 +323,68 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
                 if (active) {
                     for (int k = sj; k < ns; k += splits) {
                         const float4 a = sa[k], b = sb[k];
-                        const float dx = (xh.x - a.x) + (xl.x - b.x);
-                        const float dy = (xh.y - a.y) + (xl.y - b.y);
-                        const float dz = (xh.z - a.z) + (xl.z - b.z);
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        float rinv = rsqrtf(r2);
-                        rinv = r2 > eps2 ? rinv : 0.f;
-                        float tt = r2 * rinv * kap2pi;
-                        tt -= __fadd_rn(__fadd_rn(tt, 12582912.f), -12582912.f);
-                        float sn, cs;
-                        __sincosf(6.28318530717958647692f * tt, &sn, &cs);
-                        const float gr = cs * rinv, gi = sn * rinv;
+                        float2 ga, gb;
+                        {
+                            const float dx = (xh.x - a.x) + (xl.x - b.x);
+                            const float dy = (xh.y - a.y) + (xl.y - b.y);
+                            const float dz = (xh.z - a.z) + (xl.z - b.z);
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            float rinv = rsqrtf(r2);
+                            rinv = r2 > eps2 ? rinv : 0.f;
+                            float sn, cs;
+                            turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                            ga = make_float2(cs * rinv, sn * rinv);
+                        }
+                        {
+                            const float dx = (yh.x - a.x) + (yl.x - b.x);
+                            const float dy = (yh.y - a.y) + (yl.y - b.y);
+                            const float dz = (yh.z - a.z) + (yl.z - b.z);
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            float rinv = rsqrtf(r2);
+                            rinv = r2 > eps2 ? rinv : 0.f;
+                            float sn, cs;
+                            turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                            gb = make_float2(cs * rinv, sn * rinv);
+                        }
                         if (RB == 1) {
-                            acc[0].x = fmaf(gr, a.w, fmaf(-gi, b.w, acc[0].x));
-                            acc[0].y = fmaf(gr, b.w, fmaf(gi, a.w, acc[0].y));
+                            acc[0].x = fmaf(ga.x, a.w, fmaf(-ga.y, b.w, acc[0].x));
+                            acc[0].y = fmaf(ga.x, b.w, fmaf(ga.y, a.w, acc[0].y));
+                            bcc[0].x = fmaf(gb.x, a.w, fmaf(-gb.y, b.w, bcc[0].x));
+                            bcc[0].y = fmaf(gb.x, b.w, fmaf(gb.y, a.w, bcc[0].y));
                         } else {
 #pragma unroll
                             for (int r = 0; r < RB; ++r) {
                                 const float2 q = sq[r][k];
-                                acc[r].x = fmaf(gr, q.x, fmaf(-gi, q.y, acc[r].x));
-                                acc[r].y = fmaf(gr, q.y, fmaf(gi, q.x, acc[r].y));
+                                acc[r].x = fmaf(ga.x, q.x, fmaf(-ga.y, q.y, acc[r].x));
+                                acc[r].y = fmaf(ga.x, q.y, fmaf(ga.y, q.x, acc[r].y));
+                                bcc[r].x = fmaf(gb.x, q.x, fmaf(-gb.y, q.y, bcc[r].x));
+                                bcc[r].y = fmaf(gb.x, q.y, fmaf(gb.y, q.x, bcc[r].y));
                             }
                         }
                     }
                 }
             }
         }
+        // reduce over the splits in order: first the a targets, then the b targets
 #pragma unroll
         for (int r = 0; r < RB; ++r) red[r][threadIdx.x] = acc[r];
         __syncthreads();
-        if (active && sj == 0) {
+        if (active && sj == 0)
             for (int r = 0; r < nr; ++r) {
                 float2 s = red[r][ti];
-                for (int q = 1; q < splits; ++q) {
-                    s.x += red[r][ti + q * nt].x;
-                    s.y += red[r][ti + q * nt].y;
-                }
-                part[(int64_t)(rb0 + r) * c.p2p_parts + pbase + (t0 + ti - tb)] = s;
+                for (int q = 1; q < splits; ++q) { s.x += red[r][ti + q * np].x; s.y += red[r][ti + q * np].y; }
+                part[(int64_t)(rb0 + r) * c.p2p_parts + pbase + (t0 + ia - tb)] = s;
             }
-        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RB; ++r) red[r][threadIdx.x] = bcc[r];
+        __syncthreads();
+        if (active && sj == 0 && has_b)
+            for (int r = 0; r < nr; ++r) {
+                float2 s = red[r][ti];
+                for (int q = 1; q < splits; ++q) { s.x += red[r][ti + q * np].x; s.y += red[r][ti + q * np].y; }
+                part[(int64_t)(rb0 + r) * c.p2p_parts + pbase + (t0 + ib - tb)] = s;
+            }
         __syncthreads();
     }
 }
@@ -371,16 +411,6 @@ __global__ void __launch_bounds__(128) k_p2p_reduce(DevCommon c, const C* __rest
 // tabulated node factors of the direction's slot, so
 //   M_u[a] = P_u(a) * sum_y S_a(y_hat) (q(y) conj(E_u(y))),
 // one phase per (particle, direction) and a real-basis contraction.
-// e^{2 pi i t} for a phase given in turns, reduced exactly to [-1/2, 1/2].
-__device__ __forceinline__ void turns_sincos(float t, float* s, float* c) {
-    t -= __fadd_rn(__fadd_rn(t, 12582912.f), -12582912.f);
-    __sincosf(6.28318530717958647692f * t, s, c);
-}
-__device__ __forceinline__ void turns_sincos(double t, double* s, double* c) {
-    t -= rint(t);
-    sincospi(2.0 * t, s, c);
-}
-
 constexpr int kP2MChunk = 64;     // particles staged at a time
 constexpr int kMaxExp = 32;       // expansions handled per pass
 
