@@ -55,6 +55,41 @@ template <typename T> __device__ __forceinline__ T lagrange(int p, int m, T s) {
     return v;
 }
 
+// Loads n consecutive values from shared memory with 16-byte loads where the
+// type and count allow (the callers' rows start on 16-byte boundaries then).
+template <int n> __device__ __forceinline__ void ld_vec(const float* src, float* dst) {
+    if constexpr (n % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < n / 4; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(src)[i];
+            dst[4 * i] = v.x, dst[4 * i + 1] = v.y, dst[4 * i + 2] = v.z, dst[4 * i + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < n; ++i) dst[i] = src[i];
+    }
+}
+template <int n> __device__ __forceinline__ void ld_vec(const double* src, double* dst) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) dst[i] = src[i];
+}
+template <int n> __device__ __forceinline__ void ld_vec(const float2* src, float2* dst) {
+    if constexpr (n % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(src)[i];
+            dst[2 * i] = make_float2(v.x, v.y), dst[2 * i + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < n; ++i) dst[i] = src[i];
+    }
+}
+template <int n> __device__ __forceinline__ void ld_vec(const double2* src, double2* dst) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) dst[i] = src[i];
+}
+
 constexpr double kInv4Pi = 0.0795774715459476678844418816863;  // 1/(4 pi)
 constexpr double kInv2Pi = 0.159154943091895335768883763373;   // 1/(2 pi)
 
@@ -1219,6 +1254,267 @@ __host__ size_t l2p_smem(int P3, int RB, int epass, size_t ccplx) {
     return ((size_t)RB * epass * P3 + (size_t)RB * 128) * ccplx;
 }
 
+// ------------------------------------------------------------------ P2M / L2P, one warp per leaf
+// Leaves are small (tens of particles, mostly one expansion), so for orders
+// known at compile time a warp, not a block, handles a leaf; blocks hold four
+// independent warps synchronised with __syncwarp only.
+constexpr int kLeafWarps = 4;
+__host__ __device__ constexpr int p2m_items_per_lane(int RB) { return RB == 1 ? 4 : 1; }
+__host__ int p2m_warp_epass(int p, int RB) {
+    const int ep = p2m_items_per_lane(RB) * 32 / (p * p);
+    return ep < 1 ? 1 : ep;
+}
+__host__ size_t p2m_warp_smem(int p, int RB, int epass, size_t creal) {
+    return kLeafWarps * ((((size_t)32 * 3 * p * creal + 15) / 16) * 16 + (size_t)RB * epass * 32 * 2 * creal);
+}
+
+// P2M (Sec. 2.2) with the separated plane wave of k_p2m.  Lanes own items
+// (expansion, a1, a2) of PC outputs along a0; per particle a lane reads the PC
+// x-factors once and w = l_a1(y) l_a2(z) q conj(E_u(y)).  When a pass has at
+// most 16 items the particles are split between the half-warps (even / odd)
+// and the two partial sums are added, lower half first.
+template <typename T, int RB, int PC>
+__global__ void __launch_bounds__(32 * kLeafWarps) k_p2m_warp(DevCommon c, DevTyped<T> t,
+                                                              const typename Cplx<T>::type* __restrict__ qs,
+                                                              typename Cplx<T>::type* __restrict__ M, int R, int rb0,
+                                                              int epass) {
+    using C = typename Cplx<T>::type;
+    constexpr int P2 = PC * PC, P3 = P2 * PC, V = p2m_items_per_lane(RB), LW = 3 * PC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li = blockIdx.x * kLeafWarps + warp;
+    if (li >= c.n_p2m) return;
+    const size_t lag_bytes = (((size_t)32 * LW * sizeof(T) + 15) / 16) * 16;
+    unsigned char* base = smem_raw + (size_t)warp * (lag_bytes + (size_t)RB * epass * 32 * sizeof(C));
+    T* lag = reinterpret_cast<T*>(base);                 // [32][3][PC]
+    C* qm = reinterpret_cast<C*>(base + lag_bytes);      // [RB][epass][32]
+    const int cell = c.p2m_cells[li];
+    const int b = c.cs_beg[cell], e = c.cs_end[cell];
+    const double side = c.level_side[c.cs_level[cell]];
+    const double h = side / (PC - 1);
+    const double cx = c.cs_corner[3 * cell], cy = c.cs_corner[3 * cell + 1], cz = c.cs_corner[3 * cell + 2];
+    const int nr = min(RB, R - rb0);
+    const T k2pi = (T)(c.kappa * kInv2Pi);
+    const int ex0 = c.m_first[cell], nex = c.m_count[cell];
+    for (int e0 = 0; e0 < nex; e0 += epass) {
+        const int ne = min(epass, nex - e0);
+        const int nitems = ne * P2;
+        const int split = nitems <= 16 ? 2 : 1;
+        const int il = split == 2 ? (lane & 15) : lane, js = split == 2 ? (lane >> 4) : 0;
+        const int stride = 32 / split;
+        int yo[V], zo[V], qo[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int it = min(il + v * stride, nitems - 1);
+            const int ee = it / P2, rem = it - ee * P2;
+            yo[v] = PC + rem % PC;
+            zo[v] = 2 * PC + rem / PC;
+            qo[v] = ee * 32;
+        }
+        C acc[V][PC][RB];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int a0 = 0; a0 < PC; ++a0)
+#pragma unroll
+                for (int r = 0; r < RB; ++r) acc[v][a0][r] = czero<C>();
+        for (int j0 = b; j0 < e; j0 += 32) {
+            const int nj = min(32, e - j0);
+            __syncwarp();
+            if (lane < nj) {
+                const int64_t j = j0 + lane;
+                const double d0 = c.Ys[3 * j] - cx, d1 = c.Ys[3 * j + 1] - cy, d2 = c.Ys[3 * j + 2] - cz;
+                const T s0 = (T)(d0 / h), s1 = (T)(d1 / h), s2 = (T)(d2 / h);
+#pragma unroll
+                for (int m = 0; m < PC; ++m) {
+                    lag[lane * LW + m] = lagrange<T>(PC, m, s0);
+                    lag[lane * LW + PC + m] = lagrange<T>(PC, m, s1);
+                    lag[lane * LW + 2 * PC + m] = lagrange<T>(PC, m, s2);
+                }
+                const T x0 = (T)(d0 - 0.5 * side), x1 = (T)(d1 - 0.5 * side), x2 = (T)(d2 - 0.5 * side);
+                C q[RB];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) q[r] = r < nr ? qs[(int64_t)(rb0 + r) * c.ny + j] : czero<C>();
+                for (int ee = 0; ee < ne; ++ee) {
+                    const int slot = c.m_slot[ex0 + e0 + ee];
+                    C ph = mk((T)1, (T)0);
+                    if (slot >= 0) {
+                        const T arg = x0 * (T)c.slot_u[3 * slot] + x1 * (T)c.slot_u[3 * slot + 1] +
+                                      x2 * (T)c.slot_u[3 * slot + 2];
+                        T sn, cs;
+                        turns_sincos(arg * k2pi, &sn, &cs);
+                        ph = mk(cs, -sn);                              // conj(E_u(y))
+                    }
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) qm[((size_t)r * epass + ee) * 32 + lane] = cmul(q[r], ph);
+                }
+            }
+            __syncwarp();
+            for (int j = js; j < nj; j += split) {
+                const T* lj = lag + j * LW;
+                T lx[PC];
+                ld_vec<PC>(lj, lx);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (il + v * stride < nitems) {
+                        const T w = lj[yo[v]] * lj[zo[v]];
+#pragma unroll
+                        for (int r = 0; r < RB; ++r) {
+                            const C q = qm[(size_t)r * epass * 32 + qo[v] + j];
+                            const T wx = w * q.x, wy = w * q.y;
+#pragma unroll
+                            for (int a0 = 0; a0 < PC; ++a0) {
+                                acc[v][a0][r].x = fma(lx[a0], wx, acc[v][a0][r].x);
+                                acc[v][a0][r].y = fma(lx[a0], wy, acc[v][a0][r].y);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (split == 2) {
+#pragma unroll
+            for (int a0 = 0; a0 < PC; ++a0)
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    acc[0][a0][r].x += __shfl_down_sync(0xffffffffu, acc[0][a0][r].x, 16);
+                    acc[0][a0][r].y += __shfl_down_sync(0xffffffffu, acc[0][a0][r].y, 16);
+                }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int it = il + v * stride;
+            if (js == 0 && it < nitems) {
+                const int ee = it / P2, rem = it - ee * P2;
+                const int ex = ex0 + e0 + ee;
+                const int slot = c.m_slot[ex];
+                const C* P = t.slot_P + (int64_t)(slot < 0 ? 0 : slot) * 3 * PC;
+                const C p12 = slot >= 0 ? cmul(P[PC + rem % PC], P[2 * PC + rem / PC]) : mk((T)1, (T)0);
+#pragma unroll
+                for (int a0 = 0; a0 < PC; ++a0) {
+                    const C ph = slot >= 0 ? cmul(P[a0], p12) : p12;
+#pragma unroll
+                    for (int r = 0; r < RB; ++r)
+                        if (r < nr) M[((int64_t)ex * R + rb0 + r) * P3 + rem * PC + a0] = cmul(acc[v][a0][r], ph);
+                }
+            }
+        }
+    }
+}
+
+// L2P (Sec. 2.2): a lane per target; the leaf's expansions are staged epass at
+// a time, pre-scaled by conj(P_u(a)), and each (target, expansion) costs one
+// phase E_u(x) and a real-basis contraction over the staged rows.
+__host__ int l2p_warp_epass(int P3, int RB, size_t ccplx) {
+    const int ep = (int)(8192 / ((size_t)RB * P3 * ccplx));
+    return ep < 1 ? 1 : (ep > 8 ? 8 : ep);
+}
+__host__ size_t l2p_warp_smem(int P3, int RB, int epass, size_t ccplx) {
+    return kLeafWarps * (size_t)RB * epass * P3 * ccplx;
+}
+
+template <typename T, int RB, int PC>
+__global__ void __launch_bounds__(32 * kLeafWarps) k_l2p_warp(DevCommon c, DevTyped<T> t,
+                                                              const typename Cplx<T>::type* __restrict__ L,
+                                                              typename Cplx<T>::type* __restrict__ ps, int R, int rb0,
+                                                              int epass) {
+    using C = typename Cplx<T>::type;
+    constexpr int P3 = PC * PC * PC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li = blockIdx.x * kLeafWarps + warp;
+    if (li >= c.n_l2p) return;
+    C* Ls = reinterpret_cast<C*>(smem_raw) + (size_t)warp * RB * epass * P3;   // [epass][RB][P3]
+    const int cell = c.l2p_cells[li];
+    const int b = c.ct_beg[cell], e = c.ct_end[cell];
+    const double side = c.level_side[c.ct_level[cell]];
+    const double h = side / (PC - 1);
+    const double cx = c.ct_corner[3 * cell], cy = c.ct_corner[3 * cell + 1], cz = c.ct_corner[3 * cell + 2];
+    const int nr = min(RB, R - rb0);
+    const T k2pi = (T)(c.kappa * kInv2Pi);
+    const int ex0 = c.l_first[cell], nex = c.l_count[cell];
+    for (int t0 = b; t0 < e; t0 += 32) {
+        const bool act = t0 + lane < e;
+        const int64_t j = act ? t0 + lane : t0;
+        const double d0 = c.Xs[3 * j] - cx, d1 = c.Xs[3 * j + 1] - cy, d2 = c.Xs[3 * j + 2] - cz;
+        T lag[3][PC];
+        {
+            const T s0 = (T)(d0 / h), s1 = (T)(d1 / h), s2 = (T)(d2 / h);
+#pragma unroll
+            for (int m = 0; m < PC; ++m) {
+                lag[0][m] = lagrange<T>(PC, m, s0);
+                lag[1][m] = lagrange<T>(PC, m, s1);
+                lag[2][m] = lagrange<T>(PC, m, s2);
+            }
+        }
+        const T x0 = (T)(d0 - 0.5 * side), x1 = (T)(d1 - 0.5 * side), x2 = (T)(d2 - 0.5 * side);
+        C acc[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) acc[r] = czero<C>();
+        for (int e0 = 0; e0 < nex; e0 += epass) {
+            const int ne = min(epass, nex - e0);
+            __syncwarp();
+            for (int i = lane; i < ne * nr * P3; i += 32) {
+                const int ee = i / (nr * P3), rem = i - ee * nr * P3, r = rem / P3, a = rem - r * P3;
+                const int ex = ex0 + e0 + ee;
+                const int slot = c.l_slot[ex];
+                C v = L[((int64_t)ex * R + rb0 + r) * P3 + a];
+                if (slot >= 0) {
+                    const int a0 = a % PC, a1 = (a / PC) % PC, a2 = a / (PC * PC);
+                    const C* P = t.slot_P + (int64_t)slot * 3 * PC;
+                    v = cmulc(v, cmul(cmul(P[a0], P[PC + a1]), P[2 * PC + a2]));
+                }
+                Ls[((size_t)ee * RB + r) * P3 + a] = v;
+            }
+            __syncwarp();
+            for (int ee = 0; ee < ne; ++ee) {
+                const int slot = c.l_slot[ex0 + e0 + ee];
+                C E = mk((T)1, (T)0);
+                if (slot >= 0) {
+                    const T arg = x0 * (T)c.slot_u[3 * slot] + x1 * (T)c.slot_u[3 * slot + 1] + x2 * (T)c.slot_u[3 * slot + 2];
+                    T sn, cs;
+                    turns_sincos(arg * k2pi, &sn, &cs);
+                    E = mk(cs, sn);
+                }
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    if (r < nr) {
+                        const C* Lr = Ls + ((size_t)ee * RB + r) * P3;
+                        C sz = czero<C>();
+#pragma unroll
+                        for (int a2 = 0; a2 < PC; ++a2) {
+                            C sy = czero<C>();
+#pragma unroll
+                            for (int a1 = 0; a1 < PC; ++a1) {
+                                C lr[PC];
+                                ld_vec<PC>(Lr + (a2 * PC + a1) * PC, lr);
+                                C sx = czero<C>();
+#pragma unroll
+                                for (int a0 = 0; a0 < PC; ++a0) {
+                                    sx.x = fma(lag[0][a0], lr[a0].x, sx.x);
+                                    sx.y = fma(lag[0][a0], lr[a0].y, sx.y);
+                                }
+                                sy.x = fma(lag[1][a1], sx.x, sy.x);
+                                sy.y = fma(lag[1][a1], sx.y, sy.y);
+                            }
+                            sz.x = fma(lag[2][a2], sy.x, sz.x);
+                            sz.y = fma(lag[2][a2], sy.y, sz.y);
+                        }
+                        cfma(acc[r], E, sz);
+                    }
+                }
+            }
+        }
+        if (act)
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+                if (r < nr) {
+                    C* dst = ps + (int64_t)(rb0 + r) * c.nx + j;
+                    *dst = cadd(*dst, acc[r]);
+                }
+    }
+}
+
 // ------------------------------------------------------------------ spectra (float64)
 // g(delta) = G(side*kbar + h*delta) placed at delta mod N, then an N^3 DFT
 // with e^{-2 pi i xi.x / N} (unnormalised) along x, y and z.
@@ -1345,11 +1641,20 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
         if (c.n_p2m == 0) break;
         const int rb = R == 1 ? 1 : 4;
-        const int ep = p2m_epass(c.P3, rb, sizeof(T));
-        const size_t sm = p2m_smem(c.p, rb, ep, sizeof(T));
-        if (R == 1 && c.p == 4) k_p2m<T, 1, 4><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
-        else if (R == 1) k_p2m<T, 1><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
-        else k_p2m<T, 4><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+        if (c.p == 4 || c.p == 5) {          // one warp per leaf
+            const int ep = p2m_warp_epass(c.p, rb);
+            const size_t sm = p2m_warp_smem(c.p, rb, ep, sizeof(T));
+            const unsigned nb = (unsigned)((c.n_p2m + kLeafWarps - 1) / kLeafWarps);
+            if (c.p == 4 && R == 1) k_p2m_warp<T, 1, 4><<<nb, 32 * kLeafWarps, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+            else if (c.p == 4) k_p2m_warp<T, 4, 4><<<nb, 32 * kLeafWarps, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+            else if (R == 1) k_p2m_warp<T, 1, 5><<<nb, 32 * kLeafWarps, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+            else k_p2m_warp<T, 4, 5><<<nb, 32 * kLeafWarps, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+        } else {
+            const int ep = p2m_epass(c.P3, rb, sizeof(T));
+            const size_t sm = p2m_smem(c.p, rb, ep, sizeof(T));
+            if (R == 1) k_p2m<T, 1><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+            else k_p2m<T, 4><<<(unsigned)c.n_p2m, 128, sm, stream>>>(c, t, w.qs, w.M, R, rb0, ep);
+        }
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -1414,11 +1719,20 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
         if (c.n_l2p == 0) break;
         const int rb = R == 1 ? 1 : 4;
-        const int ep = l2p_epass(c.P3, rb, sizeof(C));
-        const size_t sm = l2p_smem(c.P3, rb, ep, sizeof(C));
-        if (R == 1 && c.p == 4) k_l2p<T, 1, 4><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
-        else if (R == 1) k_l2p<T, 1><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
-        else k_l2p<T, 4><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+        if (c.p == 4 || c.p == 5) {          // one warp per leaf
+            const int ep = l2p_warp_epass(c.P3, rb, sizeof(C));
+            const size_t sm = l2p_warp_smem(c.P3, rb, ep, sizeof(C));
+            const unsigned nb = (unsigned)((c.n_l2p + kLeafWarps - 1) / kLeafWarps);
+            if (c.p == 4 && R == 1) k_l2p_warp<T, 1, 4><<<nb, 32 * kLeafWarps, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+            else if (c.p == 4) k_l2p_warp<T, 4, 4><<<nb, 32 * kLeafWarps, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+            else if (R == 1) k_l2p_warp<T, 1, 5><<<nb, 32 * kLeafWarps, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+            else k_l2p_warp<T, 4, 5><<<nb, 32 * kLeafWarps, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+        } else {
+            const int ep = l2p_epass(c.P3, rb, sizeof(C));
+            const size_t sm = l2p_smem(c.P3, rb, ep, sizeof(C));
+            if (R == 1) k_l2p<T, 1><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+            else k_l2p<T, 4><<<(unsigned)c.n_l2p, 128, sm, stream>>>(c, t, w.L, w.ps, R, rb0, ep);
+        }
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -1451,8 +1765,6 @@ cudaError_t configure_kernels() {
     if ((e = cudaFuncSetAttribute(k_m2m<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_l2l<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_l2l<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_p2m<T, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_l2p<T, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_l2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
