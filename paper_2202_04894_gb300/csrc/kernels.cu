@@ -115,20 +115,34 @@ __global__ void k_scatter(const C* __restrict__ ps, C* __restrict__ p, const int
 }
 
 // ------------------------------------------------------------------ P2P
+// The hardware approximations (PTX rsqrt.approx / sin.approx / cos.approx,
+// flush-to-zero): arguments here are never subnormal (r^2 > eps_self^2 is
+// tested before use, phases are reduced to [-pi, pi]), so the flush changes
+// nothing and saves the subnormal handling around each instruction.
+__device__ __forceinline__ float rsqrt_hw(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void sincos_hw(float a, float* s, float* c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(a));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(a));
+}
+
 // Kernel value G(x, y) for a difference d, zero when |d|^2 <= eps2 (Sec. 5.3).
-// Single precision: 1/r from rsqrt, the phase kappa r / (2 pi) reduced exactly
-// to [-1/2, 1/2] turns (round-to-nearest by adding and subtracting 1.5 * 2^23),
-// then the hardware sine and cosine on [-pi, pi].
+// Single precision: 1/r from the hardware reciprocal square root, the phase
+// kappa r / (2 pi) reduced exactly to [-1/2, 1/2] turns (round-to-nearest by
+// adding and subtracting 1.5 * 2^23), then the hardware sine and cosine on
+// [-pi, pi].
 __device__ __forceinline__ float2 helmholtz(float dx, float dy, float dz, float kap2pi, float eps2) {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float rinv = rsqrtf(r2);
+    float rinv = rsqrt_hw(r2);
     rinv = r2 > eps2 ? rinv : 0.f;      // coincident points contribute nothing
     const float r = r2 * rinv;
     float t = r * kap2pi;
-    const float rt = (t + 12582912.f) - 12582912.f;
-    t -= rt;
+    t -= __fadd_rn(__fadd_rn(t, 12582912.f), -12582912.f);
     float s, c;
-    __sincosf(6.28318530717958647692f * t, &s, &c);
+    sincos_hw(6.28318530717958647692f * t, &s, &c);
     const float g = rinv * (float)kInv4Pi;
     return make_float2(c * g, s * g);
 }
@@ -146,7 +160,7 @@ __device__ __forceinline__ double2 helmholtz(double dx, double dy, double dz, do
 // e^{2 pi i t} for a phase given in turns, reduced exactly to [-1/2, 1/2].
 __device__ __forceinline__ void turns_sincos(float t, float* s, float* c) {
     t -= __fadd_rn(__fadd_rn(t, 12582912.f), -12582912.f);
-    __sincosf(6.28318530717958647692f * t, s, c);
+    sincos_hw(6.28318530717958647692f * t, s, c);
 }
 __device__ __forceinline__ void turns_sincos(double t, double* s, double* c) {
     t -= rint(t);
@@ -261,15 +275,18 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
     }
 }
 
-// Single-precision near field.  One block per target leaf (heaviest first);
-// the leaf's n_t targets are spread over the 128 threads as target x
-// source-split (splits = 128 / n_t), so small leaves do not leave lanes idle.
+// Single-precision near field.  One block per work unit (a target leaf and
+// at most kP2PUnitSources of its near sources, heaviest first); pairs of the
+// leaf's targets are spread over the 128 threads as target pair x
+// source-split, so small leaves do not leave lanes idle.
 // The leaf's source ranges are read as one concatenated sequence cut into
 // full tiles of 128 (a thread finds its source by binary search in the
 // ranges' prefix offsets), and the next tile is loaded into registers while
 // the current one is consumed.  Coordinates are hi + lo float pairs relative
-// to the cube centre; charges are pre-scaled by 1/(4 pi) when staged; partial
-// sums are reduced over the splits in a fixed order.
+// to the cube centre and every difference is formed from both parts: a
+// single float per coordinate, even relative to the leaf, loses too much for
+// near-coincident pairs.  Charges are pre-scaled by 1/(4 pi) when staged;
+// partial sums are reduced over the splits in a fixed order.
 constexpr int kP2PRanges = kP2PUnitRanges;   // ranges of a work unit, held in shared memory
 
 template <int RB>
@@ -364,7 +381,7 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
                             const float dy = (xh.y - a.y) + (xl.y - b.y);
                             const float dz = (xh.z - a.z) + (xl.z - b.z);
                             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            float rinv = rsqrtf(r2);
+                            float rinv = rsqrt_hw(r2);
                             rinv = r2 > eps2 ? rinv : 0.f;
                             float sn, cs;
                             turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
@@ -375,7 +392,7 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
                             const float dy = (yh.y - a.y) + (yl.y - b.y);
                             const float dz = (yh.z - a.z) + (yl.z - b.z);
                             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            float rinv = rsqrtf(r2);
+                            float rinv = rsqrt_hw(r2);
                             rinv = r2 > eps2 ? rinv : 0.f;
                             float sn, cs;
                             turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
