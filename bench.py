@@ -12,6 +12,19 @@ each rank applies its own copy of the workload; there is no data-path
 collective).  Inputs are resident in HBM for `value`; `e2e` times the
 host-buffer entry point (defmm_apply_host) with both copies inside.  L2 is
 flushed (a 512 MB write) before every timed step, outside the step's events.
+
+Two more workloads, each printing its own JSON line:
+
+  --workload batch48   48 uneven geometries (spheres, ellipsoids, box
+                       surfaces; N log-uniform in [2e4, 8e5], kappa*D in
+                       [16, 256], order 4, complex64) applied together as one
+                       replayed CUDA graph, against the same applies issued one
+                       after another.
+  --workload serve16   the request server over 16 resident geometries (N in
+                       [5e4, 2e6], kappa*D in [32, 256], order 4-6): Poisson
+                       arrivals (mean gap --gap-ms, seed 300) of requests with
+                       1-8 right-hand sides on a uniformly drawn geometry,
+                       host buffers in and out; p50/p99 latency and throughput.
 """
 from __future__ import annotations
 
@@ -187,9 +200,16 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--n", type=int, default=None, help="point count (same recipe; for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=10000, help="serve16: number of requests")
+    ap.add_argument("--gap-ms", type=float, default=2.0, help="serve16: mean inter-arrival time")
+    ap.add_argument("--streams", type=int, default=4, help="serve16: batches in flight")
+    ap.add_argument("--branches", type=int, default=8, help="batch48: graph branches")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload in ("batch48", "serve16"):
+        (bench_batch if args.workload == "batch48" else bench_serve)(args)
         return
 
     import torch
@@ -348,6 +368,162 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _plans_of(geos, defmm, W, leaf=64):
+    plans = []
+    t0 = time.perf_counter()
+    for g in geos:
+        X, kappa = W.make_geometry(g)
+        plans.append(defmm.Plan(X, kappa=kappa, order=g["order"], leaf_size=leaf))
+    return plans, time.perf_counter() - t0
+
+
+def _bus(torch):
+    try:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except Exception:
+        return None
+
+
+def bench_batch(args):
+    """48 uneven geometries: one replayed CUDA graph vs the same applies in sequence."""
+    import torch
+    import __graft_entry__
+    from paper_2202_04894_gb300 import defmm, serve, workloads as W
+    __graft_entry__.build()
+    geos = W.geometry_set(**W.BATCH48)
+    plans, plan_s = _plans_of(geos, defmm, W)
+    c64 = torch.complex64
+    qs = [torch.from_numpy(np.ascontiguousarray(W.charges(p.ny, g["seed"]))).to("cuda").to(c64)
+          for p, g in zip(plans, geos)]
+    b = serve.Batch(plans, [1] * len(plans), c64, branches=args.branches)
+    for buf, q in zip(b.inputs(), qs):
+        buf.copy_(q.t())
+    b.run()
+    torch.cuda.synchronize()
+    worst = 0.0
+    for i, (p, q) in enumerate(zip(plans, qs)):
+        hi = p.apply(q.to(torch.complex128))
+        lo = b.outputs()[i].t().to(torch.complex128)
+        worst = max(worst, float(torch.linalg.norm(lo - hi) / torch.linalg.norm(hi)))
+        del hi
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    outs = [None] * len(plans)
+
+    def seq():
+        for i, (p, q) in enumerate(zip(plans, qs)):
+            outs[i] = p.apply(q)
+
+    def timed(fn, steps):
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    for _ in range(args.warmup):
+        b.run()
+        seq()
+    clocks = ClockSampler(_bus(torch))
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    g_ms = timed(b.run, args.steps)
+    s_ms = timed(seq, args.steps)
+    clk = clocks.stop()
+    points = sum(p.nx for p in plans)
+    g_avg, s_avg = statistics.mean(g_ms), statistics.mean(s_ms)
+    info = b.info()
+    line = {"metric": METRIC, "value": points / (g_avg * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": g_avg, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "batch48", "geometries": len(plans), "points": points,
+                       "n_range": list(W.BATCH48["n_range"]), "kappa_d_range": list(W.BATCH48["kd_range"]),
+                       "order": 4, "leaf": 64, "nrhs": 1, "branches": args.branches,
+                       "l2": "flushed (512 MB write) before each step", "parallelism": "single"},
+            "sequential": {"ms_per_step": s_avg, "value": points / (s_avg * 1e-3) / 1e6,
+                           "speedup_of_graph": s_avg / g_avg},
+            "graph": {"kernel_launches": info["kernel_launches"], "graph_nodes": info["graph_nodes"]},
+            "gpu_launches": info["kernel_launches"] * args.steps,
+            "max_rel_l2_c64_vs_c128": worst, "plan_s": plan_s, "clocks": clk,
+            "p50_ms": sorted(g_ms)[len(g_ms) // 2], "p99_ms": sorted(g_ms)[min(len(g_ms) - 1, int(0.99 * len(g_ms)))]}
+    print(json.dumps(line), flush=True)
+
+
+def bench_serve(args):
+    """Poisson request stream through the request server."""
+    import torch
+    import __graft_entry__
+    from paper_2202_04894_gb300 import defmm, serve, workloads as W
+    __graft_entry__.build()
+    geos = W.geometry_set(**W.SERVE16)
+    plans, plan_s = _plans_of(geos, defmm, W)
+    c64 = torch.complex64
+    maxr = 8
+    qh = [torch.from_numpy(np.ascontiguousarray(W.charges(p.ny, g["seed"], nrhs=maxr).T)).to(c64).pin_memory()
+          for p, g in zip(plans, geos)]
+    ph = [torch.empty((maxr, p.nx), dtype=c64).pin_memory() for p in plans]   # results land here (overwritten)
+    reqs = W.request_stream(args.requests, 300, args.gap_ms, len(plans), maxr)
+    budget = 96 << 30
+    srv = serve.Server(plans, c64, streams=args.streams, max_batch_rhs=16, hbm_budget=budget)
+    for g in range(len(plans)):                                   # warm-up: every geometry once
+        srv.wait_ticket(srv.submit_ptr(g, qh[g].data_ptr(), ph[g].data_ptr(), maxr))
+    st0 = srv.stats()
+    tickets = [None] * len(reqs)
+    clocks = ClockSampler(_bus(torch))
+    clocks.start()
+    time.sleep(0.3)
+
+    def producer():
+        t0 = time.perf_counter()
+        for i, (t_ms, g, r) in enumerate(reqs):
+            delay = t0 + t_ms * 1e-3 - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = srv.submit_ptr(g, qh[g].data_ptr(), ph[g].data_ptr(), r)
+
+    t_start = time.perf_counter()
+    th = threading.Thread(target=producer)
+    th.start()
+    lat = []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(1e-4)
+        lat.append(srv.wait_ticket(tickets[i]))
+    th.join()
+    wall = time.perf_counter() - t_start
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    work = sum(plans[g].nx * r for _, g, r in reqs)
+    srt = sorted(lat)
+    offered = sum(plans[g].nx * r for _, g, r in reqs) / (reqs[-1][0] * 1e-3) / 1e6
+    line = {"metric": METRIC, "value": work / wall / 1e6, "unit": UNIT, "n_gpus": 1, "steps": len(reqs),
+            "warmup": len(plans), "ms_per_step": wall * 1e3 / len(reqs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "serve16", "geometries": len(plans),
+                       "points": [p.nx for p in plans], "orders": [g["order"] for g in geos],
+                       "kappa_d": [round(g["kappa_d"], 1) for g in geos], "requests": len(reqs),
+                       "mean_gap_ms": args.gap_ms, "rhs_per_request": "uniform 1..8", "streams": args.streams,
+                       "max_batch_rhs": 16, "hbm_budget": budget, "parallelism": "single"},
+            "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+            "mean_ms": statistics.mean(lat), "max_ms": srt[-1],
+            "offered_load": {"value": offered, "unit": UNIT},
+            "e2e": {"value": work / wall / 1e6, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * sum(plans[g].ny * r for _, g, r in reqs) // len(reqs),
+                    "d2h_bytes_per_step": 8 * sum(plans[g].nx * r for _, g, r in reqs) // len(reqs)},
+            "server": {k: st[k] - st0.get(k, 0) if k in ("submitted", "completed", "batches", "rhs_applied",
+                                                          "kernel_launches") else st[k] for k in st},
+            "gpu_launches": st["kernel_launches"] - st0["kernel_launches"], "plan_s": plan_s, "clocks": clk}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

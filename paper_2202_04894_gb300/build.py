@@ -25,6 +25,7 @@ SOURCES = [
     ("kernels.cu", "nvcc"),
     ("capi.cu", "nvcc"),
     ("noalloc.cu", "nvcc"),
+    ("serve.cu", "nvcc"),
 ]
 
 
@@ -37,7 +38,7 @@ def _nvcc() -> str:
 
 def _deps_mtime() -> float:
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(INCLUDE, "defmm.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     return max(os.path.getmtime(f) for f in files)
 
 
@@ -64,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if pr.returncode != 0:
             raise RuntimeError("compile failed: %s\n%s" % (" ".join(cmd), out.decode(errors="replace")))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
     out = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if out.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(cmd), out.stdout.decode(errors="replace")))

@@ -1287,9 +1287,11 @@ __host__ size_t p2m_warp_smem(int p, int RB, int epass, size_t creal) {
 
 // P2M (Sec. 2.2) with the separated plane wave of k_p2m.  Lanes own items
 // (expansion, a1, a2) of PC outputs along a0; per particle a lane reads the PC
-// x-factors once and w = l_a1(y) l_a2(z) q conj(E_u(y)).  When a pass has at
-// most 16 items the particles are split between the half-warps (even / odd)
-// and the two partial sums are added, lower half first.
+// x-factors once and w = l_a1(y) l_a2(z) q conj(E_u(y)).  A leaf with a
+// single expansion of at most 16 lines splits its particles between the
+// half-warps (even / odd) and adds the two partial sums, lower half first;
+// the rule depends on the leaf only, so a column's summation order does not
+// depend on how many right-hand sides are blocked together.
 template <typename T, int RB, int PC>
 __global__ void __launch_bounds__(32 * kLeafWarps) k_p2m_warp(DevCommon c, DevTyped<T> t,
                                                               const typename Cplx<T>::type* __restrict__ qs,
@@ -1316,7 +1318,7 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_p2m_warp(DevCommon c, DevTy
     for (int e0 = 0; e0 < nex; e0 += epass) {
         const int ne = min(epass, nex - e0);
         const int nitems = ne * P2;
-        const int split = nitems <= 16 ? 2 : 1;
+        const int split = (nex == 1 && P2 <= 16) ? 2 : 1;   // depends on the leaf only, not on RB
         const int il = split == 2 ? (lane & 15) : lane, js = split == 2 ? (lane >> 4) : 0;
         const int stride = 32 / split;
         int yo[V], zo[V], qo[V];

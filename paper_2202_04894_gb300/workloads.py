@@ -144,3 +144,51 @@ def make(name: str, n: int | None = None):
     kappa = w["kappa_d"] / D
     q = charges(npts, w["seed"], w["nrhs"])
     return X, q, kappa, w["order"], w["leaf"], w["dtype"]
+
+
+def _log_uniform(u: float, lo: float, hi: float) -> float:
+    return float(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo))))
+
+
+def geometry_set(count: int, seed0: int, n_range, kd_range, orders=(4,)):
+    """Uneven geometries for batched and served applies.
+
+    Geometry i (seed seed0 + i) cycles through sphere, ellipsoid (axes
+    1 : 0.5 : 0.2) and box surface; its point count and kappa*D are drawn
+    log-uniform from n_range and kd_range, its order from ``orders``.
+    Returns dicts (kind, n, seed, kappa_d, order).
+    """
+    kinds = ("sphere", "ellipsoid", "box")
+    out = []
+    for i in range(count):
+        u = uniform(seed0 + i, 3)
+        out.append(dict(kind=kinds[i % 3], n=int(round(_log_uniform(u[0], *n_range))), seed=seed0 + i,
+                        kappa_d=_log_uniform(u[1], *kd_range),
+                        order=int(orders[min(len(orders) - 1, int(u[2] * len(orders)))])))
+    return out
+
+
+def make_geometry(g: dict):
+    """(X, kappa) of a geometry_set entry; kappa = kappa*D / D with D the extent."""
+    X = points(g["kind"], g["n"], g["seed"])
+    D = float(np.max(X.max(axis=0) - X.min(axis=0)))
+    return X, g["kappa_d"] / D
+
+
+# 48 uneven geometries applied together: N log-uniform in [2*10^4, 8*10^5],
+# kappa*D log-uniform in [16, 256], order 4, one complex64 right-hand side each.
+BATCH48 = dict(count=48, seed0=100, n_range=(2e4, 8e5), kd_range=(16.0, 256.0), orders=(4,))
+# 16 resident geometries for the request server: N log-uniform in
+# [5*10^4, 2*10^6], kappa*D log-uniform in [32, 256], order 4, 5 or 6.
+SERVE16 = dict(count=16, seed0=200, n_range=(5e4, 2e6), kd_range=(32.0, 256.0), orders=(4, 5, 6))
+
+
+def request_stream(count: int, seed: int, mean_gap_ms: float, ngeom: int, max_rhs: int = 8):
+    """Poisson arrivals: (arrival_ms, geometry, nrhs) with exponential gaps of the
+    given mean, geometry uniform over ngeom and nrhs uniform in 1..max_rhs."""
+    u = uniform(seed, 3 * count).reshape(count, 3)
+    gaps = -mean_gap_ms * np.log(1.0 - u[:, 0])
+    t = np.cumsum(gaps)
+    g = np.minimum((u[:, 1] * ngeom).astype(np.int64), ngeom - 1)
+    r = 1 + np.minimum((u[:, 2] * max_rhs).astype(np.int64), max_rhs - 1)
+    return [(float(t[i]), int(g[i]), int(r[i])) for i in range(count)]

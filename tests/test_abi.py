@@ -8,7 +8,7 @@ import pytest
 
 from oracle import fmm as oracle_fmm
 from paper_2202_04894_gb300 import build as pkg_build
-from paper_2202_04894_gb300 import defmm, workloads as W
+from paper_2202_04894_gb300 import defmm, serve, workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -18,19 +18,51 @@ def _built():
     pkg_build.build()
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "defmm.h")).read()
+def _declared(header="defmm.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(defmm_[a-z_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol():
     L = defmm.lib()
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert headers == ["defmm.h", "defmm_serve.h"]
     names = _declared()
     assert len(names) >= 8
     for n in names:
         assert hasattr(L, n), n
     assert set(defmm.EXPORTED) <= set(names)
+    served = _declared("defmm_serve.h")
+    for n in served:
+        assert hasattr(L, n), n
+    assert set(serve.SERVE_EXPORTED) == set(served)
+
+
+def test_serving_argument_errors():
+    """The serving entry points reject bad arguments before touching a GPU."""
+    import ctypes
+    L = serve.slib()
+    X = W.points("sphere", 200, 1)
+    pl = _host_plan(X, kappa=1.0, order=4, leaf_size=8)
+    h = ctypes.c_void_p()
+    assert L.defmm_workspace_create(pl.handle, 1, defmm.C64, ctypes.byref(h)) == 5       # host-only plan
+    assert L.defmm_workspace_create(None, 1, defmm.C64, ctypes.byref(h)) == 1
+    b = ctypes.c_size_t()
+    assert L.defmm_workspace_bytes(pl.handle, 0, defmm.C64, ctypes.byref(b)) == 1
+    assert L.defmm_workspace_bytes(pl.handle, 3, defmm.C64, ctypes.byref(b)) == 0
+    b64, b128 = b.value, ctypes.c_size_t()
+    assert L.defmm_workspace_bytes(pl.handle, 3, defmm.C128, ctypes.byref(b128)) == 0
+    assert b64 % 256 == 0 and b128.value > b64 and b64 >= 3 * 8 * 2 * 200
+    arr = (ctypes.c_void_p * 1)(pl.handle.value)
+    rr = (ctypes.c_int * 1)(1)
+    assert L.defmm_batch_create(arr, rr, 1, defmm.C64, 0, ctypes.byref(h)) == 5
+    assert L.defmm_batch_create(arr, rr, 0, defmm.C64, 0, ctypes.byref(h)) == 1
+    o = serve.ServerOptions()
+    L.defmm_server_default_options(ctypes.byref(o))
+    assert (o.streams, o.max_batch_rhs, o.hbm_budget) == (4, 16, 4 << 30)
+    assert L.defmm_server_create(arr, 1, defmm.C64, ctypes.byref(o), ctypes.byref(h)) == 5
+    assert L.defmm_apply_ws(None, None, None, None, 1, defmm.C64, None) == 1
 
 
 def _host_plan(X, Y=None, **kw):
