@@ -131,6 +131,24 @@ defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host,
 defmm_status defmm_apply_noalloc(defmm_plan plan, const void* q, void* p, int nrhs,
                                  defmm_dtype dtype, void* stream);
 
+/* Apply-time tuning of a plan.  The paper has no counterpart: these are
+ * launch choices of this library's kernels, and no result depends on them
+ * (every output is bit-for-bit the same under any admissible value).
+ *  m2l_rhs_block - right-hand sides that share one pass of the complex64 M2L
+ *                  kernel over a staged chunk of spectra and multipoles
+ *                  (1, 2 or 4; 0 = the library's choice from nrhs and the DFT
+ *                  length).  Values the kernel for the plan's DFT length
+ *                  cannot take are lowered (N = 9: at most 2; N > 9: 1).
+ * The setting applies to applies enqueued after the call; CUDA graphs
+ * captured earlier keep the value they were captured with.
+ * Errors: DEFMM_ERR_ARG (NULL plan or tuning, value not in {0, 1, 2, 4}).    */
+typedef struct {
+    int m2l_rhs_block;
+} defmm_tuning;
+
+defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning);
+defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning);
+
 /* Frees the plan and its device memory (synchronises the device first).       */
 defmm_status defmm_destroy(defmm_plan plan);
 

@@ -242,6 +242,8 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.chk_blk_off = (const int32_t*)P(o_cbo); c.chk_nspec = (const int32_t*)P(o_cns); c.chk_blk = (const int32_t*)P(o_cb);
     c.chk_op_off = (const int32_t*)P(o_coo); c.chk_op = (const int32_t*)P(o_co);
     c.chk_max_blocks = hp.chk_max_blocks;
+    for (int v = 0; v < 3; ++v) c.chk_stage_blocks[v] = hp.chk_stage_blocks[v];
+    c.m2l_rb = 0;
     c.p2m_cells = (const int32_t*)P(o_p2m); c.n_p2m = (int64_t)hp.p2m_cells.size();
     c.l2p_cells = (const int32_t*)P(o_l2p); c.n_l2p = (int64_t)hp.l2p_cells.size();
     c.p2p_unit_leaf = (const int32_t*)P(o_pul); c.p2p_unit_off = (const int32_t*)P(o_puo);
@@ -315,6 +317,21 @@ void defmm_default_options(defmm_options* opt) {
 }
 
 const char* defmm_last_error(void) { return g_err.c_str(); }
+
+defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning) {
+    if (!plan || !tuning) return fail(DEFMM_ERR_ARG, "plan or tuning is NULL");
+    const int rb = tuning->m2l_rhs_block;
+    if (rb != 0 && rb != 1 && rb != 2 && rb != 4) return fail(DEFMM_ERR_ARG, "m2l_rhs_block must be 0, 1, 2 or 4");
+    std::lock_guard<std::mutex> g(plan->busy);
+    plan->common.m2l_rb = rb;
+    return DEFMM_OK;
+}
+
+defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning) {
+    if (!plan || !tuning) return fail(DEFMM_ERR_ARG, "plan or tuning is NULL");
+    tuning->m2l_rhs_block = plan->common.m2l_rb;
+    return DEFMM_OK;
+}
 
 defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa, int order,
                                int leaf_size, const defmm_options* opt, void* stream, defmm_plan* out) {

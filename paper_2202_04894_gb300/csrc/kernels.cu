@@ -764,7 +764,7 @@ __global__ void __launch_bounds__(MAXT) k_m2l(DevCommon c, DevTyped<T> t, const 
     const int p = c.p, N = c.N, NF = c.NF, NFpad = c.NFpad, P3 = c.P3;
     const uint32_t blk_bytes = (uint32_t)(NFpad * sizeof(C));
     C* ring = reinterpret_cast<C*>(smem_raw);
-    const int stage_elems = c.chk_max_blocks * NFpad;
+    const int stage_elems = c.chk_stage_blocks[0] * NFpad;
     // F2L work arrays reuse the ring once every copy has landed
     C* Lh = ring;                              // NF
     C* T1 = Lh + NF;                           // [az][xi_y][xi_x]  p*N*N
@@ -896,27 +896,31 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // The same group schedule with rows of samples and a warp-specialised
 // pipeline.  Consumer thread (member m, lane l) of the first 8*TPM threads
-// owns the x-row (y, z) = (l mod N, l div N) of member m (l < N^2), i.e. the
-// N samples xi = x + N*l: under a pair's symmetry (sigma, s) the row's
-// permuted indices are base(y, z) + x*step (with a wrap for a negated x), so
-// the permutation costs one row base per pair.  The last warp is the
-// producer: it keeps every stage of the ring loaded with TMA bulk copies,
-// waiting on per-stage "empty" mbarriers that the consumer warps arrive on
-// after reading a stage; consumers wait on per-stage "full" mbarriers that
-// the copies complete.  There is no block-wide barrier in the main loop.
-// Every wait is bounded; a wait that gives up raises the plan's error flag
-// and the block stops after its copies in flight have had a bounded chance to
-// land.  Needs N <= NX and N^2 <= TPM.
-template <typename T, int NX, int TPM, int PC = 0, int NC = 0>
-__global__ void __launch_bounds__(8 * TPM + 32, (sizeof(T) == 4 ? 3 : 1)) k_m2l_rows(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
-                                                          typename Cplx<T>::type* __restrict__ L, int R, int S) {
+// owns the x-rows l + j*TPM (j < ROWS) of member m; row (y, z) = (l mod N,
+// l div N) holds the N samples xi = x + N*row.  Under a pair's symmetry
+// (sigma, s) a row's permuted indices are base(y, z) + x*step (with a wrap
+// for a negated x), so the permutation costs one row base per pair.  RB
+// right-hand sides share a pass: a stage holds the chunk's spectra once and
+// RB consecutive right-hand sides of each source multipole (contiguous in
+// Mhat), so every gathered spectrum sample serves RB products.  The last warp
+// is the producer: it keeps every stage of the ring loaded with TMA bulk
+// copies, waiting on per-stage "empty" mbarriers that the consumer warps
+// arrive on after reading a stage; consumers wait on per-stage "full"
+// mbarriers that the copies complete.  There is no block-wide barrier in the
+// main loop.  Every wait is bounded; a wait that gives up raises the plan's
+// error flag and the block stops after its copies in flight have had a
+// bounded chance to land.  F2L: each thread first takes the inverse DFT of
+// its rows along x in registers (p outputs per row), then the y and z passes
+// run in shared memory.  Needs N <= NX and N^2 <= ROWS*TPM.
+template <typename T, int NX, int TPM, int ROWS, int RB, int MINB, int PC = 0, int NC = 0>
+__global__ void __launch_bounds__(8 * TPM + 32, MINB) k_m2l_rows(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
+                                                                typename Cplx<T>::type* __restrict__ L, int R, int S, int stage_elems) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int p = PC ? PC : c.p, N = NC ? NC : c.N, NF = N * N * N, NFpad = c.NFpad, P3 = p * p * p;
+    const int p = PC ? PC : c.p, N = NC ? NC : c.N, NFpad = c.NFpad, P3 = p * p * p;
     const int NN = N * N;
     const uint32_t blk_bytes = (uint32_t)(NFpad * sizeof(C));
     C* ring = reinterpret_cast<C*>(smem_raw);
-    const int stage_elems = c.chk_max_blocks * NFpad;
     __shared__ __align__(8) uint64_t full[kM2LMaxStages], empty[kM2LMaxStages];
     __shared__ C tws[16];
     __shared__ int stride[6][3];
@@ -929,9 +933,16 @@ __global__ void __launch_bounds__(8 * TPM + 32, (sizeof(T) == 4 ? 3 : 1)) k_m2l_
     const int lane = threadIdx.x & 31;
     const int m = threadIdx.x / TPM, l = threadIdx.x % TPM;
     const bool member = !producer && m < nm;     // warp belongs to a member of the group
-    const bool active = member && l < NN;        // lane owns a row
-    const int y = l % N, z = l / N;
-    const int yn = y == 0 ? 0 : N - y, zn = z == 0 ? 0 : N - z;
+    int row[ROWS], yv[ROWS], zv[ROWS], yn[ROWS], zn[ROWS];
+    bool act[ROWS];
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+        row[j] = l + j * TPM;
+        act[j] = member && row[j] < NN;          // lane owns this row
+        yv[j] = row[j] % N; zv[j] = row[j] / N;
+        yn[j] = yv[j] == 0 ? 0 : N - yv[j];
+        zn[j] = zv[j] == 0 ? 0 : N - zv[j];
+    }
     const int consumer_warps = nm * (TPM / 32);
     if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
     if (threadIdx.x < 18) {
@@ -949,12 +960,17 @@ __global__ void __launch_bounds__(8 * TPM + 32, (sizeof(T) == 4 ? 3 : 1)) k_m2l_
         mbar_fence_init();
     }
     __syncthreads();
-    uint32_t use0 = 0;   // chunks of earlier right-hand sides
-    const T scale = (T)1 / (T)NF;
-    for (int r = 0; r < R; ++r) {
-        C acc[NX];
+    uint32_t use0 = 0;   // chunks of earlier passes
+    const T scale = (T)1 / (T)(N * NN);
+    for (int r0 = 0; r0 < R; r0 += RB) {
+        const int nrb = R - r0 < RB ? R - r0 : RB;   // right-hand sides in this pass
+        C acc[ROWS][RB][NX];
 #pragma unroll
-        for (int x = 0; x < NX; ++x) acc[x] = czero<C>();
+        for (int j = 0; j < ROWS; ++j)
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+                for (int x = 0; x < NX; ++x) acc[j][rr][x] = czero<C>();
         if (producer) {
             if (lane == 0) {
                 for (int k = 0; k < nchunks; ++k) {
@@ -970,11 +986,14 @@ __global__ void __launch_bounds__(8 * TPM + 32, (sizeof(T) == 4 ? 3 : 1)) k_m2l_
                     const int b0 = c.chk_blk_off[cc], nb = c.chk_blk_off[cc + 1] - b0, nsp = c.chk_nspec[cc];
                     C* base = ring + (size_t)st * stage_elems;
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect_tx(&full[st], (uint32_t)nb * blk_bytes);
+                    mbar_expect_tx(&full[st], (uint32_t)(nsp + (nb - nsp) * nrb) * blk_bytes);
                     for (int b = 0; b < nb; ++b) {
                         const int id = c.chk_blk[b0 + b];
-                        const C* src = b < nsp ? t.spec + (int64_t)id * NFpad : Mhat + ((int64_t)id * R + r) * NFpad;
-                        tma_bulk_load(base + (size_t)b * NFpad, src, blk_bytes, &full[st]);
+                        if (b < nsp)
+                            tma_bulk_load(base + (size_t)b * NFpad, t.spec + (int64_t)id * NFpad, blk_bytes, &full[st]);
+                        else   // right-hand sides r0 .. r0+nrb-1 of one source: one contiguous copy
+                            tma_bulk_load(base + (size_t)(nsp + (b - nsp) * RB) * NFpad,
+                                          Mhat + ((int64_t)id * R + r0) * NFpad, (uint32_t)nrb * blk_bytes, &full[st]);
                     }
                     issued_sh = k + 1;
                 }
@@ -989,10 +1008,11 @@ __global__ void __launch_bounds__(8 * TPM + 32, (sizeof(T) == 4 ? 3 : 1)) k_m2l_
                     atomicExch(c.err_flag, 1);
                     break;
                 }
-                if (active) {
+                if (act[0]) {
                     const C* base = ring + (size_t)st * stage_elems;
                     const int* opoff = c.chk_op_off + 9 * (ch0 + k);
                     const int o0 = opoff[m], o1 = opoff[m + 1];
+                    const int msh = RB == 1 ? 0 : (RB - 1) * __ldg(&c.chk_nspec[ch0 + k]);
                     int op_next = o0 < o1 ? __ldg(&c.chk_op[o0]) : 0;
                     for (int o = o0; o < o1; ++o) {
                         const int op = op_next;
@@ -1000,23 +1020,36 @@ __global__ void __launch_bounds__(8 * TPM + 32, (sizeof(T) == 4 ? 3 : 1)) k_m2l_
                         const int code = op >> 16, pid = code >> 3;
                         const int s0 = stride[pid][0], s1 = stride[pid][1], s2 = stride[pid][2];
                         const C* gs = base + (size_t)(op & 255) * NFpad;
-                        const C* ms = base + (size_t)((op >> 8) & 255) * NFpad + (size_t)l * N;
-                        // permuted index of sample (x, y, z): f0(x) s0 + f1(y) s1 + f2(z) s2
-                        const int rowb = ((code & 2) ? yn : y) * s1 + ((code & 4) ? zn : z) * s2;
+                        // source block b sits at nsp + (b - nsp) * RB blocks
+                        const C* msrc = base + (size_t)(((op >> 8) & 255) * RB - msh) * NFpad;
                         const int xneg = code & 1;
-                        const int b1 = xneg ? rowb + N * s0 : rowb;   // x >= 1: b1 + x * dx
                         const int dx = xneg ? -s0 : s0;
-                        cfma(acc[0], gs[rowb], ms[0]);
 #pragma unroll
-                        for (int x = 1; x < NX; ++x)
-                            if (x < N) cfma(acc[x], gs[b1 + x * dx], ms[x]);
+                        for (int j = 0; j < ROWS; ++j) {
+                            if (j == 0 || act[j]) {
+                                // permuted index of sample (x, y, z): f0(x) s0 + f1(y) s1 + f2(z) s2
+                                const int rowb = ((code & 2) ? yn[j] : yv[j]) * s1 + ((code & 4) ? zn[j] : zv[j]) * s2;
+                                const int b1 = xneg ? rowb + N * s0 : rowb;   // x >= 1: b1 + x * dx
+                                const C* ms = msrc + (size_t)row[j] * N;
+                                const C g0 = gs[rowb];
+#pragma unroll
+                                for (int rr = 0; rr < RB; ++rr) cfma(acc[j][rr][0], g0, ms[(size_t)rr * NFpad]);
+#pragma unroll
+                                for (int x = 1; x < NX; ++x)
+                                    if (x < N) {
+                                        const C gx = gs[b1 + x * dx];
+#pragma unroll
+                                        for (int rr = 0; rr < RB; ++rr) cfma(acc[j][rr][x], gx, ms[(size_t)rr * NFpad + x]);
+                                    }
+                            }
+                        }
                     }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[st]);
             }
         }
-        __syncthreads();   // every chunk of this right-hand side consumed (or the block gave up)
+        __syncthreads();   // every chunk of this pass consumed (or the block gave up)
         if (abort_sh) {
             if (threadIdx.x == 0) {   // bounded drain of copies issued but never waited for
                 const int first = abort_at < nchunks ? abort_at : 0;
@@ -1027,59 +1060,80 @@ __global__ void __launch_bounds__(8 * TPM + 32, (sizeof(T) == 4 ? 3 : 1)) k_m2l_
             return;
         }
         use0 += nchunks;
-        // F2L of every member in parallel: member m uses its own arrays and its TPM threads
-        C* Lh = ring + (size_t)(member ? m : 0) * (NF + p * NN + p * p * N);
-        C* T1 = Lh + NF;
-        C* T2 = T1 + p * NN;
-        if (active) {
+        // F2L of every member in parallel, one right-hand side at a time; member
+        // m uses its own arrays (aliasing the drained ring) and its TPM threads
+        C* Tx = ring + (size_t)(member ? m : 0) * (NN * p + N * p * p);   // [z][y][ax]
+        C* Ty = Tx + NN * p;                                               // [z][ay][ax]
+        const int te = member ? c.grp_members[mem0 + m] : 0;
 #pragma unroll
-            for (int x = 0; x < NX; ++x)
-                if (x < N) Lh[l * N + x] = acc[x];
+        for (int rr = 0; rr < RB; ++rr) {
+            if (rr >= nrb) break;
+#pragma unroll
+            for (int j = 0; j < ROWS; ++j)
+                if (act[j])   // x: p outputs of the row, in registers
+                    for (int ax = 0; ax < p; ++ax) {
+                        C s = acc[j][rr][0];
+#pragma unroll
+                        for (int x = 1; x < NX; ++x)
+                            if (x < N) cfma(s, acc[j][rr][x], tws[(x * ax) % N]);
+                        Tx[row[j] * p + ax] = s;
+                    }
+            __syncthreads();
+            if (member)
+                for (int q = l; q < N * p * p; q += TPM) {  // y
+                    const int ax = q % p, ay = (q / p) % p, zz = q / (p * p);
+                    C s = czero<C>();
+                    for (int k = 0; k < N; ++k) cfma(s, Tx[(zz * N + k) * p + ax], tws[(k * ay) % N]);
+                    Ty[q] = s;
+                }
+            __syncthreads();
+            if (member)
+                for (int a = l; a < P3; a += TPM) {  // z, crop, 1/N^3
+                    const int ax = a % p, ay = (a / p) % p, az = a / (p * p);
+                    C s = czero<C>();
+                    for (int k = 0; k < N; ++k) cfma(s, Ty[(k * p + ay) * p + ax], tws[(k * az) % N]);
+                    L[((int64_t)te * R + r0 + rr) * P3 + a] = cscale(s, scale);
+                }
+            __syncthreads();   // Tx, Ty reused by the next right-hand side / the next pass's ring
         }
-        __syncthreads();
-        if (member)
-            for (int q = l; q < p * NN; q += TPM) {  // z
-                const int xy = q % NN, az = q / NN;
-                C s = czero<C>();
-                for (int k = 0; k < N; ++k) cfma(s, Lh[k * NN + xy], tws[(k * az) % N]);
-                T1[q] = s;
-            }
-        __syncthreads();
-        if (member)
-            for (int q = l; q < p * p * N; q += TPM) {  // y
-                const int xx = q % N, ay = (q / N) % p, az = q / (N * p);
-                C s = czero<C>();
-                for (int k = 0; k < N; ++k) cfma(s, T1[(az * N + k) * N + xx], tws[(k * ay) % N]);
-                T2[q] = s;
-            }
-        __syncthreads();
-        if (member) {
-            const int te = c.grp_members[mem0 + m];
-            for (int a = l; a < P3; a += TPM) {  // x, crop, 1/N^3
-                const int ax = a % p, rest = a / p;
-                C s = czero<C>();
-                for (int k = 0; k < N; ++k) cfma(s, T2[rest * N + k], tws[(k * ax) % N]);
-                L[((int64_t)te * R + r) * P3 + a] = cscale(s, scale);
-            }
-        }
-        __syncthreads();   // the F2L arrays alias the ring: done before the next right-hand side
     }
 }
 
-// Ring depth S and the dynamic shared memory of the M2L kernels: three stages
-// of chk_max_blocks blocks when they fit, else two; the F2L arrays (of one
-// member, or of all 8 for the row kernel) reuse the same memory.
-template <typename T> __host__ void m2l_shape(const DevCommon& c, int members, int* S, size_t* smem) {
-    const size_t stage = (size_t)c.chk_max_blocks * c.NFpad * sizeof(typename Cplx<T>::type);
+// Ring depth S and the dynamic shared memory of the per-sample M2L kernel:
+// three stages of the largest chunk when they fit, else two; the F2L arrays of
+// one member reuse the same memory.
+template <typename T> __host__ void m2l_shape(const DevCommon& c, int* S, size_t* smem) {
+    const size_t stage = (size_t)c.chk_stage_blocks[0] * c.NFpad * sizeof(typename Cplx<T>::type);
     int ss = kM2LMaxStages;
     while (ss > 2 && (size_t)ss * stage > kSmemLimit) --ss;
     const size_t ring = (size_t)ss * stage;
-    const size_t f2l = (size_t)members * ((size_t)c.NF + (size_t)c.p * c.N * c.N + (size_t)c.p * c.p * c.N) *
+    const size_t f2l = ((size_t)c.NF + (size_t)c.p * c.N * c.N + (size_t)c.p * c.p * c.N) *
                        sizeof(typename Cplx<T>::type);
     *S = ss;
     *smem = ring > f2l ? ring : f2l;
 }
 
+// Shape of a row-kernel launch with RB right-hand sides per pass: the stage
+// (in elements), the ring depth S (three stages if they fit in the shared
+// memory one block may use at the wanted residency, else two) and the dynamic
+// shared memory (ring, or the F2L arrays of 8 members if larger).  Returns
+// false if two stages or the F2L arrays do not fit in one block.
+template <typename T> __host__ bool m2l_rows_shape(const DevCommon& c, int RB, int blocks_per_sm, int* S,
+                                                   int* stage_elems, size_t* smem) {
+    const int v = RB == 1 ? 0 : (RB == 2 ? 1 : 2);
+    const size_t esz = sizeof(typename Cplx<T>::type);
+    *stage_elems = c.chk_stage_blocks[v] * c.NFpad;
+    const size_t stage = (size_t)*stage_elems * esz;
+    size_t budget = (228 * 1024) / (size_t)(blocks_per_sm < 1 ? 1 : blocks_per_sm) - 1024 - 2048;
+    if (budget > kSmemLimit) budget = kSmemLimit;
+    const size_t f2l = 8 * ((size_t)c.N * c.N * c.p + (size_t)c.N * c.p * c.p) * esz;
+    int ss = kM2LMaxStages;
+    while (ss > 2 && (size_t)ss * stage > budget) --ss;
+    const size_t ring = (size_t)ss * stage;
+    *S = ss;
+    *smem = ring > f2l ? ring : f2l;
+    return *smem <= kSmemLimit;
+}
 // ------------------------------------------------------------------ L2L
 // One warp per son expansion (entry: son id, octant, first, count into the
 // list of father expansions feeding it), the transpose of M2M:
@@ -1604,6 +1658,96 @@ cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ M2L launch
+// Right-hand sides per row-kernel pass (complex64): the plan's choice when set,
+// else 4 for N <= 8 (2 for two or three right-hand sides), 2 for N = 9 and 1
+// for longer rows, whose accumulators would not fit in registers.
+__host__ int m2l_pick_rb(const DevCommon& c, int R) {
+    if (R == 1) return 1;
+    int rb = c.m2l_rb > 0 ? c.m2l_rb : (c.N <= 8 ? (R >= 4 ? 4 : 2) : 2);
+    if (c.N > 9) return 1;
+    if (c.N == 9 && rb > 2) rb = 2;
+    return rb >= 4 ? 4 : (rb >= 2 ? 2 : 1);
+}
+
+template <typename T, int NX, int TPM, int ROWS, int RB, int MINB, int PC, int NC>
+__host__ cudaError_t rows_config() {
+    auto k = k_m2l_rows<T, NX, TPM, ROWS, RB, MINB, PC, NC>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+    if (e != cudaSuccess) return e;
+    // the row kernel's occupancy is set by shared memory: ask for the largest carveout
+    return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
+// Launches one row-kernel variant; *fits = false (nothing launched) when its
+// ring or F2L arrays do not fit in one block's shared memory.
+template <typename T, int NX, int TPM, int ROWS, int RB, int MINB, int PC, int NC>
+__host__ void rows_launch(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w, cudaStream_t stream,
+                          bool* fits) {
+    int S, stage;
+    size_t sm;
+    *fits = m2l_rows_shape<T>(c, RB, MINB, &S, &stage, &sm);
+    if (!*fits) return;
+    k_m2l_rows<T, NX, TPM, ROWS, RB, MINB, PC, NC><<<(unsigned)c.n_grp, 8 * TPM + 32, sm, stream>>>(
+        c, t, w.Mhat, w.L, w.R, S, stage);
+}
+
+// The Hadamard M2L + F2L of one apply: the row kernel for N <= 12 (rows of N
+// samples; N <= 8: 64 threads per member, N = 9: 96, N = 10..12: 64 threads
+// with two rows each), the per-sample kernel beyond.
+template <typename T>
+cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w, cudaStream_t stream) {
+    constexpr bool F = sizeof(T) == 4;
+    const int N = c.N, p = c.p;
+    bool fits = false;
+    if (N <= 8) {
+        if constexpr (F) {
+            const int rb = m2l_pick_rb(c, w.R);
+            if (p == 4 && N == 7) {
+                if (rb == 1) rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(c, t, w, stream, &fits);
+                else if (rb == 2) rows_launch<T, 8, 64, 1, 2, 2, 4, 7>(c, t, w, stream, &fits);
+                else rows_launch<T, 8, 64, 1, 4, 1, 4, 7>(c, t, w, stream, &fits);
+            } else {
+                if (rb == 1) rows_launch<T, 8, 64, 1, 1, 3, 0, 0>(c, t, w, stream, &fits);
+                else if (rb == 2) rows_launch<T, 8, 64, 1, 2, 2, 0, 0>(c, t, w, stream, &fits);
+                else rows_launch<T, 8, 64, 1, 4, 1, 0, 0>(c, t, w, stream, &fits);
+            }
+        } else {
+            if (p == 4 && N == 7) rows_launch<T, 8, 64, 1, 1, 1, 4, 7>(c, t, w, stream, &fits);
+            else rows_launch<T, 8, 64, 1, 1, 1, 0, 0>(c, t, w, stream, &fits);
+        }
+    } else if (N <= 12) {
+        if (p == 5 && N == 9) {
+            bool one = true;
+            if constexpr (F) {
+                one = m2l_pick_rb(c, w.R) == 1;
+                if (!one) rows_launch<T, 9, 96, 1, 2, 1, 5, 9>(c, t, w, stream, &fits);
+            }
+            if (one) rows_launch<T, 9, 96, 1, 1, 1, 5, 9>(c, t, w, stream, &fits);
+        } else if (p == 6 && N == 11) {
+            rows_launch<T, 12, 64, 2, 1, 1, 6, 11>(c, t, w, stream, &fits);
+        } else {
+            rows_launch<T, 12, 64, 2, 1, 1, 0, 0>(c, t, w, stream, &fits);
+        }
+    }
+    if (fits) return cudaSuccess;
+    int S;
+    size_t sm;
+    m2l_shape<T>(c, &S, &sm);
+    if (sm > kSmemLimit) return cudaErrorInvalidConfiguration;
+    if (c.NF <= 512) {          // two samples per thread, at most 256 threads
+        const int threads = ((c.NF + 1) / 2 + 31) / 32 * 32;
+        k_m2l<T, 2, 256><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, w.R, S);
+    } else if (c.NF <= 1024) {  // four samples per thread, at most 256 threads
+        const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
+        k_m2l<T, 4, 256><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, w.R, S);
+    } else {                    // four samples per thread, up to 1024 threads
+        const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
+        k_m2l<T, 4, 1024><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, w.R, S);
+    }
+    return cudaSuccess;
+}
+
 // ------------------------------------------------------------------ orchestration
 template <typename T>
 cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w,
@@ -1702,26 +1846,8 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     err = cudaMemsetAsync(w.L, 0, (size_t)w.nL * R * c.P3 * sizeof(C), stream);
     if (err != cudaSuccess) return err;
     if (c.n_grp > 0) {
-        int S, S8;
-        size_t sm, sm8;
-        m2l_shape<T>(c, 1, &S, &sm);
-        m2l_shape<T>(c, 8, &S8, &sm8);
-        if (c.N <= 8 && sm8 <= kSmemLimit) {         // rows of N <= 8 samples (N^2 <= 64), 64 threads per member
-            if (c.p == 4 && c.N == 7) k_m2l_rows<T, 8, 64, 4, 7><<<(unsigned)c.n_grp, 512 + 32, sm8, stream>>>(c, t, w.Mhat, w.L, R, S8);
-            else k_m2l_rows<T, 8, 64><<<(unsigned)c.n_grp, 512 + 32, sm8, stream>>>(c, t, w.Mhat, w.L, R, S8);
-        } else {
-            if (sm > kSmemLimit) return cudaErrorInvalidConfiguration;
-            if (c.NF <= 512) {          // two samples per thread, at most 256 threads
-                const int threads = ((c.NF + 1) / 2 + 31) / 32 * 32;
-                k_m2l<T, 2, 256><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, S);
-            } else if (c.NF <= 1024) {  // four samples per thread, at most 256 threads
-                const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
-                k_m2l<T, 4, 256><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, S);
-            } else {                    // four samples per thread, up to 1024 threads
-                const int threads = ((c.NF + 3) / 4 + 31) / 32 * 32;
-                k_m2l<T, 4, 1024><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, R, S);
-            }
-        }
+        err = launch_m2l<T>(c, t, w, stream);
+        if (err != cudaSuccess) return err;
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -1773,11 +1899,21 @@ cudaError_t configure_kernels() {
     if ((e = cudaFuncSetAttribute(k_m2l<T, 2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<T, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<T, 4, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
-    // the row kernel's occupancy is set by shared memory: ask for the largest carveout
-    if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64, 4, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_m2l_rows<T, 8, 64, 4, 7>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 4) {
+        if ((e = rows_config<T, 8, 64, 1, 1, 3, 4, 7>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 2, 2, 4, 7>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 4, 1, 4, 7>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 1, 3, 0, 0>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 2, 2, 0, 0>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 4, 1, 0, 0>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 9, 96, 1, 2, 1, 5, 9>()) != cudaSuccess) return e;
+    } else {
+        if ((e = rows_config<T, 8, 64, 1, 1, 1, 4, 7>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 1, 1, 0, 0>()) != cudaSuccess) return e;
+    }
+    if ((e = rows_config<T, 9, 96, 1, 1, 1, 5, 9>()) != cudaSuccess) return e;
+    if ((e = rows_config<T, 12, 64, 2, 1, 1, 6, 11>()) != cudaSuccess) return e;
+    if ((e = rows_config<T, 12, 64, 2, 1, 1, 0, 0>()) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T, 4, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T, 5, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2m<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;

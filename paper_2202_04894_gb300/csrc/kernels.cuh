@@ -41,6 +41,8 @@ struct DevCommon {
     const int32_t *grp_member_off, *grp_members, *grp_chunk_off;  int64_t n_grp;
     const int32_t *chk_blk_off, *chk_nspec, *chk_blk, *chk_op_off, *chk_op;
     int chk_max_blocks;
+    int chk_stage_blocks[3];  // largest stage (blocks) for 1, 2, 4 right-hand sides per pass
+    int m2l_rb;               // right-hand sides per M2L pass (0: chosen from nrhs and N)
     const int32_t* p2m_cells;  int64_t n_p2m;
     const int32_t* l2p_cells;  int64_t n_l2p;
     // near field: work units (leaf x bounded source ranges) and leaves

@@ -435,7 +435,10 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
 
     // ---- M2L groups and chunks (sibling targets sharing a father and a direction)
     {
-        const int max_blocks = std::max(2, std::min(31, 22528 / (hp.NFpad * 8)));
+        // blocks per chunk: about 22 KB of complex64 for N <= 8; for longer DFTs
+        // up to 8, as long as two stages of complex128 fit in shared memory
+        const int max_blocks = hp.N <= 8 ? std::max(2, std::min(31, 22528 / (hp.NFpad * 8)))
+                                         : std::max(2, std::min(8, 115200 / (hp.NFpad * 16)));
         hp.chk_max_blocks = max_blocks;
         struct Op { int32_t member, src_parent, src, spec, code; };
         std::unordered_map<int64_t, int32_t> group_of;   // (father cell, direction) -> group
@@ -497,6 +500,8 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
                     ++i;
                 }
                 const int32_t nsp = (int32_t)specs.size();
+                for (int v = 0; v < 3; ++v)   // stage size when 1, 2, 4 right-hand sides share it
+                    hp.chk_stage_blocks[v] = std::max(hp.chk_stage_blocks[v], nsp + (1 << v) * (int32_t)srcs.size());
                 hp.chk_nspec.push_back(nsp);
                 hp.chk_blk.insert(hp.chk_blk.end(), specs.begin(), specs.end());
                 hp.chk_blk.insert(hp.chk_blk.end(), srcs.begin(), srcs.end());

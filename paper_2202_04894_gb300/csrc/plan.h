@@ -111,6 +111,9 @@ struct HostPlan {
     std::vector<int32_t> chk_op_off;                    // 9 per chunk: op ranges of members 0..7, end
     std::vector<int32_t> chk_op;                        // spec_blk | mhat_blk << 8 | code << 16
     int32_t chk_max_blocks = 0;
+    // largest stage in blocks when RB = 1, 2, 4 right-hand sides share it:
+    // max over chunks of (spectra + RB * multipoles)
+    int32_t chk_stage_blocks[3] = {0, 0, 0};
 
     // M2M per level (parent level l): entries of 9 ints: parent exp, 8 child exps (-1)
     std::vector<std::vector<int32_t>> m2m_lvl;

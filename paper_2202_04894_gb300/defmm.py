@@ -22,7 +22,8 @@ _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
 
 EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_apply_host",
             "defmm_destroy", "defmm_plan_info", "defmm_plan_table", "defmm_profile_enable",
-            "defmm_profile_read", "defmm_apply_noalloc", "defmm_last_error"]
+            "defmm_profile_read", "defmm_apply_noalloc", "defmm_plan_set_tuning",
+            "defmm_plan_get_tuning", "defmm_last_error"]
 PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 
 
@@ -43,6 +44,10 @@ class Info(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("launches_per_apply", ctypes.c_int64),
                 ("device_error", ctypes.c_int64),
                 ("d_aabb", ctypes.c_double), ("cube_side", ctypes.c_double)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("m2l_rhs_block", ctypes.c_int)]
 
 
 class DefmmError(RuntimeError):
@@ -84,6 +89,10 @@ def lib():
         L.defmm_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]
         L.defmm_profile_read.restype = ctypes.c_int
+        L.defmm_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        L.defmm_plan_set_tuning.restype = ctypes.c_int
+        L.defmm_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        L.defmm_plan_get_tuning.restype = ctypes.c_int
         L.defmm_last_error.argtypes = []
         L.defmm_last_error.restype = ctypes.c_char_p
         _LIB = L
@@ -180,6 +189,16 @@ class Plan:
         n = ctypes.c_int()
         _check(lib().defmm_profile_read(self._h, buf, len(PHASES), ctypes.byref(n)))
         return {PHASES[i]: buf[i] for i in range(n.value)}
+
+    def set_tuning(self, m2l_rhs_block: int = 0):
+        """defmm_plan_set_tuning: launch choices of later applies (results unchanged)."""
+        t = Tuning(int(m2l_rhs_block))
+        _check(lib().defmm_plan_set_tuning(self._h, ctypes.byref(t)))
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().defmm_plan_get_tuning(self._h, ctypes.byref(t)))
+        return {"m2l_rhs_block": t.m2l_rhs_block}
 
     def table(self, name: str) -> np.ndarray:
         n = ctypes.c_int64()

@@ -88,6 +88,20 @@ def test_argument_errors():
     assert e.value.status == 5
 
 
+def test_tuning_values():
+    """Apply-time tuning takes 0, 1, 2, 4 right-hand sides per M2L pass and rejects others."""
+    pl = _host_plan(W.points("sphere", 300, 2), kappa=2.0, order=4, leaf_size=16)
+    assert pl.tuning() == {"m2l_rhs_block": 0}
+    for v in (1, 2, 4, 0):
+        pl.set_tuning(m2l_rhs_block=v)
+        assert pl.tuning()["m2l_rhs_block"] == v
+    for v in (3, -1, 8):
+        with pytest.raises(defmm.DefmmError) as e:
+            pl.set_tuning(m2l_rhs_block=v)
+        assert e.value.status == 1
+    assert pl.tuning()["m2l_rhs_block"] == 0
+
+
 def _oracle_tables(op):
     cells = np.stack([op.tt.level, op.tt.coords[:, 0], op.tt.coords[:, 1], op.tt.coords[:, 2],
                       op.tt.begin, op.tt.end, op.tt.parent], 1)
