@@ -149,6 +149,53 @@ typedef struct {
 defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning);
 defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning);
 
+/* Autotuned plan.  The paper sets Ncrit, the order and the FFT length by hand
+ * per experiment (Sec. 6); this entry point picks, by timing applies on the
+ * caller's geometry, the choices that change only the speed:
+ *  - leaf size Ncrit among 16, 24, 32, 48, 64 within [leaf_min, leaf_max]
+ *    (leaf_max itself is always a candidate),
+ *  - DFT length N among 2p-1 and 2p when opt->fft_n is 0 and tune_fft_n is
+ *    set (any N >= 2p-1 gives the same result, Sec. 2.3),
+ *  - right-hand sides per M2L pass (1, 2, 4) when nrhs > 1 and complex64.
+ * A smaller Ncrit changes the tree and so the approximation (within the
+ * order's accuracy); the other two choices change no result.
+ * Each candidate plan is built with defmm_plan_create, applied to a fixed
+ * charge block of nrhs columns (device buffers allocated for the call) and
+ * timed with CUDA events on `stream` (median of reps applies after two
+ * warm-ups).  Candidates over opt->hbm_budget are skipped.  The fastest plan
+ * is returned in *out (owned by the caller, free with defmm_destroy) and its
+ * choice in *result (may be NULL).
+ *  cache_path - NULL, or a text file of earlier choices ("defmm-tune <key>
+ *               <leaf> <fft_n> <m2l_rhs_block> <ms>" lines, key a hash of the
+ *               coordinates, sizes, kappa, order, nrhs, dtype, candidate range
+ *               and plan options).  A matching line builds the plan with the
+ *               stored choice without timing (result->from_cache = 1); after
+ *               a tuning run a line is appended.
+ * X, nx, Y, ny, kappa, order, opt, stream: as in defmm_plan_create.
+ * Errors: those of defmm_plan_create and defmm_apply; DEFMM_ERR_ARG for a bad
+ * range, nrhs or reps, or an unwritable cache file; DEFMM_ERR_OOM when no
+ * candidate fits; DEFMM_ERR_TIMEOUT if a device-side wait gave up.          */
+typedef struct {
+    int leaf_min, leaf_max;  /* Ncrit range (default 16..64) */
+    int nrhs;                /* columns the plan will be applied to (default 1) */
+    defmm_dtype dtype;       /* arithmetic of those applies (default DEFMM_C64) */
+    int reps;                /* timed applies per candidate (default 5) */
+    int tune_fft_n;          /* also try N = 2p (default 1) */
+    const char* cache_path;  /* tune cache file or NULL (default NULL) */
+} defmm_tune_options;
+
+typedef struct {
+    int leaf_size, fft_n, m2l_rhs_block; /* the choice (fft_n 0: 2p-1) */
+    double ms;                           /* its median apply time when timed */
+    int candidates;                      /* configurations timed (0 from the cache) */
+    int from_cache;                      /* 1 if the choice came from cache_path */
+} defmm_tune_result;
+
+void defmm_default_tune_options(defmm_tune_options* topt);
+defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa,
+                                 int order, const defmm_options* opt, const defmm_tune_options* topt,
+                                 void* stream, defmm_plan* out, defmm_tune_result* result);
+
 /* Frees the plan and its device memory (synchronises the device first).       */
 defmm_status defmm_destroy(defmm_plan plan);
 

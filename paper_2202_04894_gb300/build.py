@@ -26,6 +26,7 @@ SOURCES = [
     ("capi.cu", "nvcc"),
     ("noalloc.cu", "nvcc"),
     ("serve.cu", "nvcc"),
+    ("tune.cu", "nvcc"),
 ]
 
 

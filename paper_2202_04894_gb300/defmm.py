@@ -23,7 +23,8 @@ _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
 EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_apply_host",
             "defmm_destroy", "defmm_plan_info", "defmm_plan_table", "defmm_profile_enable",
             "defmm_profile_read", "defmm_apply_noalloc", "defmm_plan_set_tuning",
-            "defmm_plan_get_tuning", "defmm_last_error"]
+            "defmm_plan_get_tuning", "defmm_default_tune_options", "defmm_plan_autotune",
+            "defmm_last_error"]
 PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 
 
@@ -48,6 +49,17 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("m2l_rhs_block", ctypes.c_int)]
+
+
+class TuneOptions(ctypes.Structure):
+    _fields_ = [("leaf_min", ctypes.c_int), ("leaf_max", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("reps", ctypes.c_int), ("tune_fft_n", ctypes.c_int),
+                ("cache_path", ctypes.c_char_p)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("fft_n", ctypes.c_int), ("m2l_rhs_block", ctypes.c_int),
+                ("ms", ctypes.c_double), ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int)]
 
 
 class DefmmError(RuntimeError):
@@ -93,6 +105,12 @@ def lib():
         L.defmm_plan_set_tuning.restype = ctypes.c_int
         L.defmm_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
         L.defmm_plan_get_tuning.restype = ctypes.c_int
+        L.defmm_default_tune_options.argtypes = [ctypes.POINTER(TuneOptions)]
+        L.defmm_default_tune_options.restype = None
+        L.defmm_plan_autotune.argtypes = [vp, i64, vp, i64, dbl, ctypes.c_int, ctypes.POINTER(Options),
+                                          ctypes.POINTER(TuneOptions), vp, ctypes.POINTER(vp),
+                                          ctypes.POINTER(TuneResult)]
+        L.defmm_plan_autotune.restype = ctypes.c_int
         L.defmm_last_error.argtypes = []
         L.defmm_last_error.restype = ctypes.c_char_p
         _LIB = L
@@ -252,3 +270,34 @@ class Plan:
                                       R, C64 if qm.dtype == torch.complex64 else C128, _stream_handle(stream)))
         res = pc.t()
         return res[:, 0] if squeeze else res
+
+
+def autotune(X, Y=None, kappa=1.0, order=4, nrhs=1, dtype=C64, leaf_range=(16, 64), reps=5,
+             tune_fft_n=True, cache_path=None, stream=None, **options):
+    """defmm_plan_autotune: the fastest of the candidate plans for this geometry.
+
+    Returns (plan, choice) with choice = {leaf_size, fft_n, m2l_rhs_block, ms,
+    candidates, from_cache}.  The timing runs in the library (CUDA events on
+    ``stream``); this function only marshals arguments.
+    """
+    Xh = Plan._points(X)
+    Yh = None if Y is None else Plan._points(Y)
+    opt = default_options(**options)
+    t = TuneOptions()
+    lib().defmm_default_tune_options(ctypes.byref(t))
+    t.leaf_min, t.leaf_max = int(leaf_range[0]), int(leaf_range[1])
+    t.nrhs, t.dtype, t.reps, t.tune_fft_n = int(nrhs), int(dtype), int(reps), 1 if tune_fft_n else 0
+    t.cache_path = None if cache_path is None else os.fsencode(cache_path)
+    h = ctypes.c_void_p()
+    r = TuneResult()
+    _check(lib().defmm_plan_autotune(
+        ctypes.c_void_p(Xh.data_ptr()), Xh.shape[0],
+        None if Yh is None else ctypes.c_void_p(Yh.data_ptr()),
+        Xh.shape[0] if Yh is None else Yh.shape[0], float(kappa), int(order), ctypes.byref(opt),
+        ctypes.byref(t), _stream_handle(stream), ctypes.byref(h), ctypes.byref(r)))
+    plan = Plan.__new__(Plan)
+    plan._h = h
+    plan._keep = None
+    plan.nx = Xh.shape[0]
+    plan.ny = Xh.shape[0] if Yh is None else Yh.shape[0]
+    return plan, {name: getattr(r, name) for name, _ in TuneResult._fields_}

@@ -149,3 +149,18 @@ def test_degenerate_inputs_host_plan():
     dup = np.repeat(np.array([[1.0, 2.0, 3.0]]), 10, axis=0)
     pl = _host_plan(dup, kappa=3.0, order=4, leaf_size=3)
     assert pl.info()["nlevels"] == 22
+
+
+def test_autotune_argument_errors():
+    """defmm_plan_autotune validates its arguments before touching a GPU."""
+    X = W.points("sphere", 100, 1)
+    for kw in (dict(leaf_range=(0, 64)), dict(leaf_range=(64, 32)), dict(nrhs=0), dict(reps=0)):
+        with pytest.raises(defmm.DefmmError) as e:
+            defmm.autotune(X, kappa=1.0, order=4, **kw)
+        assert e.value.status == 1
+    with pytest.raises(defmm.DefmmError) as e:
+        defmm.autotune(X, kappa=1.0, order=1)
+    assert e.value.status == 1
+    with pytest.raises(defmm.DefmmError) as e:
+        defmm.autotune(X, kappa=1.0, order=4, flags=defmm.PLAN_HOST_ONLY)
+    assert e.value.status == 5
