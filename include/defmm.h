@@ -132,18 +132,30 @@ defmm_status defmm_apply_noalloc(defmm_plan plan, const void* q, void* p, int nr
                                  defmm_dtype dtype, void* stream);
 
 /* Apply-time tuning of a plan.  The paper has no counterpart: these are
- * launch choices of this library's kernels, and no result depends on them
- * (every output is bit-for-bit the same under any admissible value).
- *  m2l_rhs_block - right-hand sides that share one pass of the complex64 M2L
- *                  kernel over a staged chunk of spectra and multipoles
- *                  (1, 2 or 4; 0 = the library's choice from nrhs and the DFT
- *                  length).  Values the kernel for the plan's DFT length
- *                  cannot take are lowered (N = 9: at most 2; N > 9: 1).
+ * launch choices of this library's kernels.
+ *  m2l_rhs_block  - right-hand sides that share one pass of the complex64 M2L
+ *                   kernel over a staged chunk of spectra and multipoles
+ *                   (1, 2 or 4; 0 = the library's choice from nrhs and the
+ *                   DFT length).  Values the kernel for the plan's DFT length
+ *                   cannot take are lowered (N = 9: at most 2; N > 9: 1).
+ *                   No output depends on it (bit for bit).
+ *  p2p_tc_min_rhs - complex64 applies with at least this many right-hand
+ *                   sides form the near field (Sec. 5.3) as tensor-core
+ *                   products, 32 columns per pass, with three tf32 products
+ *                   per operand pair (single-precision accuracy); fewer
+ *                   columns use the CUDA-core kernel.  0 (the default) never
+ *                   uses the tensor cores: with leaves of ~20 targets their
+ *                   per-tile overhead makes them slower than the CUDA cores on
+ *                   the measured workloads; defmm_plan_autotune times both.
+ *                   The two kernels round differently (both within
+ *                   single-precision accuracy of the same sum).
  * The setting applies to applies enqueued after the call; CUDA graphs
  * captured earlier keep the value they were captured with.
- * Errors: DEFMM_ERR_ARG (NULL plan or tuning, value not in {0, 1, 2, 4}).    */
+ * Errors: DEFMM_ERR_ARG (NULL plan or tuning, m2l_rhs_block not in
+ * {0, 1, 2, 4}, p2p_tc_min_rhs < 0).                                         */
 typedef struct {
     int m2l_rhs_block;
+    int p2p_tc_min_rhs;
 } defmm_tuning;
 
 defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning);
@@ -156,9 +168,12 @@ defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning);
  *    (leaf_max itself is always a candidate),
  *  - DFT length N among 2p-1 and 2p when opt->fft_n is 0 and tune_fft_n is
  *    set (any N >= 2p-1 gives the same result, Sec. 2.3),
- *  - right-hand sides per M2L pass (1, 2, 4) when nrhs > 1 and complex64.
+ *  - right-hand sides per M2L pass (1, 2, 4) when nrhs > 1 and complex64,
+ *  - the tensor-core near field on or off when nrhs >= 8 and complex64
+ *    (defmm_tuning.p2p_tc_min_rhs).
  * A smaller Ncrit changes the tree and so the approximation (within the
- * order's accuracy); the other two choices change no result.
+ * order's accuracy); the tensor-core near field changes rounding only; the
+ * other choices change no result.
  * Each candidate plan is built with defmm_plan_create, applied to a fixed
  * charge block of nrhs columns (device buffers allocated for the call) and
  * timed with CUDA events on `stream` (median of reps applies after two
@@ -166,7 +181,7 @@ defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning);
  * is returned in *out (owned by the caller, free with defmm_destroy) and its
  * choice in *result (may be NULL).
  *  cache_path - NULL, or a text file of earlier choices ("defmm-tune <key>
- *               <leaf> <fft_n> <m2l_rhs_block> <ms>" lines, key a hash of the
+ *               <leaf> <fft_n> <m2l_rhs_block> <tc> <ms>" lines, key a hash of the
  *               coordinates, sizes, kappa, order, nrhs, dtype, candidate range
  *               and plan options).  A matching line builds the plan with the
  *               stored choice without timing (result->from_cache = 1); after
@@ -186,6 +201,7 @@ typedef struct {
 
 typedef struct {
     int leaf_size, fft_n, m2l_rhs_block; /* the choice (fft_n 0: 2p-1) */
+    int p2p_tensor_cores;                /* 1: tensor-core near field chosen */
     double ms;                           /* its median apply time when timed */
     int candidates;                      /* configurations timed (0 from the cache) */
     int from_cache;                      /* 1 if the choice came from cache_path */

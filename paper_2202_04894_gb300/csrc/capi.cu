@@ -244,6 +244,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.chk_max_blocks = hp.chk_max_blocks;
     for (int v = 0; v < 3; ++v) c.chk_stage_blocks[v] = hp.chk_stage_blocks[v];
     c.m2l_rb = 0;
+    c.p2p_tc_min_rhs = 0;
     c.p2m_cells = (const int32_t*)P(o_p2m); c.n_p2m = (int64_t)hp.p2m_cells.size();
     c.l2p_cells = (const int32_t*)P(o_l2p); c.n_l2p = (int64_t)hp.l2p_cells.size();
     c.p2p_unit_leaf = (const int32_t*)P(o_pul); c.p2p_unit_off = (const int32_t*)P(o_puo);
@@ -322,14 +323,17 @@ defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning) 
     if (!plan || !tuning) return fail(DEFMM_ERR_ARG, "plan or tuning is NULL");
     const int rb = tuning->m2l_rhs_block;
     if (rb != 0 && rb != 1 && rb != 2 && rb != 4) return fail(DEFMM_ERR_ARG, "m2l_rhs_block must be 0, 1, 2 or 4");
+    if (tuning->p2p_tc_min_rhs < 0) return fail(DEFMM_ERR_ARG, "p2p_tc_min_rhs must be >= 0");
     std::lock_guard<std::mutex> g(plan->busy);
     plan->common.m2l_rb = rb;
+    plan->common.p2p_tc_min_rhs = tuning->p2p_tc_min_rhs;
     return DEFMM_OK;
 }
 
 defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning) {
     if (!plan || !tuning) return fail(DEFMM_ERR_ARG, "plan or tuning is NULL");
     tuning->m2l_rhs_block = plan->common.m2l_rb;
+    tuning->p2p_tc_min_rhs = plan->common.p2p_tc_min_rhs;
     return DEFMM_OK;
 }
 

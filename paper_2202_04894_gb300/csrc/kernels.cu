@@ -22,6 +22,7 @@
 #include "kernels.cuh"
 #include "plan.h"
 #include "symmetry.h"
+#include "tcgen05.cuh"
 
 namespace defmm {
 
@@ -1658,6 +1659,246 @@ cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, 
     return cudaGetLastError();
 }
 
+// Tensor-core near field for many right-hand sides (complex64).  With R
+// columns the near field of a work unit is the dense product
+//   P[t, r] = sum_s G(x_t, y_s) Q[s, r],
+// so per right-hand-side block of 32 columns one block computes it as a real
+// GEMM on the tcgen05 tensor cores, M = 64 rows (Re and Im of 32 columns),
+// N = the leaf's targets (a tile of <= 64, padded to a multiple of 8),
+// K = 2 x (sources of a tile of 16):
+//   D[(r, re), t] = sum_s Qr[s,r] Gr[t,s] - Qi[s,r] Gi[t,s],
+//   D[(r, im), t] = sum_s Qi[s,r] Gr[t,s] + Qr[s,r] Gi[t,s],
+// A = [[Qr, -Qi], [Qi, Qr]] interleaved per source (K index 2s + part),
+// B[(s, part), t] = (Gr, Gi)[t, s].  The kernel values G are formed on the
+// CUDA cores exactly as in k_p2p_f32 (hi + lo coordinates, reduced phase)
+// once per interaction for all 32 columns.  Each operand is split into a tf32
+// head and a tail (x = hi + lo, hi = tf32 rounding of x) and the three
+// products lo*hi + hi*lo + hi*hi of a tile of 16 sources are summed in f32 in
+// tensor memory (tf32 alone would leave ~1e-4 relative error).  The tensor
+// cores' accumulation truncates, so its error grows with the number of MMAs
+// summed into one accumulator: each tile therefore gets a fresh sum (12 MMAs)
+// in one of two tensor-memory buffers, and the threads add finished tiles, in
+// order, into f32 registers while the tensor cores work on the next tile.
+// Operands live in shared memory as K-major core matrices without swizzle;
+// two stages let the CUDA cores form the next tile while the tensor cores
+// consume the previous one (completion tracked by tcgen05.commit on
+// mbarriers).  Every wait is bounded; a wait that gives up raises the plan's
+// error flag, the block waits (bounded) for its issued MMAs, frees its tensor
+// memory and stops.
+constexpr int kTcSrc = 16;               // sources per tile: K = 32
+constexpr int kTcTgt = 64;               // targets per tile: N <= 64
+constexpr int kTcStageFloats = 4 * 2048; // A hi, A lo, B hi, B lo: 64 x 32 floats each
+constexpr size_t kTcSmem = 2 * kTcStageFloats * sizeof(float);
+
+// Offset (floats) of element (row, k) of a 64 x 32 K-major operand: core
+// matrix (k/4, row/8) at ((k/4)*8 + row/8) * 32 floats, row row%8 at +4*(row%8).
+__device__ __forceinline__ int tc_off(int row, int k) {
+    return (((k >> 2) << 3) + (row >> 3)) * 32 + ((row & 7) << 2) + (k & 3);
+}
+
+__device__ __forceinline__ void tc_split_store(float* hi, float* lo, int off, float a, float b) {
+    const float ah = tc::to_tf32(a), bh = tc::to_tf32(b);
+    *reinterpret_cast<float2*>(hi + off) = make_float2(ah, bh);
+    *reinterpret_cast<float2*>(lo + off) = make_float2(a - ah, b - bh);
+}
+
+__global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __restrict__ qs,
+                                                float2* __restrict__ part, int R, int rb0) {
+    extern __shared__ __align__(1024) float tsm[];
+    __shared__ float4 th[kTcTgt], tl[kTcTgt];      // target hi / lo coordinates
+    __shared__ float4 sh[kTcSrc], sl[kTcSrc];      // source hi / lo coordinates of the tile
+    __shared__ float2 qsm[kTcSrc][33];             // charges / (4 pi) of the tile, [source][column]
+    __shared__ int rbeg[kP2PRanges], roff[kP2PRanges + 1];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t taddr_sh;
+    __shared__ int fail_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int u = blockIdx.x;
+    const int cell = c.p2p_leaf[c.p2p_unit_leaf[u]];
+    const int tb = c.ct_beg[cell], te = c.ct_end[cell];
+    const int64_t pbase = c.p2p_part[u];
+    const int nr = min(32, R - rb0);
+    const float kap2pi = (float)(c.kappa * kInv2Pi);
+    const float eps2 = (float)(c.eps_self * c.eps_self);
+    const float inv4pi = (float)kInv4Pi;
+    const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fail_sh = 0;
+        mbar_fence_init();
+    }
+    if (warp == 0) tc::alloc(&taddr_sh, 128);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = taddr_sh;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    uint32_t uses[2] = {0, 0};   // commits issued on each stage's barrier (uniform)
+    bool unread[2] = {false, false};
+    int last_st = 0;
+    int N = 8;
+    // D row 16 w + i sits in TMEM lane 32 w + i (i < 16): Re rows from warps 0-1, Im from 2-3.
+    // acc[col] is this thread's row of the target tile, summed over the source tiles in
+    // f32 (each tile's own sum stays in the tensor cores, a short accumulation chain).
+    float acc[kTcTgt];
+#pragma unroll
+    for (int j = 0; j < kTcTgt; ++j) acc[j] = 0.f;
+    auto take = [&](int st) {    // adds the finished tile in TMEM buffer st to acc
+        tc::fence_after_sync();
+#pragma unroll
+        for (int cc = 0; cc < kTcTgt / 16; ++cc)
+            if (cc * 16 < N) {
+                float v[16];
+                tc::ld16(taddr + lane_base + (uint32_t)(64 * st + 16 * cc), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[16 * cc + j] += v[j];
+            }
+        tc::fence_before_sync();
+        unread[st] = false;
+    };
+    for (int t0 = tb; t0 < te; t0 += kTcTgt) {
+        const int nt = min(kTcTgt, te - t0);
+        N = (nt + 7) & ~7;
+        const uint32_t idesc = tc::idesc_tf32(64, N);
+        if (tid < nt) { th[tid] = c.Xh[t0 + tid]; tl[tid] = c.Xl[t0 + tid]; }
+        for (int g0 = r0; g0 < r1; g0 += kP2PRanges) {          // batches of ranges
+            const int ng = min(kP2PRanges, r1 - g0);
+            __syncthreads();
+            for (int k = tid; k < ng; k += blockDim.x) {
+                rbeg[k] = c.p2p_sbeg[g0 + k];
+                roff[k] = c.p2p_soff[g0 + k] - c.p2p_soff[g0];
+            }
+            if (tid == 0) roff[ng] = c.p2p_soff[g0 + ng - 1] - c.p2p_soff[g0] + c.p2p_send[g0 + ng - 1] - c.p2p_sbeg[g0 + ng - 1];
+            __syncthreads();
+            const int total = roff[ng];
+            auto source_of = [&](int f) {
+                int lo = 0, hi = ng - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (roff[mid] <= f) lo = mid; else hi = mid - 1;
+                }
+                return rbeg[lo] + (f - roff[lo]);
+            };
+            for (int f0 = 0; f0 < total; f0 += kTcSrc) {
+                const int ns = min(kTcSrc, total - f0);
+                const int st = (int)((uses[0] + uses[1]) & 1);
+                // the MMAs that last used this stage (its shared operands and its TMEM
+                // buffer) must be done before either is rewritten; their tile is taken
+                if (uses[st] > 0 && !mbar_wait(&bar[st], (uses[st] - 1) & 1)) fail_sh = 1;
+                if (unread[st]) take(st);
+                // stage the tile's sources and charges (coalesced over sources)
+                {
+                    const int s = tid & 15;
+                    int64_t j = -1;
+                    if (s < ns) j = source_of(f0 + s);
+                    if (tid < kTcSrc) {
+                        if (j >= 0) { sh[s] = c.Yh[j]; sl[s] = c.Yl[j]; }
+                        else { sh[s] = make_float4(0.f, 0.f, 0.f, 0.f); sl[s] = sh[s]; }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int r = (tid >> 4) + 8 * k;
+                        float2 q = make_float2(0.f, 0.f);
+                        if (j >= 0 && r < nr) {
+                            q = qs[(int64_t)(rb0 + r) * c.ny + j];
+                            q = make_float2(q.x * inv4pi, q.y * inv4pi);
+                        }
+                        qsm[s][r] = q;
+                    }
+                }
+                __syncthreads();
+                if (fail_sh) break;
+                float* Ahi = tsm + st * kTcStageFloats;
+                float* Alo = Ahi + 2048;
+                float* Bhi = Ahi + 4096;
+                float* Blo = Ahi + 6144;
+                // A: rows r (Re) and 32 + r (Im), columns 2s (Re q) and 2s + 1 (Im q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int s = warp + 4 * k, r = lane;
+                    const float2 q = qsm[s][r];
+                    tc_split_store(Ahi, Alo, tc_off(r, 2 * s), q.x, -q.y);
+                    tc_split_store(Ahi, Alo, tc_off(32 + r, 2 * s), q.y, q.x);
+                }
+                // B: kernel values of the tile, zero outside the targets and sources
+                for (int idx = tid; idx < N * kTcSrc; idx += blockDim.x) {
+                    const int t = idx % N, s = idx / N;
+                    float gr = 0.f, gi = 0.f;
+                    if (t < nt && s < ns) {
+                        const float4 xh = th[t], xl = tl[t], a = sh[s], b = sl[s];
+                        const float dx = (xh.x - a.x) + (xl.x - b.x);
+                        const float dy = (xh.y - a.y) + (xl.y - b.y);
+                        const float dz = (xh.z - a.z) + (xl.z - b.z);
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        float rinv = rsqrt_hw(r2);
+                        rinv = r2 > eps2 ? rinv : 0.f;
+                        float sn, cs;
+                        turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                        gr = cs * rinv;
+                        gi = sn * rinv;
+                    }
+                    tc_split_store(Bhi, Blo, tc_off(t, 2 * s), gr, gi);
+                }
+                tc::fence_smem_to_async();
+                __syncthreads();
+                if (tid == 0) {
+                    tc::fence_after_sync();
+                    const uint32_t d = taddr + (uint32_t)(64 * st);
+                    const uint32_t a0 = smem_u32(Ahi), l0 = smem_u32(Alo), b0 = smem_u32(Bhi), m0 = smem_u32(Blo);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {   // K = 8 per MMA: two core matrices along K
+                        const uint32_t o = ks * 2048;
+                        const uint64_t ah = tc::smem_desc(a0 + o, 1024, 128), al = tc::smem_desc(l0 + o, 1024, 128);
+                        const uint64_t bh = tc::smem_desc(b0 + o, 1024, 128), bl = tc::smem_desc(m0 + o, 1024, 128);
+                        tc::mma_tf32(d, al, bh, idesc, ks > 0);   // a fresh sum per tile
+                        tc::mma_tf32(d, ah, bl, idesc, true);
+                        tc::mma_tf32(d, ah, bh, idesc, true);
+                    }
+                    tc::commit(&bar[st]);
+                }
+                ++uses[st];
+                unread[st] = true;
+                last_st = st;
+            }
+            if (fail_sh) break;
+        }
+        if (fail_sh) break;
+        // take the last two tiles, older first
+        for (int k = 0; k < 2; ++k) {
+            const int st = k == 0 ? last_st ^ 1 : last_st;
+            if (!unread[st]) continue;
+            if (!mbar_wait(&bar[st], (uses[st] - 1) & 1)) fail_sh = 1;
+            take(st);   // warp-collective load: taken even after a failed wait (results dropped)
+        }
+        __syncthreads();
+        if (fail_sh) break;
+        if (lane < 16) {
+            const int r = (16 * warp + lane) & 31;
+            if (r < nr) {
+                float* dst = reinterpret_cast<float*>(part + (int64_t)(rb0 + r) * c.p2p_parts + pbase + (t0 - tb)) + (warp >= 2 ? 1 : 0);
+#pragma unroll
+                for (int j = 0; j < kTcTgt; ++j)
+                    if (j < nt) dst[2 * j] = acc[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kTcTgt; ++j) acc[j] = 0.f;
+    }
+    if (fail_sh) {
+        if (tid == 0) {
+            atomicExch(c.err_flag, 1);
+            // bounded wait for the MMAs already issued before the memory they use is released
+            if (uses[0] > 0) (void)mbar_wait(&bar[0], (uses[0] - 1) & 1);
+            if (uses[1] > 0) (void)mbar_wait(&bar[1], (uses[1] - 1) & 1);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    tc::fence_after_sync();
+    if (warp == 0) tc::dealloc(taddr, 128);
+}
+
 // ------------------------------------------------------------------ M2L launch
 // Right-hand sides per row-kernel pass (complex64): the plan's choice when set,
 // else 4 for N <= 8 (2 for two or three right-hand sides), 2 for N = 9 and 1
@@ -1784,7 +2025,18 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     DEFMM_CHECK_LAUNCH();
     DEFMM_MARK();
     // near field: work units write partial sums, reduced per target in fixed order
-    for (int rb0 = 0; rb0 < R; rb0 += (R == 1 ? 1 : 4)) {
+    bool p2p_done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        // many right-hand sides: the near field as tensor-core products, 32 columns per pass
+        if (c.p2p_tc_min_rhs > 0 && R >= c.p2p_tc_min_rhs && c.n_p2p_units > 0) {
+            for (int rb0 = 0; rb0 < R; rb0 += 32) {
+                k_p2p_tc<<<(unsigned)c.n_p2p_units, 128, kTcSmem, stream>>>(c, w.qs, w.part, R, rb0);
+                DEFMM_CHECK_LAUNCH();
+            }
+            p2p_done = true;
+        }
+    }
+    for (int rb0 = 0; rb0 < R && !p2p_done; rb0 += (R == 1 ? 1 : 4)) {
         if (c.n_p2p_units == 0) break;
         if constexpr (std::is_same<T, float>::value) {
             if (R == 1) k_p2p_f32<1><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
@@ -1828,6 +2080,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         const unsigned blocks = (unsigned)((m2m[l].n + wpb_mm - 1) / wpb_mm);
         if (c.p == 4) k_m2m<T, 4><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
         else if (c.p == 5) k_m2m<T, 5><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
+        else if (c.p == 6) k_m2m<T, 6><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
         else k_m2m<T><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
         DEFMM_CHECK_LAUNCH();
     }
@@ -1838,6 +2091,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         const unsigned blocks = (unsigned)((c.n_m2f + wpb - 1) / wpb);
         if (c.p == 4 && c.N == 7) k_m2f<T, 4, 7><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
         else if (c.p == 5 && c.N == 9) k_m2f<T, 5, 9><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
+        else if (c.p == 6 && c.N == 11) k_m2f<T, 6, 11><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
         else k_m2f<T><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
         DEFMM_CHECK_LAUNCH();
     }
@@ -1857,6 +2111,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         const unsigned blocks = (unsigned)((l2l[l].n + wpb_mm - 1) / wpb_mm);
         if (c.p == 4) k_l2l<T, 4><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);
         else if (c.p == 5) k_l2l<T, 5><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);
+        else if (c.p == 6) k_l2l<T, 6><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);
         else k_l2l<T><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);
         DEFMM_CHECK_LAUNCH();
     }
@@ -1900,6 +2155,7 @@ cudaError_t configure_kernels() {
     if ((e = cudaFuncSetAttribute(k_m2l<T, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2l<T, 4, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if constexpr (sizeof(T) == 4) {
+        if ((e = cudaFuncSetAttribute(k_p2p_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem)) != cudaSuccess) return e;
         if ((e = rows_config<T, 8, 64, 1, 1, 3, 4, 7>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 8, 64, 1, 2, 2, 4, 7>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 8, 64, 1, 4, 1, 4, 7>()) != cudaSuccess) return e;
@@ -1916,6 +2172,9 @@ cudaError_t configure_kernels() {
     if ((e = rows_config<T, 12, 64, 2, 1, 1, 0, 0>()) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T, 4, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2f<T, 5, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2f<T, 6, 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_m2m<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_l2l<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2m<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_m2m<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_l2l<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess) return e;

@@ -43,6 +43,8 @@ struct DevCommon {
     int chk_max_blocks;
     int chk_stage_blocks[3];  // largest stage (blocks) for 1, 2, 4 right-hand sides per pass
     int m2l_rb;               // right-hand sides per M2L pass (0: chosen from nrhs and N)
+    int p2p_tc_min_rhs;       // complex64 applies with at least this many columns use the
+                              // tensor-core near field (0: never)
     const int32_t* p2m_cells;  int64_t n_p2m;
     const int32_t* l2p_cells;  int64_t n_l2p;
     // near field: work units (leaf x bounded source ranges) and leaves

@@ -48,7 +48,7 @@ class Info(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("m2l_rhs_block", ctypes.c_int)]
+    _fields_ = [("m2l_rhs_block", ctypes.c_int), ("p2p_tc_min_rhs", ctypes.c_int)]
 
 
 class TuneOptions(ctypes.Structure):
@@ -59,7 +59,8 @@ class TuneOptions(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("fft_n", ctypes.c_int), ("m2l_rhs_block", ctypes.c_int),
-                ("ms", ctypes.c_double), ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int)]
+                ("p2p_tensor_cores", ctypes.c_int), ("ms", ctypes.c_double), ("candidates", ctypes.c_int),
+                ("from_cache", ctypes.c_int)]
 
 
 class DefmmError(RuntimeError):
@@ -208,15 +209,15 @@ class Plan:
         _check(lib().defmm_profile_read(self._h, buf, len(PHASES), ctypes.byref(n)))
         return {PHASES[i]: buf[i] for i in range(n.value)}
 
-    def set_tuning(self, m2l_rhs_block: int = 0):
-        """defmm_plan_set_tuning: launch choices of later applies (results unchanged)."""
-        t = Tuning(int(m2l_rhs_block))
+    def set_tuning(self, m2l_rhs_block: int = 0, p2p_tc_min_rhs: int = 0):
+        """defmm_plan_set_tuning: launch choices of later applies."""
+        t = Tuning(int(m2l_rhs_block), int(p2p_tc_min_rhs))
         _check(lib().defmm_plan_set_tuning(self._h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
         t = Tuning()
         _check(lib().defmm_plan_get_tuning(self._h, ctypes.byref(t)))
-        return {"m2l_rhs_block": t.m2l_rhs_block}
+        return {"m2l_rhs_block": t.m2l_rhs_block, "p2p_tc_min_rhs": t.p2p_tc_min_rhs}
 
     def table(self, name: str) -> np.ndarray:
         n = ctypes.c_int64()

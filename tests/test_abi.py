@@ -91,14 +91,17 @@ def test_argument_errors():
 def test_tuning_values():
     """Apply-time tuning takes 0, 1, 2, 4 right-hand sides per M2L pass and rejects others."""
     pl = _host_plan(W.points("sphere", 300, 2), kappa=2.0, order=4, leaf_size=16)
-    assert pl.tuning() == {"m2l_rhs_block": 0}
+    assert pl.tuning() == {"m2l_rhs_block": 0, "p2p_tc_min_rhs": 0}
     for v in (1, 2, 4, 0):
-        pl.set_tuning(m2l_rhs_block=v)
-        assert pl.tuning()["m2l_rhs_block"] == v
+        pl.set_tuning(m2l_rhs_block=v, p2p_tc_min_rhs=v)
+        assert pl.tuning() == {"m2l_rhs_block": v, "p2p_tc_min_rhs": v}
     for v in (3, -1, 8):
         with pytest.raises(defmm.DefmmError) as e:
             pl.set_tuning(m2l_rhs_block=v)
         assert e.value.status == 1
+    with pytest.raises(defmm.DefmmError) as e:
+        pl.set_tuning(p2p_tc_min_rhs=-1)
+    assert e.value.status == 1
     assert pl.tuning()["m2l_rhs_block"] == 0
 
 

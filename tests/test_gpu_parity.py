@@ -85,6 +85,49 @@ def test_against_oracle(case):
         assert _rel(p64[:, r], ref[:, r]) <= TOL64
 
 
+TC_CASES = [CASES[0], CASES[1], CASES[3], CASES[4], CASES[8]]
+
+
+@pytest.mark.parametrize("case", TC_CASES)
+def test_tensor_core_near_field_against_oracle(case):
+    """The tcgen05 near field (forced on for 2 columns) against the oracle: leaves
+    of up to 200 targets (several target tiles), two trees, orders 3-6."""
+    kind, n, other, kd, order, leaf, fft_n = case
+    X = W.points(kind, n, 21)
+    Y = None if other is None else 0.5 * W.points(other[0], other[1], 22)
+    P = X if Y is None else np.vstack([X, Y])
+    kappa = kd / float(np.max(P.max(0) - P.min(0)))
+    q = W.charges(len(X) if Y is None else len(Y), 23, nrhs=2)
+    plan = defmm.Plan(X, Y, kappa=kappa, order=order, leaf_size=leaf, fft_n=fft_n)
+    ref = oracle_fmm.fmm(X, q, kappa, order=order, leaf=leaf, Y=Y,
+                         fft_n=fft_n if fft_n else None)
+    cuda_cores = _gpu(plan, q, torch.complex64)
+    plan.set_tuning(p2p_tc_min_rhs=1)
+    tensor = _gpu(plan, q, torch.complex64)
+    assert plan.info()["device_error"] == 0
+    for r in range(q.shape[1]):
+        assert _rel(tensor[:, r], ref[:, r]) <= TOL64, _rel(tensor[:, r], ref[:, r])
+    assert _rel(tensor, cuda_cores) <= TOL64
+    assert np.array_equal(tensor, _gpu(plan, q, torch.complex64))    # deterministic
+
+
+def test_tensor_core_near_field_many_columns():
+    """40 columns: one full 32-column tensor-core pass and a ragged one of 8; every
+    column against the complex128 path, and a column alone equals it in the block."""
+    X = W.points("box", 6000, 33)
+    kappa = 24.0
+    q = W.charges(6000, 34, nrhs=40)
+    plan = defmm.Plan(X, kappa=kappa, order=4, leaf_size=48)
+    p128 = _gpu(plan, q, torch.complex128)
+    plan.set_tuning(p2p_tc_min_rhs=32)
+    p64 = _gpu(plan, q, torch.complex64)          # 40 >= 32: tensor-core near field
+    for r in range(40):
+        assert _rel(p64[:, r], p128[:, r]) <= TOL64
+    plan.set_tuning(p2p_tc_min_rhs=1)
+    one = _gpu(plan, q[:, 37], torch.complex64)
+    assert _rel(one, p64[:, 37]) <= 1e-6
+
+
 def test_multi_rhs_columns_and_determinism():
     X = W.points("sphere", 4000, 31)
     kappa = 20.0

@@ -52,4 +52,11 @@ def test_autotune_choice_cache_and_results(tmp_path):
     _, c3 = defmm.autotune(X, kappa=kappa, order=4, nrhs=1, leaf_range=(48, 64), reps=2,
                            tune_fft_n=False, cache_path=str(cache))
     assert c3["from_cache"] == 0 and c3["candidates"] == 2 and c3["m2l_rhs_block"] == 0
+    assert c3["p2p_tensor_cores"] == 0
     assert len(cache.read_text().splitlines()) == 2
+
+    # 8 columns: the tensor-core near field is a candidate too
+    p8, c4 = defmm.autotune(X, kappa=kappa, order=4, nrhs=8, leaf_range=(64, 64), reps=2,
+                            tune_fft_n=False, cache_path=str(cache))
+    assert c4["candidates"] == 2 * 3 and c4["p2p_tensor_cores"] in (0, 1)
+    assert p8.tuning()["p2p_tc_min_rhs"] == (1 if c4["p2p_tensor_cores"] else 0)
