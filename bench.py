@@ -199,6 +199,9 @@ def main():
     ap.add_argument("--impl", default="defmm", choices=["defmm", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--n", type=int, default=None, help="point count (same recipe; for profiling)")
+    ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides (same charge recipe; for profiling)")
+    ap.add_argument("--p2p-tensor-cores", action="store_true",
+                    help="tensor-core near field (defmm_tuning.p2p_tc_min_rhs = 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=10000, help="serve16: number of requests")
     ap.add_argument("--gap-ms", type=float, default=2.0, help="serve16: mean inter-arrival time")
@@ -228,11 +231,15 @@ def main():
         dist.barrier()
     W_ = W.WORKLOADS[args.workload]
     X, q, kappa, order, leaf, dtype = W.make(args.workload, n=args.n)
+    if args.nrhs:
+        q = W.charges(len(X), W_["seed"], args.nrhs)
     cdt = torch.complex64 if dtype == "c64" else torch.complex128
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     plan = defmm.Plan(X, kappa=kappa, order=order, leaf_size=leaf)
     plan_s = time.perf_counter() - t0
+    if args.p2p_tensor_cores:
+        plan.set_tuning(p2p_tc_min_rhs=1)
     info = plan.info()
     R = q.shape[1]
     qd = torch.from_numpy(np.ascontiguousarray(q)).to("cuda").to(cdt)
@@ -353,6 +360,7 @@ def main():
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": args.workload, "points": len(X), "kappa_d": W_["kappa_d"], "order": order,
                            "leaf": leaf, "nrhs": R, "distribution": W_["kind"], "l2": "flushed (512 MB write) before each step",
+                           "p2p": "tensor cores (tcgen05)" if args.p2p_tensor_cores else "cuda cores",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "m2l_roofline": m2l_roof, "p2p_roofline": p2p_roof,
                 "cpu_baseline": cpu,

@@ -1780,6 +1780,25 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
                 }
                 return rbeg[lo] + (f - roff[lo]);
             };
+            // the next tile's sources and charges are fetched into registers while
+            // the current tile is formed (coalesced over sources)
+            float4 pf_h = make_float4(0.f, 0.f, 0.f, 0.f), pf_l = pf_h;
+            float2 pf_q[4];
+            auto fetch = [&](int f) {
+                const int s = tid & 15;
+                int64_t j = -1;
+                if (f + s < total) j = source_of(f + s);
+                if (tid < kTcSrc) {
+                    pf_h = j >= 0 ? c.Yh[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    pf_l = j >= 0 ? c.Yl[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int r = (tid >> 4) + 8 * k;
+                    pf_q[k] = (j >= 0 && r < nr) ? qs[(int64_t)(rb0 + r) * c.ny + j] : make_float2(0.f, 0.f);
+                }
+            };
+            fetch(0);
             for (int f0 = 0; f0 < total; f0 += kTcSrc) {
                 const int ns = min(kTcSrc, total - f0);
                 const int st = (int)((uses[0] + uses[1]) & 1);
@@ -1787,28 +1806,16 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
                 // buffer) must be done before either is rewritten; their tile is taken
                 if (uses[st] > 0 && !mbar_wait(&bar[st], (uses[st] - 1) & 1)) fail_sh = 1;
                 if (unread[st]) take(st);
-                // stage the tile's sources and charges (coalesced over sources)
                 {
                     const int s = tid & 15;
-                    int64_t j = -1;
-                    if (s < ns) j = source_of(f0 + s);
-                    if (tid < kTcSrc) {
-                        if (j >= 0) { sh[s] = c.Yh[j]; sl[s] = c.Yl[j]; }
-                        else { sh[s] = make_float4(0.f, 0.f, 0.f, 0.f); sl[s] = sh[s]; }
-                    }
+                    if (tid < kTcSrc) { sh[s] = pf_h; sl[s] = pf_l; }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int r = (tid >> 4) + 8 * k;
-                        float2 q = make_float2(0.f, 0.f);
-                        if (j >= 0 && r < nr) {
-                            q = qs[(int64_t)(rb0 + r) * c.ny + j];
-                            q = make_float2(q.x * inv4pi, q.y * inv4pi);
-                        }
-                        qsm[s][r] = q;
-                    }
+                    for (int k = 0; k < 4; ++k)
+                        qsm[s][(tid >> 4) + 8 * k] = make_float2(pf_q[k].x * inv4pi, pf_q[k].y * inv4pi);
                 }
                 __syncthreads();
                 if (fail_sh) break;
+                if (f0 + kTcSrc < total) fetch(f0 + kTcSrc);   // in flight while this tile is formed
                 float* Ahi = tsm + st * kTcStageFloats;
                 float* Alo = Ahi + 2048;
                 float* Bhi = Ahi + 4096;
