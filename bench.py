@@ -329,14 +329,22 @@ def main():
     kernel_phases = {k: v for k, v in phase_avg.items() if k not in ("total", "join_wait")}
     dominant = max(kernel_phases, key=kernel_phases.get)
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    # P2P: 3 SFU operations (rsqrt, sin, cos) per interaction; 16 SFU results
-    # per clock per SM on 152 SMs
+    # P2P, one right-hand side: 3 SFU operations (rsqrt, sin, cos) per
+    # interaction; 16 SFU results per clock per SM on 152 SMs.  Several
+    # right-hand sides: 4 FP32 FMA per interaction and column (complex
+    # multiply-add) against 128 FMA per clock per SM.
     inter = info["p2p_interactions"] * R
     p2p_achieved = inter / (phase_avg["p2p"] * 1e-3) / 1e9
-    p2p_peak = 152 * 16 / 3 * sm_max * 1e6 / 1e9
+    if R == 1:
+        p2p_peak = 152 * 16 / 3 * sm_max * 1e6 / 1e9
+        p2p_src = "SFU: 152 SMs x 16/clk / 3 per interaction at %.0f MHz" % sm_max
+        p2p_unit = "Ginteractions/s"
+    else:
+        p2p_peak = 152 * 128 / 4 * sm_max * 1e6 / 1e9
+        p2p_src = "FP32 FMA: 152 SMs x 128/clk / 4 per interaction and column at %.0f MHz" % sm_max
+        p2p_unit = "Ginteraction-columns/s"
     p2p_roof = {"kernel": "p2p", "bound": "alu", "achieved": p2p_achieved, "peak": p2p_peak,
-                "unit": "Ginteractions/s", "frac": p2p_achieved / p2p_peak, "traffic": None,
-                "peak_source": "SFU: 152 SMs x 16/clk / 3 per interaction at %.0f MHz" % sm_max}
+                "unit": p2p_unit, "frac": p2p_achieved / p2p_peak, "traffic": None, "peak_source": p2p_src}
     per_pair = _recorded_traffic_per_pair()
     m2l_traffic = None if per_pair is None or R != 1 else per_pair * info["n_m2l_pairs"]
     m2l_roof = {"kernel": "m2l", "bound": "hbm", "achieved": m2l_gbs, "peak": peak_gbs, "unit": "GB/s",

@@ -212,6 +212,43 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
                                  int order, const defmm_options* opt, const defmm_tune_options* topt,
                                  void* stream, defmm_plan* out, defmm_tune_result* result);
 
+/* Iterative solve with the FMM operator: restarted GMRES (Saad and Schultz,
+ * 1986) for (sigma I + A) x = b, A the plan's operator (p = A q).  The paper
+ * applies the operator repeatedly inside iterative boundary-integral solvers
+ * (Sec. 1, Sec. 7); a shifted single-layer system is the simplest such use.
+ *  b, x   - device, n complex values each (n = nx = ny, caller's point order);
+ *           x holds the initial guess on entry and the solution on return.
+ *  dtype  - DEFMM_C64 or DEFMM_C128: the precision of the applies and of the
+ *           Krylov vectors (inner products accumulate in float64).
+ *  opt    - NULL for defaults: sigma = 1, tol = 1e-6 (relative residual
+ *           ||b - (sigma x + A x)|| / ||b||), restart 30, max_iter 200 applies.
+ *  stream - all device work goes to it; the call synchronises it once per
+ *           Arnoldi step and returns when done.
+ * Every product is one defmm_apply; Arnoldi uses classical Gram-Schmidt twice;
+ * the true residual is recomputed at each restart and reported in *result
+ * (may be NULL): iterations (applies in the Arnoldi steps), rel_residual,
+ * converged (rel_residual <= tol).  Not converging is not an error.
+ * Allocates (n x (restart + 1)) complex values of device scratch per call.
+ * Errors: DEFMM_ERR_ARG (NULL pointers, nx != ny, restart outside [1, 1000],
+ * max_iter < 0, tol < 0), DEFMM_ERR_UNSUPPORTED (dtype, host-only plan),
+ * DEFMM_ERR_OOM, DEFMM_ERR_CUDA, DEFMM_ERR_BUSY, DEFMM_ERR_TIMEOUT.          */
+typedef struct {
+    double shift_re, shift_im; /* sigma */
+    double tol;
+    int restart;
+    int max_iter;
+} defmm_gmres_options;
+
+typedef struct {
+    int iterations;
+    double rel_residual;
+    int converged;
+} defmm_gmres_result;
+
+void defmm_default_gmres_options(defmm_gmres_options* opt);
+defmm_status defmm_gmres(defmm_plan plan, const void* b, void* x, defmm_dtype dtype,
+                         const defmm_gmres_options* opt, void* stream, defmm_gmres_result* result);
+
 /* Frees the plan and its device memory (synchronises the device first).       */
 defmm_status defmm_destroy(defmm_plan plan);
 

@@ -27,6 +27,7 @@ SOURCES = [
     ("noalloc.cu", "nvcc"),
     ("serve.cu", "nvcc"),
     ("tune.cu", "nvcc"),
+    ("gmres.cu", "nvcc"),
 ]
 
 

@@ -24,7 +24,7 @@ EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_
             "defmm_destroy", "defmm_plan_info", "defmm_plan_table", "defmm_profile_enable",
             "defmm_profile_read", "defmm_apply_noalloc", "defmm_plan_set_tuning",
             "defmm_plan_get_tuning", "defmm_default_tune_options", "defmm_plan_autotune",
-            "defmm_last_error"]
+            "defmm_default_gmres_options", "defmm_gmres", "defmm_last_error"]
 PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 
 
@@ -61,6 +61,15 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("fft_n", ctypes.c_int), ("m2l_rhs_block", ctypes.c_int),
                 ("p2p_tensor_cores", ctypes.c_int), ("ms", ctypes.c_double), ("candidates", ctypes.c_int),
                 ("from_cache", ctypes.c_int)]
+
+
+class GmresOptions(ctypes.Structure):
+    _fields_ = [("shift_re", ctypes.c_double), ("shift_im", ctypes.c_double), ("tol", ctypes.c_double),
+                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int)]
+
+
+class GmresResult(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double), ("converged", ctypes.c_int)]
 
 
 class DefmmError(RuntimeError):
@@ -112,6 +121,11 @@ def lib():
                                           ctypes.POINTER(TuneOptions), vp, ctypes.POINTER(vp),
                                           ctypes.POINTER(TuneResult)]
         L.defmm_plan_autotune.restype = ctypes.c_int
+        L.defmm_default_gmres_options.argtypes = [ctypes.POINTER(GmresOptions)]
+        L.defmm_default_gmres_options.restype = None
+        L.defmm_gmres.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(GmresOptions), vp,
+                                  ctypes.POINTER(GmresResult)]
+        L.defmm_gmres.restype = ctypes.c_int
         L.defmm_last_error.argtypes = []
         L.defmm_last_error.restype = ctypes.c_char_p
         _LIB = L
@@ -218,6 +232,26 @@ class Plan:
         t = Tuning()
         _check(lib().defmm_plan_get_tuning(self._h, ctypes.byref(t)))
         return {"m2l_rhs_block": t.m2l_rhs_block, "p2p_tc_min_rhs": t.p2p_tc_min_rhs}
+
+    def gmres(self, b, x0=None, shift=1.0, tol=1e-6, restart=30, max_iter=200, stream=None):
+        """defmm_gmres: solves (shift I + A) x = b on the GPU.  b: complex64/complex128
+        CUDA tensor (n,).  Returns (x, {iterations, rel_residual, converged})."""
+        import torch
+        if b.dim() != 1 or b.shape[0] != self.nx or self.nx != self.ny:
+            raise ValueError("b must have shape (n,) with n = nx = ny")
+        if b.dtype not in (torch.complex64, torch.complex128):
+            raise TypeError("b must be complex64 or complex128")
+        bc = b.contiguous()
+        x = torch.zeros_like(bc) if x0 is None else x0.to(bc.dtype).contiguous().clone()
+        o = GmresOptions()
+        lib().defmm_default_gmres_options(ctypes.byref(o))
+        o.shift_re, o.shift_im = float(complex(shift).real), float(complex(shift).imag)
+        o.tol, o.restart, o.max_iter = float(tol), int(restart), int(max_iter)
+        r = GmresResult()
+        _check(lib().defmm_gmres(self._h, ctypes.c_void_p(bc.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                 C64 if bc.dtype == torch.complex64 else C128, ctypes.byref(o),
+                                 _stream_handle(stream), ctypes.byref(r)))
+        return x, {name: getattr(r, name) for name, _ in GmresResult._fields_}
 
     def table(self, name: str) -> np.ndarray:
         n = ctypes.c_int64()

@@ -167,3 +167,26 @@ def test_autotune_argument_errors():
     with pytest.raises(defmm.DefmmError) as e:
         defmm.autotune(X, kappa=1.0, order=4, flags=defmm.PLAN_HOST_ONLY)
     assert e.value.status == 5
+
+
+def test_gmres_argument_errors():
+    """defmm_gmres validates its arguments before touching a GPU."""
+    import ctypes
+    L = defmm.lib()
+    pl = _host_plan(W.points("sphere", 200, 1), kappa=1.0, order=4, leaf_size=8)
+    o = defmm.GmresOptions()
+    L.defmm_default_gmres_options(ctypes.byref(o))
+    assert (o.shift_re, o.shift_im, o.tol, o.restart, o.max_iter) == (1.0, 0.0, 1e-6, 30, 200)
+    dummy = ctypes.c_void_p(16)
+    assert L.defmm_gmres(None, dummy, dummy, defmm.C64, ctypes.byref(o), None, None) == 1
+    assert L.defmm_gmres(pl.handle, None, dummy, defmm.C64, ctypes.byref(o), None, None) == 1
+    assert L.defmm_gmres(pl.handle, dummy, dummy, 7, ctypes.byref(o), None, None) == 5
+    for field, bad in (("restart", 0), ("max_iter", -1), ("tol", -1.0)):
+        b = defmm.GmresOptions()
+        L.defmm_default_gmres_options(ctypes.byref(b))
+        setattr(b, field, bad)
+        assert L.defmm_gmres(pl.handle, dummy, dummy, defmm.C64, ctypes.byref(b), None, None) == 1
+    assert L.defmm_gmres(pl.handle, dummy, dummy, defmm.C64, ctypes.byref(o), None, None) == 5   # host-only
+    two = _host_plan(W.points("sphere", 200, 1), W.points("sphere", 150, 2), kappa=1.0, order=4, leaf_size=8)
+    # a non-square operator is refused (checked after the host-only test)
+    assert L.defmm_gmres(two.handle, dummy, dummy, defmm.C64, ctypes.byref(o), None, None) == 5
