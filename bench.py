@@ -52,20 +52,30 @@ SAMPLE_N = 16000          # cpu_baseline: ~10-20 s of single-core oracle work
 ORACLE_S_PER_POINT = 6e-4  # measured oracle cost on this recipe, used to size samples
 
 
+M2L_BEGIN = "// The same group schedule with rows of samples"
+M2L_END = "// Ring depth S and the dynamic shared memory of the per-sample M2L kernel"
+
+
+def m2l_rows_source_sha():
+    """sha256 (first 16 hex) of the row M2L kernel's source text in kernels.cu."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2202_04894_gb300", "csrc", "kernels.cu")).read()
+    a, b = src.index(M2L_BEGIN), src.index(M2L_END)
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+
+
 def _recorded_traffic_per_pair():
     """DRAM bytes per M2L pair from the committed ncu summary, or None when the
-    kernels have changed since those counters were taken."""
-    import hashlib
+    row M2L kernel has changed since those counters were taken."""
     import re
     path = os.path.join(ROOT, "profiles", "m2l_rows_sphere300k_kD128_p4.md")
-    src = os.path.join(ROOT, "paper_2202_04894_gb300", "csrc", "kernels.cu")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
+        sha = m2l_rows_source_sha()
+    except (OSError, ValueError):
         return None
     m = re.search(r"traffic_bytes_per_pair:\s*([0-9.]+)", text)
-    h = re.search(r"kernels.cu sha256 \(first 16 hex\):\s*([0-9a-f]+)", text)
+    h = re.search(r"k_m2l_rows source sha256 \(first 16 hex\):\s*([0-9a-f]+)", text)
     if not m or not h or h.group(1) != sha:
         return None
     return float(m.group(1))

@@ -575,7 +575,7 @@ __host__ size_t p2m_smem(int p, int RB, int epass, size_t creal) {
 // M2M, L2L and M2F work on one small expansion at a time: one warp per item,
 // synchronised with __syncwarp only; blocks hold `wpb` independent warps.
 // ------------------------------------------------------------------ M2M
-// One warp per father expansion (entry: father id, 8 son ids or -1):
+// One warp per (father expansion, right-hand side) (entry: father id, 8 son ids or -1):
 //   M_f^v[a] = P_v(a) sum_sons sum_b T_o[a, b] conj(Q_v,o(b)) M_son[b],
 // T_o the tensor product of the 1-D son->father matrices, applied as three
 // 1-D passes (Sec. 5.2.1).
@@ -589,7 +589,9 @@ __global__ void __launch_bounds__(256) k_m2m(DevCommon c, DevTyped<T> t, const i
     __shared__ T m1s[2 * 8 * 8];
     for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) m1s[i] = t.m1[i];
     __syncthreads();
-    const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;   // (item, right-hand side)
+    const int64_t item = wid / R;
+    const int rr = (int)(wid % R);
     if (item >= n) return;
     C* A = reinterpret_cast<C*>(smem_raw) + (size_t)warp * (2 * P3 + 72);
     C* B = A + P3;
@@ -601,7 +603,8 @@ __global__ void __launch_bounds__(256) k_m2m(DevCommon c, DevTyped<T> t, const i
     for (int i = lane; i < 3 * p; i += 32) Ps[i] = slot >= 0 ? t.slot_P[(int64_t)slot * 3 * p + i] : mk((T)1, (T)0);
     for (int i = lane; i < 6 * p; i += 32) Qs[i] = slot >= 0 ? t.slot_Q[(int64_t)slot * 6 * p + i] : mk((T)1, (T)0);
     __syncwarp();
-    for (int r = 0; r < R; ++r) {
+    {   // this warp's right-hand side
+        const int r = rr;
         C acc[16];
 #pragma unroll
         for (int v = 0; v < 16; ++v) acc[v] = czero<C>();
@@ -657,7 +660,7 @@ __global__ void __launch_bounds__(256) k_m2m(DevCommon c, DevTyped<T> t, const i
 }
 
 // ------------------------------------------------------------------ M2F
-// One warp per Fourier multipole: zero-pad and forward DFT (F chi, Sec. 4.1.1),
+// One warp per (Fourier multipole, right-hand side): zero-pad and forward DFT (F chi, Sec. 4.1.1),
 // pruned to the p non-zero inputs per line.
 template <typename T, int PC = 0, int NC = 0>
 __global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ M,
@@ -669,13 +672,16 @@ __global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const t
     __shared__ C tws[16];
     if (threadIdx.x < N) tws[threadIdx.x] = mk(t.tw[threadIdx.x].x, -t.tw[threadIdx.x].y);   // e^{-2 pi i m / N}
     __syncthreads();
-    const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;   // (item, right-hand side)
+    const int64_t item = wid / R;
+    const int rr = (int)(wid % R);
     if (item >= c.n_m2f) return;
     C* A = reinterpret_cast<C*>(smem_raw) + (size_t)warp * (P3 + p * p * N + p * N * N);
     C* B = A + P3;              // [bz][by][xi_x]   p*p*N
     C* D = B + p * p * N;       // [bz][xi_y][xi_x] p*N*N
     const int e = c.m2f_list[item];
-    for (int r = 0; r < R; ++r) {
+    {   // this warp's right-hand side
+        const int r = rr;
         for (int a = lane; a < P3; a += 32) A[a] = M[((int64_t)e * R + r) * P3 + a];
         __syncwarp();
         for (int i = lane; i < p * p * N; i += 32) {
@@ -1136,7 +1142,7 @@ template <typename T> __host__ bool m2l_rows_shape(const DevCommon& c, int RB, i
     return *smem <= kSmemLimit;
 }
 // ------------------------------------------------------------------ L2L
-// One warp per son expansion (entry: son id, octant, first, count into the
+// One warp per (son expansion, right-hand side) (entry: son id, octant, first, count into the
 // list of father expansions feeding it), the transpose of M2M:
 //   L_son[b] += sum_fathers Q_v,o(b) sum_a T_o[a, b] conj(P_v(a)) L_v[a].
 template <typename T, int PC = 0>
@@ -1149,7 +1155,9 @@ __global__ void __launch_bounds__(256) k_l2l(DevCommon c, DevTyped<T> t, const i
     __shared__ T m1s[2 * 8 * 8];
     for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) m1s[i] = t.m1[i];
     __syncthreads();
-    const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;   // (item, right-hand side)
+    const int64_t item = wid / R;
+    const int rr = (int)(wid % R);
     if (item >= n) return;
     C* A = reinterpret_cast<C*>(smem_raw) + (size_t)warp * (2 * P3 + 72);
     C* B = A + P3;
@@ -1161,7 +1169,8 @@ __global__ void __launch_bounds__(256) k_l2l(DevCommon c, DevTyped<T> t, const i
     const T* mx = m1s + ox * p * p;
     const T* my = m1s + oy * p * p;
     const T* mz = m1s + oz * p * p;
-    for (int r = 0; r < R; ++r) {
+    {   // this warp's right-hand side
+        const int r = rr;
         C acc[16];
 #pragma unroll
         for (int v = 0; v < 16; ++v) acc[v] = czero<C>();
@@ -2043,10 +2052,13 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
             p2p_done = true;
         }
     }
-    for (int rb0 = 0; rb0 < R && !p2p_done; rb0 += (R == 1 ? 1 : 4)) {
+    // complex64: 8 columns per pass from 8 columns on (each kernel value serves 8 products)
+    const int p2p_rb = R == 1 ? 1 : ((std::is_same<T, float>::value && R >= 8) ? 8 : 4);
+    for (int rb0 = 0; rb0 < R && !p2p_done; rb0 += p2p_rb) {
         if (c.n_p2p_units == 0) break;
         if constexpr (std::is_same<T, float>::value) {
             if (R == 1) k_p2p_f32<1><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+            else if (p2p_rb == 8) k_p2p_f32<8><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
             else k_p2p_f32<4><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
         } else {
             if (R == 1) k_p2p<T, 1><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
@@ -2084,7 +2096,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     const int wpb_mm = warps_per_block(per_warp_mm);
     for (int l = n_m2m_levels - 1; l >= 0; --l) {
         if (m2m[l].n == 0) continue;
-        const unsigned blocks = (unsigned)((m2m[l].n + wpb_mm - 1) / wpb_mm);
+        const unsigned blocks = (unsigned)((m2m[l].n * R + wpb_mm - 1) / wpb_mm);   // a warp per (item, column)
         if (c.p == 4) k_m2m<T, 4><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
         else if (c.p == 5) k_m2m<T, 5><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
         else if (c.p == 6) k_m2m<T, 6><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, m2m[l].data, m2m[l].n, w.M, R);
@@ -2095,7 +2107,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     if (c.n_m2f > 0) {
         const size_t per_warp = ((size_t)c.P3 + (size_t)c.p * c.p * c.N + (size_t)c.p * c.N * c.N) * sizeof(C);
         const int wpb = warps_per_block(per_warp);
-        const unsigned blocks = (unsigned)((c.n_m2f + wpb - 1) / wpb);
+        const unsigned blocks = (unsigned)((c.n_m2f * R + wpb - 1) / wpb);   // a warp per (item, column)
         if (c.p == 4 && c.N == 7) k_m2f<T, 4, 7><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
         else if (c.p == 5 && c.N == 9) k_m2f<T, 5, 9><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
         else if (c.p == 6 && c.N == 11) k_m2f<T, 6, 11><<<blocks, 32 * wpb, wpb * per_warp, stream>>>(c, t, w.M, w.Mhat, R);
@@ -2115,7 +2127,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     // downward pass
     for (int l = 1; l < n_l2l_levels; ++l) {
         if (l2l[l].n == 0) continue;
-        const unsigned blocks = (unsigned)((l2l[l].n + wpb_mm - 1) / wpb_mm);
+        const unsigned blocks = (unsigned)((l2l[l].n * R + wpb_mm - 1) / wpb_mm);   // a warp per (item, column)
         if (c.p == 4) k_l2l<T, 4><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);
         else if (c.p == 5) k_l2l<T, 5><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);
         else if (c.p == 6) k_l2l<T, 6><<<blocks, 32 * wpb_mm, wpb_mm * per_warp_mm, stream>>>(c, t, l2l[l].data, l2l[l].n, l2l_par[l], w.L, R);

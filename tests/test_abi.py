@@ -190,3 +190,12 @@ def test_gmres_argument_errors():
     two = _host_plan(W.points("sphere", 200, 1), W.points("sphere", 150, 2), kappa=1.0, order=4, leaf_size=8)
     # a non-square operator is refused (checked after the host-only test)
     assert L.defmm_gmres(two.handle, dummy, dummy, defmm.C64, ctypes.byref(o), None, None) == 5
+
+
+def test_bench_finds_the_row_kernel_source():
+    """bench.py keys the recorded M2L DRAM traffic to the row kernel's source text."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.m2l_rows_source_sha()
+    assert len(h) == 16 and int(h, 16) >= 0
