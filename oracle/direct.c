@@ -1,6 +1,8 @@
 /* O(N^2) direct sum of Eq. (1.1), Sec. 1, in plain C and double precision.
  *
- *   p(x) = sum_y exp(i kappa |x-y|) / (4 pi |x-y|) q(y),  skipping |x-y| <= eps.
+ *   p(x) = sum_y exp((i kappa - lambda) |x-y|) / (4 pi |x-y|) q(y),  skipping |x-y| <= eps
+ *
+ * (lambda = damping >= 0; 0 gives the paper's Helmholtz kernel).
  *
  * Test infrastructure only: part of the CPU oracle, never linked into the
  * CUDA library.  X: nx*3 row-major, Y: ny*3 row-major, q: ny*nrhs complex
@@ -11,7 +13,7 @@
 #include <stdint.h>
 
 void oracle_direct_sum(const double* X, int64_t nx, const double* Y, int64_t ny,
-                       const double* q, int64_t nrhs, double kappa, double eps,
+                       const double* q, int64_t nrhs, double kappa, double damping, double eps,
                        const int64_t* targets, double* out, int64_t nt) {
     const double inv4pi = 1.0 / (4.0 * M_PI);
     (void)nx;
@@ -26,8 +28,9 @@ void oracle_direct_sum(const double* X, int64_t nx, const double* Y, int64_t ny,
             double dx = x[0] - Y[3 * j], dy = x[1] - Y[3 * j + 1], dz = x[2] - Y[3 * j + 2];
             double rr = sqrt(dx * dx + dy * dy + dz * dz);
             if (!(rr > eps)) continue;
-            double gr = cos(kappa * rr) * inv4pi / rr;
-            double gi = sin(kappa * rr) * inv4pi / rr;
+            double mag = exp(-damping * rr) * inv4pi / rr;
+            double gr = cos(kappa * rr) * mag;
+            double gi = sin(kappa * rr) * mag;
             for (int64_t r = 0; r < nrhs; ++r) {
                 double qr = q[2 * (r * ny + j)], qi = q[2 * (r * ny + j) + 1];
                 out[2 * (r * nt + it)] += gr * qr - gi * qi;

@@ -71,3 +71,31 @@ def test_c_direct_matches_numpy():
     got = direct.direct_sum_c(np.array([[0, 0, 1.5]]), Y, w, 2.0, 1e-12)[0]
     want = np.sin(1.0) / 1.0 * np.exp(3j) / (4 * np.pi * 1.5)
     assert abs(got - want) < 1e-12 * abs(want)
+
+
+@pytest.mark.parametrize("kappa,damping", [(0.0, 2.0), (3.0, 1.5), (0.0, 0.0)])
+def test_shell_mean_value_damped(kappa, damping):
+    """The damped kernel is the Helmholtz kernel of the complex wavenumber
+    k = kappa + i*damping, so the spherical mean value over a sphere of radius a
+    seen from R > a is sin(k a)/(k a) * exp(i k R)/(4 pi R); for kappa = 0 that
+    is sinh(damping a)/(damping a) * exp(-damping R)/(4 pi R) (Yukawa)."""
+    a, R = 0.5, 1.7
+    Y, w = _sphere_quadrature(48, 96, a)
+    x = np.array([[0.3 * R, -0.4 * R, np.sqrt(1 - 0.25) * R]])
+    got = direct.direct_sum(x, Y, w, kappa, 1e-12, damping=damping)[0]
+    k = kappa + 1j * damping
+    j0 = 1.0 if k == 0 else np.sin(k * a) / (k * a)
+    want = j0 * np.exp(1j * k * R) / (4 * np.pi * R)
+    assert abs(got - want) <= 1e-12 * abs(want)
+    if kappa == 0 and damping > 0:
+        yukawa = np.sinh(damping * a) / (damping * a) * np.exp(-damping * R) / (4 * np.pi * R)
+        assert abs(got - yukawa) <= 1e-12 * yukawa
+
+
+def test_c_direct_matches_numpy_damped():
+    X = W.points("box", 300, 9)
+    q = W.charges(300, 9, nrhs=2)
+    tg = np.array([3, 77, 299])
+    a = direct.direct_sum(X, X, q, 4.0, 1e-10, targets=tg, damping=2.5)
+    b = direct.direct_sum_c(X, X, q, 4.0, 1e-10, targets=tg, damping=2.5)
+    assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a))

@@ -71,3 +71,20 @@ def test_two_trees_and_low_frequency():
         want = direct.direct_sum(X, Y, q, kappa, plan.eps_self)
         assert _rel(got, want) < 2e-4
         assert plan.tt is not plan.ts
+
+
+@pytest.mark.parametrize("kd,damping_d", [(0.0, 8.0), (16.0, 4.0)])
+def test_damped_kernel_against_direct_sum(kd, damping_d):
+    """Yukawa (kappa = 0) and damped Helmholtz: the FMM with the damped kernel
+    converges to the direct sum with it (order 5 below 1e-4, order 3 above)."""
+    X = W.points("sphere", 1500, 12)
+    D = float(np.max(X.max(0) - X.min(0)))
+    kappa, lam = kd / D, damping_d / D
+    q = W.charges(1500, 13)[:, 0]
+    want = direct.direct_sum(X, X, q, kappa, direct.eps_self(X), damping=lam)
+    e3 = _rel(fmm.fmm(X, q, kappa, order=3, leaf=20, damping=lam), want)
+    e5 = _rel(fmm.fmm(X, q, kappa, order=5, leaf=20, damping=lam), want)
+    assert e5 < 1e-4 and e5 < e3 / 5
+    # the damping changes the result (the kernel is really used everywhere)
+    undamped = direct.direct_sum(X, X, q, kappa, direct.eps_self(X))
+    assert _rel(undamped, want) > 0.1
