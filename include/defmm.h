@@ -57,7 +57,15 @@ typedef enum { DEFMM_C64 = 0, DEFMM_C128 = 1 } defmm_dtype;
  *               defmm_plan_table, and defmm_apply returns DEFMM_ERR_UNSUPPORTED.
  *  hbm_budget - refuse plans whose device footprint exceeds this many bytes
  *               (0: no limit).  Checked at plan creation (plan tables and
- *               one-RHS workspace) and at each apply (workspace for nrhs).   */
+ *               one-RHS workspace) and at each apply (workspace for nrhs).
+ *  damping    - lambda >= 0: the kernel becomes exp((i kappa - lambda) r) /
+ *               (4 pi r), the Helmholtz kernel of the complex wavenumber
+ *               kappa + i lambda (default 0, the paper's kernel).  kappa = 0
+ *               gives the Yukawa (modified Helmholtz) kernel, kappa = lambda =
+ *               0 the Laplace kernel; the method holds for such asymptotically
+ *               smooth kernels (Sec. 1).  kappa alone sets the directional
+ *               (high-frequency) structure; lambda enters the near field and
+ *               the transfer spectra only.                                    */
 typedef struct {
     double eta;
     double hf_kw;
@@ -65,6 +73,7 @@ typedef struct {
     int flags;
     double self_eps;
     size_t hbm_budget;
+    double damping;
 } defmm_options;
 
 #define DEFMM_PLAN_HOST_ONLY 1
@@ -87,7 +96,8 @@ void defmm_default_options(defmm_options* opt);
  *  stream    - cudaStream_t for the plan's device work (NULL: legacy stream);
  *              the call returns after that work is complete.
  *  out       - receives the plan.  X and Y are only read during the call.
- * Errors: DEFMM_ERR_ARG, DEFMM_ERR_OOM, DEFMM_ERR_CUDA.                       */
+ * Errors: DEFMM_ERR_ARG (also for damping < 0 or not finite), DEFMM_ERR_OOM,
+ * DEFMM_ERR_CUDA.                                                             */
 defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int64_t ny,
                                double kappa, int order, int leaf_size,
                                const defmm_options* opt, void* stream, defmm_plan* out);

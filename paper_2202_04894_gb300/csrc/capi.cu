@@ -1,6 +1,8 @@
 // C ABI of the library (include/defmm.h): plan upload, workspace and calls.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -221,7 +223,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
 
     DevCommon& c = pl->common;
     c.p = hp.p; c.N = hp.N; c.NF = hp.NF; c.NFpad = hp.NFpad; c.P3 = hp.P3;
-    c.nx = hp.nx; c.ny = hp.ny; c.kappa = hp.kappa; c.eps_self = hp.eps_self;
+    c.nx = hp.nx; c.ny = hp.ny; c.kappa = hp.kappa; c.eps_self = hp.eps_self; c.damping = hp.damping;
     c.Xs = (const double*)P(o_Xs); c.Ys = (const double*)P(o_Ys);
     c.perm_t = (const int64_t*)P(o_pt); c.perm_s = (const int64_t*)P(o_ps);
     c.Xh = (const float4*)P(o_Xh); c.Xl = (const float4*)P(o_Xl);
@@ -272,7 +274,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     pl->tf.spec = (const float2*)P(o_specf);
 
     cudaError_t e = launch_spectra((const int32_t*)P(o_sl), (const int32_t*)P(o_sk), (int)nspec,
-                                   (const double*)P(o_lside), hp.p, hp.N, hp.NFpad, hp.kappa,
+                                   (const double*)P(o_lside), hp.p, hp.N, hp.NFpad, hp.kappa, hp.damping,
                                    (double2*)P(o_specd), (float2*)P(o_specf), stream);
     if (e != cudaSuccess) return cuda_fail(e, "spectra kernel");
     CK(cudaStreamSynchronize(stream), "plan creation");
@@ -315,6 +317,7 @@ void defmm_default_options(defmm_options* opt) {
     opt->flags = 0;
     opt->self_eps = 1e-10;
     opt->hbm_budget = 0;
+    opt->damping = 0.0;
 }
 
 const char* defmm_last_error(void) { return g_err.c_str(); }
@@ -356,6 +359,7 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
         });
         if (g_config_err != cudaSuccess) return cuda_fail(g_config_err, "kernel configuration");
     }
+    if (!(o.damping >= 0.0) || !std::isfinite(o.damping)) return fail(DEFMM_ERR_ARG, "damping must be finite and >= 0");
     defmm_plan_s* pl = new (std::nothrow) defmm_plan_s;
     if (!pl) return fail(DEFMM_ERR_OOM, "host allocation");
     pl->hbm_budget = o.hbm_budget;
@@ -373,6 +377,7 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
         delete pl;
         return fail(DEFMM_ERR_ARG, ex.what());
     }
+    pl->hp.damping = o.damping;
     pl->host_only = host_only;
     s = host_only ? DEFMM_OK : upload(pl, hx, hy, (cudaStream_t)stream);
     if (s != DEFMM_OK) {

@@ -93,6 +93,7 @@ template <int n> __device__ __forceinline__ void ld_vec(const double2* src, doub
 
 constexpr double kInv4Pi = 0.0795774715459476678844418816863;  // 1/(4 pi)
 constexpr double kInv2Pi = 0.159154943091895335768883763373;   // 1/(2 pi)
+constexpr double kLog2E = 1.44269504088896340735992468100;     // log2(e)
 
 // ------------------------------------------------------------------ gather / scatter
 template <typename C>
@@ -125,6 +126,11 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float ex2_hw(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ void sincos_hw(float a, float* s, float* c) {
     asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(a));
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(a));
@@ -147,12 +153,14 @@ __device__ __forceinline__ float2 helmholtz(float dx, float dy, float dz, float 
     const float g = rinv * (float)kInv4Pi;
     return make_float2(c * g, s * g);
 }
-__device__ __forceinline__ double2 helmholtz(double dx, double dy, double dz, double kappa, double eps2) {
+__device__ __forceinline__ double2 helmholtz(double dx, double dy, double dz, double kappa, double eps2,
+                                             double damping) {
     double r2 = dx * dx + dy * dy + dz * dz;
     double r = sqrt(r2);
     double s, c;
     sincos(kappa * r, &s, &c);
     double g = kInv4Pi / r;
+    if (damping > 0.0) g *= exp(-damping * r);
     double2 out = make_double2(c * g, s * g);
     if (!(r2 > eps2)) out = make_double2(0.0, 0.0);
     return out;
@@ -246,8 +254,8 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
                         dxa += xa.lo - ex; dya += ya.lo - ey; dza += za.lo - ez;
                         dxb += xb.lo - ex; dyb += yb.lo - ey; dzb += zb.lo - ez;
                     }
-                    const C ga = helmholtz(dxa, dya, dza, kpar, eps2);
-                    const C gb = helmholtz(dxb, dyb, dzb, kpar, eps2);
+                    const C ga = helmholtz(dxa, dya, dza, kpar, eps2, (T)c.damping);
+                    const C gb = helmholtz(dxb, dyb, dzb, kpar, eps2, (T)c.damping);
 #pragma unroll
                     for (int r = 0; r < RB; ++r) {
                         const C qv = sq[r][k];
@@ -290,7 +298,7 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
 // partial sums are reduced over the splits in a fixed order.
 constexpr int kP2PRanges = kP2PUnitRanges;   // ranges of a work unit, held in shared memory
 
-template <int RB>
+template <int RB, bool DAMP = false>
 __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __restrict__ qs,
                                                  float2* __restrict__ part, int R, int rb0) {
     __shared__ float4 sa[128];   // hi x, y, z and Re q / (4 pi)   (RB == 1)
@@ -306,6 +314,7 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
     const float kap2pi = (float)(c.kappa * kInv2Pi);
     const float eps2 = (float)(c.eps_self * c.eps_self);
     const float inv4pi = (float)kInv4Pi;
+    const float lam2 = (float)(c.damping * kLog2E);     // damping in powers of 2 per unit length
     const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];
     for (int t0 = tb; t0 < te; t0 += 256) {
         // two targets per thread: target pairs (2i, 2i+1) x source splits
@@ -386,6 +395,7 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
                             rinv = r2 > eps2 ? rinv : 0.f;
                             float sn, cs;
                             turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                            if (DAMP) rinv *= ex2_hw(-lam2 * (r2 * rinv));
                             ga = make_float2(cs * rinv, sn * rinv);
                         }
                         {
@@ -397,6 +407,7 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
                             rinv = r2 > eps2 ? rinv : 0.f;
                             float sn, cs;
                             turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                            if (DAMP) rinv *= ex2_hw(-lam2 * (r2 * rinv));
                             gb = make_float2(cs * rinv, sn * rinv);
                         }
                         if (RB == 1) {
@@ -1603,7 +1614,8 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_l2p_warp(DevCommon c, DevTy
 // with e^{-2 pi i xi.x / N} (unnormalised) along x, y and z.
 __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spec_level, const int32_t* __restrict__ kbar,
                                                  const double* __restrict__ level_side, int p, int N, int NFpad,
-                                                 double kappa, double2* __restrict__ out_d, float2* __restrict__ out_f) {
+                                                 double kappa, double damping, double2* __restrict__ out_d,
+                                                 float2* __restrict__ out_f) {
     extern __shared__ unsigned char smem_raw[];
     const int NF = N * N * N;
     double2* A = reinterpret_cast<double2*>(smem_raw);
@@ -1627,7 +1639,7 @@ __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spe
         const double r = sqrt(vx * vx + vy * vy + vz * vz);
         double s, c;
         sincos(kappa * r, &s, &c);
-        const double g = kInv4Pi / r;
+        const double g = kInv4Pi / r * (damping > 0.0 ? exp(-damping * r) : 1.0);
         const int ix = (dx + N) % N, iy = (dy + N) % N, iz = (dz + N) % N;
         A[(iz * N + iy) * N + ix] = make_double2(c * g, s * g);
     }
@@ -1659,12 +1671,12 @@ __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spe
 
 cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
                            const double* level_side, int p, int N, int NFpad, double kappa,
-                           double2* out_d, float2* out_f, cudaStream_t stream) {
+                           double damping, double2* out_d, float2* out_f, cudaStream_t stream) {
     if (nspec == 0) return cudaSuccess;
     size_t smem = 2 * (size_t)N * N * N * sizeof(double2);
     cudaError_t err = cudaFuncSetAttribute(k_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_spectra<<<nspec, 256, smem, stream>>>(spec_level, spec_kbar, level_side, p, N, NFpad, kappa, out_d, out_f);
+    k_spectra<<<nspec, 256, smem, stream>>>(spec_level, spec_kbar, level_side, p, N, NFpad, kappa, damping, out_d, out_f);
     return cudaGetLastError();
 }
 
@@ -1730,6 +1742,7 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
     const float kap2pi = (float)(c.kappa * kInv2Pi);
     const float eps2 = (float)(c.eps_self * c.eps_self);
     const float inv4pi = (float)kInv4Pi;
+    const float lam2 = (float)(c.damping * kLog2E);
     const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -1851,6 +1864,7 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
                         rinv = r2 > eps2 ? rinv : 0.f;
                         float sn, cs;
                         turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                        if (lam2 != 0.f) rinv *= ex2_hw(-lam2 * (r2 * rinv));
                         gr = cs * rinv;
                         gi = sn * rinv;
                     }
@@ -2057,9 +2071,16 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     for (int rb0 = 0; rb0 < R && !p2p_done; rb0 += p2p_rb) {
         if (c.n_p2p_units == 0) break;
         if constexpr (std::is_same<T, float>::value) {
-            if (R == 1) k_p2p_f32<1><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-            else if (p2p_rb == 8) k_p2p_f32<8><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-            else k_p2p_f32<4><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+            const unsigned nu = (unsigned)c.n_p2p_units;
+            if (c.damping > 0.0) {
+                if (R == 1) k_p2p_f32<1, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                else if (p2p_rb == 8) k_p2p_f32<8, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                else k_p2p_f32<4, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+            } else {
+                if (R == 1) k_p2p_f32<1><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                else if (p2p_rb == 8) k_p2p_f32<8><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                else k_p2p_f32<4><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+            }
         } else {
             if (R == 1) k_p2p<T, 1><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
             else k_p2p<T, 4><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);

@@ -17,6 +17,7 @@ struct DevCommon {
     int p, N, NF, NFpad, P3;
     int64_t nx, ny;
     double kappa, eps_self;
+    double damping;          // lambda >= 0: G = exp((i kappa - lambda) r) / (4 pi r)
     const double* Xs;        // nx*3 targets, Morton order
     const double* Ys;        // ny*3 sources, Morton order
     const float4* Xh;        // targets minus the cube centre, float hi part (w unused)
@@ -97,6 +98,6 @@ constexpr int kNumPhases = 9;  // gather p2p p2m m2m m2f m2l l2l l2p scatter
 // Forms the canonical transfer spectra in float64 (Sec. 2.3 Eq. FourierDiagonal).
 cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
                            const double* level_side, int p, int N, int NFpad, double kappa,
-                           double2* out_d, float2* out_f, cudaStream_t stream);
+                           double damping, double2* out_d, float2* out_f, cudaStream_t stream);
 
 }  // namespace defmm

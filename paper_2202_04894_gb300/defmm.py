@@ -31,7 +31,7 @@ PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 class Options(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("hf_kw", ctypes.c_double), ("fft_n", ctypes.c_int),
                 ("flags", ctypes.c_int), ("self_eps", ctypes.c_double),
-                ("hbm_budget", ctypes.c_size_t)]
+                ("hbm_budget", ctypes.c_size_t), ("damping", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

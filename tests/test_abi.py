@@ -72,7 +72,8 @@ def _host_plan(X, Y=None, **kw):
 def test_argument_errors():
     X = W.points("sphere", 100, 1)
     for kw, frag in [(dict(order=1), "order"), (dict(order=9), "order"), (dict(leaf_size=0), "leaf"),
-                     (dict(kappa=-1.0), "kappa"), (dict(fft_n=5, order=4), "fft_n")]:
+                     (dict(kappa=-1.0), "kappa"), (dict(fft_n=5, order=4), "fft_n"),
+                     (dict(damping=-0.5), "damping"), (dict(damping=float("inf")), "damping")]:
         args = dict(kappa=1.0, order=4, leaf_size=8)
         args.update(kw)
         with pytest.raises(defmm.DefmmError) as e:

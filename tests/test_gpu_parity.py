@@ -147,6 +147,25 @@ def test_m2l_rhs_blocks_are_bitwise_identical(order):
     assert _rel(outs[0], ref) <= TOL64
 
 
+@pytest.mark.parametrize("kind,kd,damping_d,order", [("sphere", 0.0, 8.0, 5), ("box", 24.0, 6.0, 4),
+                                                     ("ellipsoid", 48.0, 2.0, 4)])
+def test_damped_kernel_against_oracle(kind, kd, damping_d, order):
+    """Yukawa (kappa = 0) and damped Helmholtz kernels exp((i kappa - lambda) r)/(4 pi r):
+    complex128 and complex64 (CUDA-core and tensor-core near field) against the oracle."""
+    X = W.points(kind, 2500, 71)
+    D = float(np.max(X.max(0) - X.min(0)))
+    kappa, lam = kd / D, damping_d / D
+    q = W.charges(2500, 72, nrhs=2)
+    plan = defmm.Plan(X, kappa=kappa, order=order, leaf_size=20, damping=lam)
+    ref = oracle_fmm.fmm(X, q, kappa, order=order, leaf=20, damping=lam)
+    assert _rel(_gpu(plan, q, torch.complex128), ref) <= TOL128
+    assert _rel(_gpu(plan, q, torch.complex64), ref) <= TOL64
+    plan.set_tuning(p2p_tc_min_rhs=1)
+    assert _rel(_gpu(plan, q, torch.complex64), ref) <= TOL64
+    undamped = oracle_fmm.fmm(X, q, kappa, order=order, leaf=20)
+    assert _rel(undamped, ref) > 0.05
+
+
 def test_multi_rhs_columns_and_determinism():
     X = W.points("sphere", 4000, 31)
     kappa = 20.0
