@@ -65,7 +65,11 @@ typedef enum { DEFMM_C64 = 0, DEFMM_C128 = 1 } defmm_dtype;
  *               0 the Laplace kernel; the method holds for such asymptotically
  *               smooth kernels (Sec. 1).  kappa alone sets the directional
  *               (high-frequency) structure; lambda enters the near field and
- *               the transfer spectra only.                                    */
+ *               the transfer spectra only.
+ *  m2l_chunk_blocks - most spectra + Fourier multipoles staged together by the
+ *               M2L kernel (0: the library's default, 8 for N = 7 or 9; a
+ *               positive value >= 2 may only lower it).  Smaller chunks use
+ *               less shared memory per block; no result depends on it.       */
 typedef struct {
     double eta;
     double hf_kw;
@@ -74,6 +78,7 @@ typedef struct {
     double self_eps;
     size_t hbm_budget;
     double damping;
+    int m2l_chunk_blocks;
 } defmm_options;
 
 #define DEFMM_PLAN_HOST_ONLY 1
@@ -159,13 +164,20 @@ defmm_status defmm_apply_noalloc(defmm_plan plan, const void* q, void* p, int nr
  *                   the measured workloads; defmm_plan_autotune times both.
  *                   The two kernels round differently (both within
  *                   single-precision accuracy of the same sum).
+ *  m2l_members_per_block - sibling targets per M2L thread block, 4 or 8
+ *                   (0 = the library's choice: 4 for N = 9 with one column per
+ *                   pass, else 8).  With 4, groups of more siblings take two
+ *                   blocks, each staging the group's chunks; smaller blocks fit
+ *                   more per SM.  Kernels without a 4-member variant use 8.
+ *                   No output depends on it (bit for bit).
  * The setting applies to applies enqueued after the call; CUDA graphs
  * captured earlier keep the value they were captured with.
  * Errors: DEFMM_ERR_ARG (NULL plan or tuning, m2l_rhs_block not in
- * {0, 1, 2, 4}, p2p_tc_min_rhs < 0).                                         */
+ * {0, 1, 2, 4}, p2p_tc_min_rhs < 0, m2l_members_per_block not in {0, 4, 8}). */
 typedef struct {
     int m2l_rhs_block;
     int p2p_tc_min_rhs;
+    int m2l_members_per_block;
 } defmm_tuning;
 
 defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning);
@@ -180,7 +192,9 @@ defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning);
  *    set (any N >= 2p-1 gives the same result, Sec. 2.3),
  *  - right-hand sides per M2L pass (1, 2, 4) when nrhs > 1 and complex64,
  *  - the tensor-core near field on or off when nrhs >= 8 and complex64
- *    (defmm_tuning.p2p_tc_min_rhs).
+ *    (defmm_tuning.p2p_tc_min_rhs),
+ *  - 8 or 4 sibling targets per M2L block for complex64
+ *    (defmm_tuning.m2l_members_per_block).
  * A smaller Ncrit changes the tree and so the approximation (within the
  * order's accuracy); the tensor-core near field changes rounding only; the
  * other choices change no result.
@@ -191,7 +205,7 @@ defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning);
  * is returned in *out (owned by the caller, free with defmm_destroy) and its
  * choice in *result (may be NULL).
  *  cache_path - NULL, or a text file of earlier choices ("defmm-tune <key>
- *               <leaf> <fft_n> <m2l_rhs_block> <tc> <ms>" lines, key a hash of the
+ *               <leaf> <fft_n> <m2l_rhs_block> <tc> <members> <ms>" lines, key a hash of the
  *               coordinates, sizes, kappa, order, nrhs, dtype, candidate range
  *               and plan options).  A matching line builds the plan with the
  *               stored choice without timing (result->from_cache = 1); after
@@ -212,6 +226,7 @@ typedef struct {
 typedef struct {
     int leaf_size, fft_n, m2l_rhs_block; /* the choice (fft_n 0: 2p-1) */
     int p2p_tensor_cores;                /* 1: tensor-core near field chosen */
+    int m2l_members_per_block;           /* 8, 4 (0 for complex128: the default) */
     double ms;                           /* its median apply time when timed */
     int candidates;                      /* configurations timed (0 from the cache) */
     int from_cache;                      /* 1 if the choice came from cache_path */

@@ -187,6 +187,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     size_t o_su = b.add(hp.slot_u);
     size_t o_m2f = b.add(hp.m2f_list);
     size_t o_gmo = b.add(hp.grp_member_off), o_gm = b.add(hp.grp_members), o_gco = b.add(hp.grp_chunk_off);
+    size_t o_ghf = b.add(hp.grp_half);
     size_t o_cbo = b.add(hp.chk_blk_off), o_cns = b.add(hp.chk_nspec), o_cb = b.add(hp.chk_blk);
     size_t o_coo = b.add(hp.chk_op_off), o_co = b.add(hp.chk_op);
     size_t o_p2m = b.add(hp.p2m_cells), o_l2p = b.add(hp.l2p_cells);
@@ -241,11 +242,13 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.grp_member_off = (const int32_t*)P(o_gmo); c.grp_members = (const int32_t*)P(o_gm);
     c.grp_chunk_off = (const int32_t*)P(o_gco);
     c.n_grp = (int64_t)hp.grp_member_off.size() - 1;
+    c.grp_half = (const int32_t*)P(o_ghf); c.n_grp_half = (int64_t)hp.grp_half.size();
     c.chk_blk_off = (const int32_t*)P(o_cbo); c.chk_nspec = (const int32_t*)P(o_cns); c.chk_blk = (const int32_t*)P(o_cb);
     c.chk_op_off = (const int32_t*)P(o_coo); c.chk_op = (const int32_t*)P(o_co);
     c.chk_max_blocks = hp.chk_max_blocks;
     for (int v = 0; v < 3; ++v) c.chk_stage_blocks[v] = hp.chk_stage_blocks[v];
     c.m2l_rb = 0;
+    c.m2l_members = 0;
     c.p2p_tc_min_rhs = 0;
     c.p2m_cells = (const int32_t*)P(o_p2m); c.n_p2m = (int64_t)hp.p2m_cells.size();
     c.l2p_cells = (const int32_t*)P(o_l2p); c.n_l2p = (int64_t)hp.l2p_cells.size();
@@ -318,6 +321,7 @@ void defmm_default_options(defmm_options* opt) {
     opt->self_eps = 1e-10;
     opt->hbm_budget = 0;
     opt->damping = 0.0;
+    opt->m2l_chunk_blocks = 0;
 }
 
 const char* defmm_last_error(void) { return g_err.c_str(); }
@@ -327,9 +331,12 @@ defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning) 
     const int rb = tuning->m2l_rhs_block;
     if (rb != 0 && rb != 1 && rb != 2 && rb != 4) return fail(DEFMM_ERR_ARG, "m2l_rhs_block must be 0, 1, 2 or 4");
     if (tuning->p2p_tc_min_rhs < 0) return fail(DEFMM_ERR_ARG, "p2p_tc_min_rhs must be >= 0");
+    const int mb = tuning->m2l_members_per_block;
+    if (mb != 0 && mb != 4 && mb != 8) return fail(DEFMM_ERR_ARG, "m2l_members_per_block must be 0, 4 or 8");
     std::lock_guard<std::mutex> g(plan->busy);
     plan->common.m2l_rb = rb;
     plan->common.p2p_tc_min_rhs = tuning->p2p_tc_min_rhs;
+    plan->common.m2l_members = mb;
     return DEFMM_OK;
 }
 
@@ -337,6 +344,7 @@ defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning) {
     if (!plan || !tuning) return fail(DEFMM_ERR_ARG, "plan or tuning is NULL");
     tuning->m2l_rhs_block = plan->common.m2l_rb;
     tuning->p2p_tc_min_rhs = plan->common.p2p_tc_min_rhs;
+    tuning->m2l_members_per_block = plan->common.m2l_members;
     return DEFMM_OK;
 }
 
@@ -360,6 +368,7 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
         if (g_config_err != cudaSuccess) return cuda_fail(g_config_err, "kernel configuration");
     }
     if (!(o.damping >= 0.0) || !std::isfinite(o.damping)) return fail(DEFMM_ERR_ARG, "damping must be finite and >= 0");
+    if (o.m2l_chunk_blocks < 0 || o.m2l_chunk_blocks == 1) return fail(DEFMM_ERR_ARG, "m2l_chunk_blocks must be 0 or >= 2");
     defmm_plan_s* pl = new (std::nothrow) defmm_plan_s;
     if (!pl) return fail(DEFMM_ERR_OOM, "host allocation");
     pl->hbm_budget = o.hbm_budget;
@@ -369,7 +378,7 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
     if (s != DEFMM_OK) { delete pl; return s; }
     try {
         build_host_plan(hx.data(), nx, same ? nullptr : hy.data(), same ? nx : ny, kappa, order, leaf_size, o.eta,
-                        o.hf_kw, o.fft_n, o.self_eps, pl->hp);
+                        o.hf_kw, o.fft_n, o.self_eps, o.m2l_chunk_blocks, pl->hp);
     } catch (const std::bad_alloc&) {
         delete pl;
         return fail(DEFMM_ERR_OOM, "host allocation while building the plan");

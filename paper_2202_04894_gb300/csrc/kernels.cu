@@ -913,8 +913,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // The same group schedule with rows of samples and a warp-specialised
-// pipeline.  Consumer thread (member m, lane l) of the first 8*TPM threads
-// owns the x-rows l + j*TPM (j < ROWS) of member m; row (y, z) = (l mod N,
+// pipeline.  A block takes the MAXM (8 or 4) members of a group or, with
+// MAXM = 4, one half of a larger group (its own pass over the group's chunks,
+// using the ops of its members only).  Consumer thread (member m, lane l) of
+// the first MAXM*TPM threads owns the x-rows l + j*TPM (j < ROWS) of member m; row (y, z) = (l mod N,
 // l div N) holds the N samples xi = x + N*row.  Under a pair's symmetry
 // (sigma, s) a row's permuted indices are base(y, z) + x*step (with a wrap
 // for a negated x), so the permutation costs one row base per pair.  RB
@@ -930,9 +932,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // bounded chance to land.  F2L: each thread first takes the inverse DFT of
 // its rows along x in registers (p outputs per row), then the y and z passes
 // run in shared memory.  Needs N <= NX and N^2 <= ROWS*TPM.
-template <typename T, int NX, int TPM, int ROWS, int RB, int MINB, int PC = 0, int NC = 0>
-__global__ void __launch_bounds__(8 * TPM + 32, MINB) k_m2l_rows(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
-                                                                typename Cplx<T>::type* __restrict__ L, int R, int S, int stage_elems) {
+template <typename T, int NX, int TPM, int ROWS, int RB, int MINB, int PC = 0, int NC = 0, int MAXM = 8>
+__global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c, DevTyped<T> t, const typename Cplx<T>::type* __restrict__ Mhat,
+                                                                   typename Cplx<T>::type* __restrict__ L, int R, int S, int stage_elems) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int p = PC ? PC : c.p, N = NC ? NC : c.N, NFpad = c.NFpad, P3 = p * p * p;
@@ -944,10 +946,16 @@ __global__ void __launch_bounds__(8 * TPM + 32, MINB) k_m2l_rows(DevCommon c, De
     __shared__ int stride[6][3];
     __shared__ int abort_store, issued_sh, abort_at;
     volatile int& abort_sh = abort_store;   // written and polled by different warps
-    const int g = blockIdx.x;
-    const int mem0 = c.grp_member_off[g], nm = c.grp_member_off[g + 1] - mem0;
+    int g = blockIdx.x, mb = 0;                  // group, first member of this block
+    if (MAXM == 4) {
+        const int code = c.grp_half[blockIdx.x];
+        g = code >> 1;
+        mb = 4 * (code & 1);
+    }
+    const int mem0 = c.grp_member_off[g] + mb;
+    const int nm = min(MAXM, c.grp_member_off[g + 1] - mem0);
     const int ch0 = c.grp_chunk_off[g], nchunks = c.grp_chunk_off[g + 1] - ch0;
-    const bool producer = threadIdx.x >= 8 * TPM;
+    const bool producer = threadIdx.x >= MAXM * TPM;
     const int lane = threadIdx.x & 31;
     const int m = threadIdx.x / TPM, l = threadIdx.x % TPM;
     const bool member = !producer && m < nm;     // warp belongs to a member of the group
@@ -1029,7 +1037,7 @@ __global__ void __launch_bounds__(8 * TPM + 32, MINB) k_m2l_rows(DevCommon c, De
                 if (act[0]) {
                     const C* base = ring + (size_t)st * stage_elems;
                     const int* opoff = c.chk_op_off + 9 * (ch0 + k);
-                    const int o0 = opoff[m], o1 = opoff[m + 1];
+                    const int o0 = opoff[mb + m], o1 = opoff[mb + m + 1];
                     const int msh = RB == 1 ? 0 : (RB - 1) * __ldg(&c.chk_nspec[ch0 + k]);
                     int op_next = o0 < o1 ? __ldg(&c.chk_op[o0]) : 0;
                     for (int o = o0; o < o1; ++o) {
@@ -1134,9 +1142,9 @@ template <typename T> __host__ void m2l_shape(const DevCommon& c, int* S, size_t
 // Shape of a row-kernel launch with RB right-hand sides per pass: the stage
 // (in elements), the ring depth S (three stages if they fit in the shared
 // memory one block may use at the wanted residency, else two) and the dynamic
-// shared memory (ring, or the F2L arrays of 8 members if larger).  Returns
-// false if two stages or the F2L arrays do not fit in one block.
-template <typename T> __host__ bool m2l_rows_shape(const DevCommon& c, int RB, int blocks_per_sm, int* S,
+// shared memory (ring, or the F2L arrays of `members` members if larger).
+// Returns false if two stages or the F2L arrays do not fit in one block.
+template <typename T> __host__ bool m2l_rows_shape(const DevCommon& c, int RB, int blocks_per_sm, int members, int* S,
                                                    int* stage_elems, size_t* smem) {
     const int v = RB == 1 ? 0 : (RB == 2 ? 1 : 2);
     const size_t esz = sizeof(typename Cplx<T>::type);
@@ -1144,7 +1152,7 @@ template <typename T> __host__ bool m2l_rows_shape(const DevCommon& c, int RB, i
     const size_t stage = (size_t)*stage_elems * esz;
     size_t budget = (228 * 1024) / (size_t)(blocks_per_sm < 1 ? 1 : blocks_per_sm) - 1024 - 2048;
     if (budget > kSmemLimit) budget = kSmemLimit;
-    const size_t f2l = 8 * ((size_t)c.N * c.N * c.p + (size_t)c.N * c.p * c.p) * esz;
+    const size_t f2l = (size_t)members * ((size_t)c.N * c.N * c.p + (size_t)c.N * c.p * c.p) * esz;
     int ss = kM2LMaxStages;
     while (ss > 2 && (size_t)ss * stage > budget) --ss;
     const size_t ring = (size_t)ss * stage;
@@ -1725,7 +1733,7 @@ __device__ __forceinline__ void tc_split_store(float* hi, float* lo, int off, fl
 
 __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __restrict__ qs,
                                                 float2* __restrict__ part, int R, int rb0) {
-    extern __shared__ __align__(1024) float tsm[];
+    extern __shared__ __align__(128) float tsm[];
     __shared__ float4 th[kTcTgt], tl[kTcTgt];      // target hi / lo coordinates
     __shared__ float4 sh[kTcSrc], sl[kTcSrc];      // source hi / lo coordinates of the tile
     __shared__ float2 qsm[kTcSrc][33];             // charges / (4 pi) of the tile, [source][column]
@@ -1941,9 +1949,9 @@ __host__ int m2l_pick_rb(const DevCommon& c, int R) {
     return rb >= 4 ? 4 : (rb >= 2 ? 2 : 1);
 }
 
-template <typename T, int NX, int TPM, int ROWS, int RB, int MINB, int PC, int NC>
+template <typename T, int NX, int TPM, int ROWS, int RB, int MINB, int PC, int NC, int MAXM = 8>
 __host__ cudaError_t rows_config() {
-    auto k = k_m2l_rows<T, NX, TPM, ROWS, RB, MINB, PC, NC>;
+    auto k = k_m2l_rows<T, NX, TPM, ROWS, RB, MINB, PC, NC, MAXM>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
     if (e != cudaSuccess) return e;
     // the row kernel's occupancy is set by shared memory: ask for the largest carveout
@@ -1952,14 +1960,15 @@ __host__ cudaError_t rows_config() {
 
 // Launches one row-kernel variant; *fits = false (nothing launched) when its
 // ring or F2L arrays do not fit in one block's shared memory.
-template <typename T, int NX, int TPM, int ROWS, int RB, int MINB, int PC, int NC>
+template <typename T, int NX, int TPM, int ROWS, int RB, int MINB, int PC, int NC, int MAXM = 8>
 __host__ void rows_launch(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w, cudaStream_t stream,
                           bool* fits) {
     int S, stage;
     size_t sm;
-    *fits = m2l_rows_shape<T>(c, RB, MINB, &S, &stage, &sm);
+    *fits = m2l_rows_shape<T>(c, RB, MINB, MAXM, &S, &stage, &sm);
     if (!*fits) return;
-    k_m2l_rows<T, NX, TPM, ROWS, RB, MINB, PC, NC><<<(unsigned)c.n_grp, 8 * TPM + 32, sm, stream>>>(
+    const unsigned blocks = (unsigned)(MAXM == 4 ? c.n_grp_half : c.n_grp);
+    k_m2l_rows<T, NX, TPM, ROWS, RB, MINB, PC, NC, MAXM><<<blocks, MAXM * TPM + 32, sm, stream>>>(
         c, t, w.Mhat, w.L, w.R, S, stage);
 }
 
@@ -1975,7 +1984,8 @@ cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T
         if constexpr (F) {
             const int rb = m2l_pick_rb(c, w.R);
             if (p == 4 && N == 7) {
-                if (rb == 1) rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(c, t, w, stream, &fits);
+                if (rb == 1 && c.m2l_members == 4) rows_launch<T, 8, 64, 1, 1, 4, 4, 7, 4>(c, t, w, stream, &fits);
+                else if (rb == 1) rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(c, t, w, stream, &fits);
                 else if (rb == 2) rows_launch<T, 8, 64, 1, 2, 2, 4, 7>(c, t, w, stream, &fits);
                 else rows_launch<T, 8, 64, 1, 4, 1, 4, 7>(c, t, w, stream, &fits);
             } else {
@@ -1991,10 +2001,14 @@ cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T
         if (p == 5 && N == 9) {
             bool one = true;
             if constexpr (F) {
+                // one column per pass: blocks of 4 members (two per SM) measured faster;
+                // two columns: blocks of 8 (the larger ring wins)
                 one = m2l_pick_rb(c, w.R) == 1;
-                if (!one) rows_launch<T, 9, 96, 1, 2, 1, 5, 9>(c, t, w, stream, &fits);
+                if (!one && c.m2l_members == 4) rows_launch<T, 9, 96, 1, 2, 2, 5, 9, 4>(c, t, w, stream, &fits);
+                else if (!one) rows_launch<T, 9, 96, 1, 2, 1, 5, 9>(c, t, w, stream, &fits);
+                else if (c.m2l_members != 8) rows_launch<T, 9, 96, 1, 1, 2, 5, 9, 4>(c, t, w, stream, &fits);
             }
-            if (one) rows_launch<T, 9, 96, 1, 1, 1, 5, 9>(c, t, w, stream, &fits);
+            if (one && !fits) rows_launch<T, 9, 96, 1, 1, 1, 5, 9>(c, t, w, stream, &fits);
         } else if (p == 6 && N == 11) {
             rows_launch<T, 12, 64, 2, 1, 1, 6, 11>(c, t, w, stream, &fits);
         } else {
@@ -2203,6 +2217,9 @@ cudaError_t configure_kernels() {
         if ((e = rows_config<T, 8, 64, 1, 2, 2, 0, 0>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 8, 64, 1, 4, 1, 0, 0>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 9, 96, 1, 2, 1, 5, 9>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 1, 4, 4, 7, 4>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 9, 96, 1, 2, 2, 5, 9, 4>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 9, 96, 1, 1, 2, 5, 9, 4>()) != cudaSuccess) return e;
     } else {
         if ((e = rows_config<T, 8, 64, 1, 1, 1, 4, 7>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 8, 64, 1, 1, 1, 0, 0>()) != cudaSuccess) return e;

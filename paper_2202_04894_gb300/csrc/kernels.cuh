@@ -40,10 +40,12 @@ struct DevCommon {
     const int32_t* m2f_list;  int64_t n_m2f;
     // M2L schedule: groups of sibling targets, chunks of staged blocks and pair ops
     const int32_t *grp_member_off, *grp_members, *grp_chunk_off;  int64_t n_grp;
+    const int32_t* grp_half;  int64_t n_grp_half;   // blocks of <= 4 members: group * 2 + half
     const int32_t *chk_blk_off, *chk_nspec, *chk_blk, *chk_op_off, *chk_op;
     int chk_max_blocks;
     int chk_stage_blocks[3];  // largest stage (blocks) for 1, 2, 4 right-hand sides per pass
     int m2l_rb;               // right-hand sides per M2L pass (0: chosen from nrhs and N)
+    int m2l_members;          // members per M2L block, 4 or 8 (0: 8)
     int p2p_tc_min_rhs;       // complex64 applies with at least this many columns use the
                               // tensor-core near field (0: never)
     const int32_t* p2m_cells;  int64_t n_p2m;

@@ -211,7 +211,7 @@ template <typename U> static bool units_for_leaf_empty(const std::vector<U>& uni
 
 void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa,
                      int order, int leaf, double eta, double hf_kw, int fft_n, double self_eps,
-                     HostPlan& hp) {
+                     int chunk_blocks, HostPlan& hp) {
     if (nx < 1 || ny < 1) throw std::runtime_error("nx and ny must be >= 1");
     if (order < 2 || order > kMaxOrder) throw std::runtime_error("order must be in [2, 8]");
     if (leaf < 1) throw std::runtime_error("leaf_size must be >= 1");
@@ -437,8 +437,9 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
     {
         // blocks per chunk: about 22 KB of complex64 for N <= 8; for longer DFTs
         // up to 8, as long as two stages of complex128 fit in shared memory
-        const int max_blocks = hp.N <= 8 ? std::max(2, std::min(31, 22528 / (hp.NFpad * 8)))
-                                         : std::max(2, std::min(8, 115200 / (hp.NFpad * 16)));
+        int max_blocks = hp.N <= 8 ? std::max(2, std::min(31, 22528 / (hp.NFpad * 8)))
+                                   : std::max(2, std::min(8, 115200 / (hp.NFpad * 16)));
+        if (chunk_blocks > 0) max_blocks = std::max(2, std::min(max_blocks, chunk_blocks));   // may only shrink
         hp.chk_max_blocks = max_blocks;
         struct Op { int32_t member, src_parent, src, spec, code; };
         std::unordered_map<int64_t, int32_t> group_of;   // (father cell, direction) -> group
@@ -522,6 +523,11 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
                 hp.chk_op_off.push_back(base + (int32_t)k);
             }
             hp.grp_chunk_off.push_back((int32_t)hp.chk_nspec.size());
+        }
+        // the same groups cut into blocks of at most 4 members (heaviest first)
+        for (size_t gi = 0; gi + 1 < hp.grp_member_off.size(); ++gi) {
+            const int nm = hp.grp_member_off[gi + 1] - hp.grp_member_off[gi];
+            for (int h = 0; 4 * h < nm; ++h) hp.grp_half.push_back((int32_t)(2 * gi + h));
         }
     }
 

@@ -107,6 +107,7 @@ struct HostPlan {
     // sorted by member.  Groups are ordered by work, heaviest first.
     std::vector<int32_t> grp_member_off, grp_members;   // CSR: group -> local expansion ids
     std::vector<int32_t> grp_chunk_off;                 // CSR: group -> chunks
+    std::vector<int32_t> grp_half;                      // blocks of <= 4 members: group * 2 + half
     std::vector<int32_t> chk_blk_off, chk_nspec;        // CSR: chunk -> blocks; spectra first
     std::vector<int32_t> chk_blk;                       // spectrum id or Fourier-multipole slot
     std::vector<int32_t> chk_op_off;                    // 9 per chunk: op ranges of members 0..7, end
@@ -144,6 +145,6 @@ struct HostPlan {
 // Throws std::runtime_error with a message on invalid input.
 void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa,
                      int order, int leaf, double eta, double hf_kw, int fft_n, double self_eps,
-                     HostPlan& hp);
+                     int chunk_blocks, HostPlan& hp);
 
 }  // namespace defmm

@@ -9,7 +9,8 @@
 //  - DFT length N (plan time; 2p-1 and 2p, any N >= 2p-1 gives the same
 //    result, Sec. 2.3),
 //  - right-hand sides per M2L pass (apply time; 1, 2, 4 when nrhs > 1),
-//  - the tensor-core near field on or off (apply time; nrhs >= 8, complex64).
+//  - the tensor-core near field on or off (apply time; nrhs >= 8, complex64),
+//  - sibling targets per M2L block, 8 or 4 (apply time; complex64).
 // Every candidate plan is built with the public entry points, applied to a
 // fixed pseudo-random charge block of nrhs columns, and timed with CUDA events
 // on the caller's stream (median of `reps` applies after two warm-up applies).
@@ -17,7 +18,7 @@
 // being timed).  The fastest becomes the returned plan.
 //
 // Tune cache: a text file with one line per tuned geometry,
-//   defmm-tune <key> <leaf> <fft_n> <m2l_rhs_block> <tensor-core near field 0/1> <ms>
+//   defmm-tune <key> <leaf> <fft_n> <m2l_rhs_block> <tensor-core near field 0/1> <members> <ms>
 // where key is a 64-bit FNV-1a hash of the coordinates, sizes, kappa, order,
 // nrhs, dtype, the candidate range and the plan options.  A hit builds the
 // plan directly with the stored choice; a miss tunes and appends a line.
@@ -51,7 +52,7 @@ struct Fnv {
 std::mutex g_cache_mutex;
 
 struct Choice {
-    int leaf = 0, fft_n = 0, rb = 0, tc = 0;
+    int leaf = 0, fft_n = 0, rb = 0, tc = 0, mem = 0;
     double ms = 0;
 };
 
@@ -65,9 +66,10 @@ bool cache_lookup(const char* path, uint64_t key, Choice* c) {
     while (std::fgets(line, sizeof line, f)) {
         uint64_t k;
         Choice v;
-        if (std::sscanf(line, "defmm-tune %" SCNx64 " %d %d %d %d %lf", &k, &v.leaf, &v.fft_n, &v.rb, &v.tc, &v.ms) == 6 &&
+        if (std::sscanf(line, "defmm-tune %" SCNx64 " %d %d %d %d %d %lf", &k, &v.leaf, &v.fft_n, &v.rb, &v.tc, &v.mem,
+                        &v.ms) == 7 &&
             k == key && v.leaf >= 1 && v.fft_n >= 0 && (v.rb == 0 || v.rb == 1 || v.rb == 2 || v.rb == 4) &&
-            (v.tc == 0 || v.tc == 1)) {
+            (v.tc == 0 || v.tc == 1) && (v.mem == 0 || v.mem == 4 || v.mem == 8)) {
             *c = v;   // the last matching line wins
             found = true;
         }
@@ -81,7 +83,7 @@ bool cache_store(const char* path, uint64_t key, const Choice& c) {
     std::lock_guard<std::mutex> lk(g_cache_mutex);
     FILE* f = std::fopen(path, "a");
     if (!f) return false;
-    std::fprintf(f, "defmm-tune %016" PRIx64 " %d %d %d %d %.6f\n", key, c.leaf, c.fft_n, c.rb, c.tc, c.ms);
+    std::fprintf(f, "defmm-tune %016" PRIx64 " %d %d %d %d %d %.6f\n", key, c.leaf, c.fft_n, c.rb, c.tc, c.mem, c.ms);
     return std::fclose(f) == 0;
 }
 
@@ -195,6 +197,8 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
     if (t.nrhs > 1 && t.dtype == DEFMM_C64) rbs = {1, 2, 4};
     std::vector<int> tcs = {0};
     if (t.nrhs >= 8 && t.dtype == DEFMM_C64) tcs = {0, 1};
+    std::vector<int> mems = {0};
+    if (t.dtype == DEFMM_C64) mems = {8, 4};
 
     // cache key: coordinates (host or device), sizes, parameters
     Fnv key;
@@ -225,7 +229,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
         }
         key.val(nx); key.val(nys); key.val(same); key.val(kappa); key.val(order);
         key.val(t.nrhs); key.val((int)t.dtype); key.val(t.leaf_min); key.val(t.leaf_max); key.val(t.tune_fft_n);
-        key.val(o.eta); key.val(o.hf_kw); key.val(o.fft_n); key.val(o.self_eps); key.val(o.damping);
+        key.val(o.eta); key.val(o.hf_kw); key.val(o.fft_n); key.val(o.self_eps); key.val(o.damping); key.val(o.m2l_chunk_blocks);
     }
 
     defmm_tune_result res{};
@@ -236,10 +240,11 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
         defmm_plan pl = nullptr;
         defmm_status s = defmm_plan_create(X, nx, Y, ny, kappa, order, hit.leaf, &oc, stream, &pl);
         if (s != DEFMM_OK) return s;
-        defmm_tuning tn{hit.rb, hit.tc ? 1 : 0};
+        defmm_tuning tn{hit.rb, hit.tc ? 1 : 0, hit.mem};
         s = defmm_plan_set_tuning(pl, &tn);
         if (s != DEFMM_OK) { defmm_destroy(pl); return s; }
         res.leaf_size = hit.leaf; res.fft_n = hit.fft_n; res.m2l_rhs_block = hit.rb; res.p2p_tensor_cores = hit.tc;
+        res.m2l_members_per_block = hit.mem;
         res.ms = hit.ms;
         res.candidates = 0; res.from_cache = 1;
         if (result) *result = res;
@@ -281,8 +286,9 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
             bool kept = false;
             bool oom = false;
             for (int tc : tcs) {
+                for (int mem : mems)
                 for (int rb : rbs) {
-                    defmm_tuning tn{rb, tc ? 1 : 0};
+                    defmm_tuning tn{rb, tc ? 1 : 0, mem};
                     s = defmm_plan_set_tuning(pl, &tn);
                     double ms = 0;
                     if (s == DEFMM_OK) s = time_applies(pl, b, t.nrhs, t.dtype, t.reps, st, &ms);
@@ -294,7 +300,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
                     }
                     ++timed;
                     if (ms < bc.ms) {
-                        bc.leaf = leaf; bc.fft_n = fft; bc.rb = rb; bc.tc = tc; bc.ms = ms;
+                        bc.leaf = leaf; bc.fft_n = fft; bc.rb = rb; bc.tc = tc; bc.mem = mem; bc.ms = ms;
                         if (!kept) {
                             if (best) defmm_destroy(best);
                             best = pl;
@@ -308,7 +314,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
         }
     }
     if (!best) return defmm::set_error(DEFMM_ERR_OOM, "autotune: no candidate fits the device or hbm_budget");
-    defmm_tuning tn{bc.rb, bc.tc ? 1 : 0};
+    defmm_tuning tn{bc.rb, bc.tc ? 1 : 0, bc.mem};
     defmm_status s = defmm_plan_set_tuning(best, &tn);
     if (s != DEFMM_OK) { defmm_destroy(best); return s; }
     if (!cache_store(t.cache_path, key.h, bc)) {
@@ -316,6 +322,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
         return defmm::set_error(DEFMM_ERR_ARG, std::string("autotune: cannot append to ") + t.cache_path);
     }
     res.leaf_size = bc.leaf; res.fft_n = bc.fft_n; res.m2l_rhs_block = bc.rb; res.p2p_tensor_cores = bc.tc;
+    res.m2l_members_per_block = bc.mem;
     res.ms = bc.ms;
     res.candidates = timed; res.from_cache = 0;
     if (result) *result = res;

@@ -31,7 +31,8 @@ PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 class Options(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("hf_kw", ctypes.c_double), ("fft_n", ctypes.c_int),
                 ("flags", ctypes.c_int), ("self_eps", ctypes.c_double),
-                ("hbm_budget", ctypes.c_size_t), ("damping", ctypes.c_double)]
+                ("hbm_budget", ctypes.c_size_t), ("damping", ctypes.c_double),
+                ("m2l_chunk_blocks", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -48,7 +49,8 @@ class Info(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("m2l_rhs_block", ctypes.c_int), ("p2p_tc_min_rhs", ctypes.c_int)]
+    _fields_ = [("m2l_rhs_block", ctypes.c_int), ("p2p_tc_min_rhs", ctypes.c_int),
+                ("m2l_members_per_block", ctypes.c_int)]
 
 
 class TuneOptions(ctypes.Structure):
@@ -59,7 +61,8 @@ class TuneOptions(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("fft_n", ctypes.c_int), ("m2l_rhs_block", ctypes.c_int),
-                ("p2p_tensor_cores", ctypes.c_int), ("ms", ctypes.c_double), ("candidates", ctypes.c_int),
+                ("p2p_tensor_cores", ctypes.c_int), ("m2l_members_per_block", ctypes.c_int),
+                ("ms", ctypes.c_double), ("candidates", ctypes.c_int),
                 ("from_cache", ctypes.c_int)]
 
 
@@ -223,15 +226,16 @@ class Plan:
         _check(lib().defmm_profile_read(self._h, buf, len(PHASES), ctypes.byref(n)))
         return {PHASES[i]: buf[i] for i in range(n.value)}
 
-    def set_tuning(self, m2l_rhs_block: int = 0, p2p_tc_min_rhs: int = 0):
+    def set_tuning(self, m2l_rhs_block: int = 0, p2p_tc_min_rhs: int = 0, m2l_members_per_block: int = 0):
         """defmm_plan_set_tuning: launch choices of later applies."""
-        t = Tuning(int(m2l_rhs_block), int(p2p_tc_min_rhs))
+        t = Tuning(int(m2l_rhs_block), int(p2p_tc_min_rhs), int(m2l_members_per_block))
         _check(lib().defmm_plan_set_tuning(self._h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
         t = Tuning()
         _check(lib().defmm_plan_get_tuning(self._h, ctypes.byref(t)))
-        return {"m2l_rhs_block": t.m2l_rhs_block, "p2p_tc_min_rhs": t.p2p_tc_min_rhs}
+        return {"m2l_rhs_block": t.m2l_rhs_block, "p2p_tc_min_rhs": t.p2p_tc_min_rhs,
+                "m2l_members_per_block": t.m2l_members_per_block}
 
     def gmres(self, b, x0=None, shift=1.0, tol=1e-6, restart=30, max_iter=200, stream=None):
         """defmm_gmres: solves (shift I + A) x = b on the GPU.  b: complex64/complex128

@@ -73,7 +73,8 @@ def test_argument_errors():
     X = W.points("sphere", 100, 1)
     for kw, frag in [(dict(order=1), "order"), (dict(order=9), "order"), (dict(leaf_size=0), "leaf"),
                      (dict(kappa=-1.0), "kappa"), (dict(fft_n=5, order=4), "fft_n"),
-                     (dict(damping=-0.5), "damping"), (dict(damping=float("inf")), "damping")]:
+                     (dict(damping=-0.5), "damping"), (dict(damping=float("inf")), "damping"),
+                     (dict(m2l_chunk_blocks=1), "m2l_chunk_blocks"), (dict(m2l_chunk_blocks=-2), "m2l_chunk_blocks")]:
         args = dict(kappa=1.0, order=4, leaf_size=8)
         args.update(kw)
         with pytest.raises(defmm.DefmmError) as e:
@@ -92,10 +93,15 @@ def test_argument_errors():
 def test_tuning_values():
     """Apply-time tuning takes 0, 1, 2, 4 right-hand sides per M2L pass and rejects others."""
     pl = _host_plan(W.points("sphere", 300, 2), kappa=2.0, order=4, leaf_size=16)
-    assert pl.tuning() == {"m2l_rhs_block": 0, "p2p_tc_min_rhs": 0}
+    assert pl.tuning() == {"m2l_rhs_block": 0, "p2p_tc_min_rhs": 0, "m2l_members_per_block": 0}
     for v in (1, 2, 4, 0):
-        pl.set_tuning(m2l_rhs_block=v, p2p_tc_min_rhs=v)
-        assert pl.tuning() == {"m2l_rhs_block": v, "p2p_tc_min_rhs": v}
+        pl.set_tuning(m2l_rhs_block=v, p2p_tc_min_rhs=v, m2l_members_per_block=v if v in (0, 4) else 8)
+        assert pl.tuning() == {"m2l_rhs_block": v, "p2p_tc_min_rhs": v,
+                               "m2l_members_per_block": v if v in (0, 4) else 8}
+    for v in (2, 6, -4):
+        with pytest.raises(defmm.DefmmError) as e:
+            pl.set_tuning(m2l_members_per_block=v)
+        assert e.value.status == 1
     for v in (3, -1, 8):
         with pytest.raises(defmm.DefmmError) as e:
             pl.set_tuning(m2l_rhs_block=v)

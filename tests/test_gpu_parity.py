@@ -130,19 +130,25 @@ def test_tensor_core_near_field_many_columns():
 
 @pytest.mark.parametrize("order", [4, 5, 6])
 def test_m2l_rhs_blocks_are_bitwise_identical(order):
-    """1, 2 and 4 right-hand sides per M2L pass (with a ragged last pass: 5 columns)
-    give the same bits, and equal the oracle; N = 7, 9 (blocks of at most 2) and 11
-    (one column per pass)."""
+    """1, 2 and 4 right-hand sides per M2L pass (with a ragged last pass: 5 columns),
+    blocks of 8 or 4 members and a smaller chunk budget give the same bits, and equal
+    the oracle; N = 7, 9 (blocks of at most 2 columns) and 11 (one column per pass)."""
     X = W.points("sphere", 3000, 61)
     q = W.charges(3000, 62, nrhs=5)
     kappa = 30.0
     plan = defmm.Plan(X, kappa=kappa, order=order, leaf_size=24)
     outs = []
     for rb in (1, 2, 4, 0):
-        plan.set_tuning(m2l_rhs_block=rb)
-        outs.append(_gpu(plan, q, torch.complex64))
+        for members in (8, 4):
+            plan.set_tuning(m2l_rhs_block=rb, m2l_members_per_block=members)
+            outs.append(_gpu(plan, q, torch.complex64))
+            outs.append(_gpu(plan, q[:, 3], torch.complex64)[:, None])   # one column alone
     for o in outs[1:]:
-        assert np.array_equal(o, outs[0])
+        assert np.array_equal(o, outs[o.shape[1] == 1])
+    # smaller chunks stage fewer blocks at a time: same bits
+    small = defmm.Plan(X, kappa=kappa, order=order, leaf_size=24, m2l_chunk_blocks=3)
+    small.set_tuning(m2l_members_per_block=4)
+    assert np.array_equal(_gpu(small, q, torch.complex64), outs[0])
     ref = oracle_fmm.fmm(X, q, kappa, order=order, leaf=24)
     assert _rel(outs[0], ref) <= TOL64
 
