@@ -2010,7 +2010,10 @@ cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T
             }
             if (one && !fits) rows_launch<T, 9, 96, 1, 1, 1, 5, 9>(c, t, w, stream, &fits);
         } else if (p == 6 && N == 11) {
-            rows_launch<T, 12, 64, 2, 1, 1, 6, 11>(c, t, w, stream, &fits);
+            if constexpr (F) {   // complex64: blocks of 4 members, two per SM, unless 8 are asked for
+                if (c.m2l_members != 8) rows_launch<T, 12, 64, 2, 1, 2, 6, 11, 4>(c, t, w, stream, &fits);
+            }
+            if (!fits) rows_launch<T, 12, 64, 2, 1, 1, 6, 11>(c, t, w, stream, &fits);
         } else {
             rows_launch<T, 12, 64, 2, 1, 1, 0, 0>(c, t, w, stream, &fits);
         }
@@ -2220,6 +2223,7 @@ cudaError_t configure_kernels() {
         if ((e = rows_config<T, 8, 64, 1, 1, 4, 4, 7, 4>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 9, 96, 1, 2, 2, 5, 9, 4>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 9, 96, 1, 1, 2, 5, 9, 4>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 12, 64, 2, 1, 2, 6, 11, 4>()) != cudaSuccess) return e;
     } else {
         if ((e = rows_config<T, 8, 64, 1, 1, 1, 4, 7>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 8, 64, 1, 1, 1, 0, 0>()) != cudaSuccess) return e;
