@@ -1858,25 +1858,35 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
                     tc_split_store(Ahi, Alo, tc_off(r, 2 * s), q.x, -q.y);
                     tc_split_store(Ahi, Alo, tc_off(32 + r, 2 * s), q.y, q.x);
                 }
-                // B: kernel values of the tile, zero outside the targets and sources
-                for (int idx = tid; idx < N * kTcSrc; idx += blockDim.x) {
-                    const int t = idx % N, s = idx / N;
-                    float gr = 0.f, gi = 0.f;
-                    if (t < nt && s < ns) {
-                        const float4 xh = th[t], xl = tl[t], a = sh[s], b = sl[s];
-                        const float dx = (xh.x - a.x) + (xl.x - b.x);
-                        const float dy = (xh.y - a.y) + (xl.y - b.y);
-                        const float dz = (xh.z - a.z) + (xl.z - b.z);
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        float rinv = rsqrt_hw(r2);
-                        rinv = r2 > eps2 ? rinv : 0.f;
-                        float sn, cs;
-                        turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
-                        if (lam2 != 0.f) rinv *= ex2_hw(-lam2 * (r2 * rinv));
-                        gr = cs * rinv;
-                        gi = sn * rinv;
+                // B: kernel values of the tile, zero outside the targets and sources.
+                // Thread -> target t (a lane of 32 or 64) and a group of 4 or 8 sources.
+                {
+                    const bool narrow = N <= 32;
+                    const int t = narrow ? (tid & 31) : (tid & 63);
+                    const int sg = narrow ? (tid >> 5) : (tid >> 6);
+                    const int spg = narrow ? 4 : 8;
+                    if (t < N) {
+                        const float4 xh = th[t], xl = tl[t];
+                        for (int i = 0; i < spg; ++i) {
+                            const int s = sg * spg + i;
+                            float gr = 0.f, gi = 0.f;
+                            if (t < nt && s < ns) {
+                                const float4 a = sh[s], b = sl[s];
+                                const float dx = (xh.x - a.x) + (xl.x - b.x);
+                                const float dy = (xh.y - a.y) + (xl.y - b.y);
+                                const float dz = (xh.z - a.z) + (xl.z - b.z);
+                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                float rinv = rsqrt_hw(r2);
+                                rinv = r2 > eps2 ? rinv : 0.f;
+                                float sn, cs;
+                                turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                                if (lam2 != 0.f) rinv *= ex2_hw(-lam2 * (r2 * rinv));
+                                gr = cs * rinv;
+                                gi = sn * rinv;
+                            }
+                            tc_split_store(Bhi, Blo, tc_off(t, 2 * s), gr, gi);
+                        }
                     }
-                    tc_split_store(Bhi, Blo, tc_off(t, 2 * s), gr, gi);
                 }
                 tc::fence_smem_to_async();
                 __syncthreads();
