@@ -138,6 +138,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(total_ms, dist=None, device="cpu"):
+    """The timed region's length (ms) as the slowest rank saw it; identity on one process."""
+    if dist is None:
+        return float(total_ms)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, points, nrhs, ms_per_step):
+    """Mpoints*RHS/s of the whole job: every rank applies its own replica of the workload."""
+    return world * points * nrhs / (ms_per_step * 1e-3) / 1e6
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -305,14 +320,10 @@ def main():
     clk = clocks.stop()
     plan.profile(False)
     launches_per_apply = int(plan.info()["launches_per_apply"])
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     ms_per_step = total_ms / args.steps
+    value = whole_job_value(world, len(X), R, ms_per_step)
     units = world * len(X) * R
-    value = units / (ms_per_step * 1e-3) / 1e6
 
     # end to end through the host-buffer entry point (pinned host memory)
     qh = torch.from_numpy(np.ascontiguousarray(q.T)).to(cdt).pin_memory()
