@@ -120,7 +120,7 @@ struct DeviceBuffers {
     }
 };
 
-// Median time (ms) of `reps` applies after two warm-up applies; < 0 on error.
+// Median time (ms, into *ms) of `reps` applies after two warm-up applies.
 defmm_status time_applies(defmm_plan plan, DeviceBuffers& b, int nrhs, defmm_dtype dt, int reps,
                           cudaStream_t st, double* ms) {
     for (int w = 0; w < 2; ++w) {
@@ -199,6 +199,11 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
     if (t.nrhs >= 8 && t.dtype == DEFMM_C64) tcs = {0, 1};
     std::vector<int> mems = {0};
     if (t.dtype == DEFMM_C64) mems = {8, 4};
+    struct Launch { int tc, mem, rb; };   // apply-time choices timed on every candidate plan
+    std::vector<Launch> launches;
+    for (int tc : tcs)
+        for (int mem : mems)
+            for (int rb : rbs) launches.push_back({tc, mem, rb});
 
     // cache key: coordinates (host or device), sizes, parameters
     Fnv key;
@@ -284,31 +289,26 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
             if (s == DEFMM_ERR_OOM) continue;            // over the budget: not a candidate
             if (s != DEFMM_OK) { if (best) defmm_destroy(best); return s; }
             bool kept = false;
-            bool oom = false;
-            for (int tc : tcs) {
-                for (int mem : mems)
-                for (int rb : rbs) {
-                    defmm_tuning tn{rb, tc ? 1 : 0, mem};
-                    s = defmm_plan_set_tuning(pl, &tn);
-                    double ms = 0;
-                    if (s == DEFMM_OK) s = time_applies(pl, b, t.nrhs, t.dtype, t.reps, st, &ms);
-                    if (s == DEFMM_ERR_OOM) { oom = true; break; }   // workspace over the budget
-                    if (s != DEFMM_OK) {
-                        defmm_destroy(pl);
+            for (const Launch& lc : launches) {
+                defmm_tuning tn{lc.rb, lc.tc ? 1 : 0, lc.mem};
+                s = defmm_plan_set_tuning(pl, &tn);
+                double ms = 0;
+                if (s == DEFMM_OK) s = time_applies(pl, b, t.nrhs, t.dtype, t.reps, st, &ms);
+                if (s == DEFMM_ERR_OOM) break;   // this plan's workspace is over the budget
+                if (s != DEFMM_OK) {
+                    defmm_destroy(pl);
+                    if (best) defmm_destroy(best);
+                    return s;
+                }
+                ++timed;
+                if (ms < bc.ms) {
+                    bc.leaf = leaf; bc.fft_n = fft; bc.rb = lc.rb; bc.tc = lc.tc; bc.mem = lc.mem; bc.ms = ms;
+                    if (!kept) {
                         if (best) defmm_destroy(best);
-                        return s;
-                    }
-                    ++timed;
-                    if (ms < bc.ms) {
-                        bc.leaf = leaf; bc.fft_n = fft; bc.rb = rb; bc.tc = tc; bc.mem = mem; bc.ms = ms;
-                        if (!kept) {
-                            if (best) defmm_destroy(best);
-                            best = pl;
-                            kept = true;
-                        }
+                        best = pl;
+                        kept = true;
                     }
                 }
-                if (oom) break;
             }
             if (!kept) defmm_destroy(pl);
         }
