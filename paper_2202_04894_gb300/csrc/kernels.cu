@@ -2093,18 +2093,21 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
             p2p_done = true;
         }
     }
-    // complex64: 8 columns per pass from 8 columns on (each kernel value serves 8 products)
-    const int p2p_rb = R == 1 ? 1 : ((std::is_same<T, float>::value && R >= 8) ? 8 : 4);
+    // complex64: 8 columns per pass from 8 columns on, 16 from 16 on (each kernel value
+    // serves that many products)
+    const int p2p_rb = R == 1 ? 1 : (!std::is_same<T, float>::value ? 4 : (R >= 16 ? 16 : (R >= 8 ? 8 : 4)));
     for (int rb0 = 0; rb0 < R && !p2p_done; rb0 += p2p_rb) {
         if (c.n_p2p_units == 0) break;
         if constexpr (std::is_same<T, float>::value) {
             const unsigned nu = (unsigned)c.n_p2p_units;
             if (c.damping > 0.0) {
                 if (R == 1) k_p2p_f32<1, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                else if (p2p_rb == 16) k_p2p_f32<16, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else if (p2p_rb == 8) k_p2p_f32<8, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else k_p2p_f32<4, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
             } else {
                 if (R == 1) k_p2p_f32<1><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                else if (p2p_rb == 16) k_p2p_f32<16><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else if (p2p_rb == 8) k_p2p_f32<8><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else k_p2p_f32<4><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
             }
