@@ -9,7 +9,11 @@ P2M, M2M, M2F, Hadamard M2L + F2L, L2L, L2P, scatter.
 
 One JSON line on rank 0.  value = Mpoints*RHS/s over all ranks (replicas:
 each rank applies its own copy of the workload; there is no data-path
-collective).  Inputs are resident in HBM for `value`; `e2e` times the
+collective).  With --sharded and N > 1 the ranks split the one workload
+instead (defmm_plan_set_shard: each rank computes its Morton range of target
+leaves, the upward pass replicated) and an all-reduce of p inside the timed
+region assembles the result: strong scaling.  Inputs are resident in HBM for
+`value`; `e2e` times the
 host-buffer entry point (defmm_apply_host) with both copies inside.  L2 is
 flushed (a 512 MB write) before every timed step, outside the step's events.
 
@@ -148,6 +152,20 @@ def max_over_ranks(total_ms, dist=None, device="cpu"):
     return float(t.item())
 
 
+def exchange_shards(p, dist=None):
+    """The exchange step of the sharded apply: each rank holds its shard's
+    potentials and zeros elsewhere; an all-reduce (sum) leaves the whole result
+    on every rank (adding zeros changes no bit)."""
+    if dist is None:
+        return p
+    if p.is_complex():
+        v = __import__("torch").view_as_real(p)
+        dist.all_reduce(v)
+        return p
+    dist.all_reduce(p)
+    return p
+
+
 def whole_job_value(world, points, nrhs, ms_per_step):
     """Mpoints*RHS/s of the whole job: every rank applies its own replica of the workload."""
     return world * points * nrhs / (ms_per_step * 1e-3) / 1e6
@@ -227,6 +245,8 @@ def main():
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides (same charge recipe; for profiling)")
     ap.add_argument("--p2p-tensor-cores", action="store_true",
                     help="tensor-core near field (defmm_tuning.p2p_tc_min_rhs = 1)")
+    ap.add_argument("--sharded", action="store_true",
+                    help="N > 1: split the one workload across the ranks (strong scaling) instead of replicas")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=10000, help="serve16: number of requests")
     ap.add_argument("--gap-ms", type=float, default=2.0, help="serve16: mean inter-arrival time")
@@ -265,6 +285,9 @@ def main():
     plan_s = time.perf_counter() - t0
     if args.p2p_tensor_cores:
         plan.set_tuning(p2p_tc_min_rhs=1)
+    sharded = args.sharded and world > 1
+    if sharded:   # this rank computes its shard of the targets; an all-reduce assembles p
+        plan.set_shard(world, rank)
     info = plan.info()
     R = q.shape[1]
     qd = torch.from_numpy(np.ascontiguousarray(q)).to("cuda").to(cdt)
@@ -305,10 +328,13 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     step_ms = []
+    pbuf = torch.empty((R, len(X)), dtype=cdt, device="cuda") if sharded else None
     for k in range(args.steps):
         flush.fill_(float(k))
         starts[k].record(stream)
-        plan.apply(qd)
+        plan.apply(qd, out=pbuf)
+        if sharded:
+            exchange_shards(pbuf, dist)
         ends[k].record(stream)
         ends[k].synchronize()
         step_ms.append(starts[k].elapsed_time(ends[k]))
@@ -322,8 +348,8 @@ def main():
     launches_per_apply = int(plan.info()["launches_per_apply"])
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = whole_job_value(world, len(X), R, ms_per_step)
-    units = world * len(X) * R
+    value = whole_job_value(1 if sharded else world, len(X), R, ms_per_step)
+    units = (1 if sharded else world) * len(X) * R
 
     # end to end through the host-buffer entry point (pinned host memory)
     qh = torch.from_numpy(np.ascontiguousarray(q.T)).to(cdt).pin_memory()
@@ -385,12 +411,14 @@ def main():
     if rank == 0:
         srt = sorted(step_ms)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "strong" if sharded else "weak",
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": args.workload, "points": len(X), "kappa_d": W_["kappa_d"], "order": order,
                            "leaf": leaf, "nrhs": R, "distribution": W_["kind"], "l2": "flushed (512 MB write) before each step",
                            "p2p": "tensor cores (tcgen05)" if args.p2p_tensor_cores else "cuda cores",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": ("sharded targets, all-reduce of p" if sharded else "replicas") if world > 1
+                           else "single"},
                 "roofline": roof, "m2l_roofline": m2l_roof, "p2p_roofline": p2p_roof,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(X) * R * csz,

@@ -274,6 +274,32 @@ void defmm_default_gmres_options(defmm_gmres_options* opt);
 defmm_status defmm_gmres(defmm_plan plan, const void* b, void* x, defmm_dtype dtype,
                          const defmm_gmres_options* opt, void* stream, defmm_gmres_result* result);
 
+/* One shard of the operator for a multi-GPU split of one geometry.  The
+ * target leaves are cut, in Morton order, into nshards contiguous ranges of
+ * about equal estimated work (near-field interactions plus the M2L pairs of
+ * each leaf and its ancestors); shard s computes the potentials of its range.
+ * The upward pass (P2M, M2M, M2F) is replicated on every shard, M2L and the
+ * downward pass run only for target cells that hold targets of the shard
+ * (cells on a range boundary are computed by each shard that needs them).
+ * The paper's algorithm is single-core (Sec. 6); this split follows its tree.
+ *
+ * defmm_plan_set_shard makes later defmm_apply / defmm_apply_host calls on
+ * this plan compute shard `shard` of `nshards` (nshards = 1: the whole
+ * operator, the default): p receives the shard's potentials in the caller's
+ * order and zeros elsewhere, so summing the nshards outputs (an all-reduce
+ * across GPUs) gives the whole result, bit for bit.  Workspace, batch,
+ * server and no-allocation applies always compute the whole operator.  The
+ * call synchronises `stream` and the device, builds the shard's tables (one
+ * device allocation held by the plan) and returns.
+ * defmm_plan_shard_range gives the shard's targets in Morton (sorted) order:
+ * positions [first, first + count) of defmm_plan_table(plan, "perm_t", ...);
+ * it needs no GPU (host-only plans too).
+ * Errors: DEFMM_ERR_ARG (NULL pointers, not 0 <= shard < nshards),
+ * DEFMM_ERR_UNSUPPORTED (host-only plan, set_shard), DEFMM_ERR_BUSY,
+ * DEFMM_ERR_CUDA.                                                            */
+defmm_status defmm_plan_set_shard(defmm_plan plan, int nshards, int shard, void* stream);
+defmm_status defmm_plan_shard_range(defmm_plan plan, int nshards, int shard, int64_t* first, int64_t* count);
+
 /* Frees the plan and its device memory (synchronises the device first).       */
 defmm_status defmm_destroy(defmm_plan plan);
 

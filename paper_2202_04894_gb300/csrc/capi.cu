@@ -1,6 +1,7 @@
 // C ABI of the library (include/defmm.h): plan upload, workspace and calls.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include <cstdio>
@@ -299,7 +300,20 @@ template <typename T> defmm_status apply_impl(defmm_plan_s* pl, Workspace<T>& w,
     dw.part = w.part;
     const DevTyped<T>& typed = typed_tables(pl, (T*)nullptr);
     int launches = 0;
-    cudaError_t e = launch_apply<T>(pl->common, typed, dw, pl->m2m.data(), (int)pl->m2m.size(), pl->l2l.data(),
+    DevCommon c = pl->common;
+    const LevelList* l2l = pl->l2l.data();
+    if (pl->sh.nshards > 1) {   // this plan's shard of the targets
+        const auto& h = pl->sh;
+        c.sh_on = 1;
+        c.sh_grp = h.grp; c.n_grp = h.n_grp;
+        c.grp_half = h.half; c.n_grp_half = h.n_half;
+        c.sh_unit = h.unit; c.n_p2p_units = h.n_unit;
+        c.sh_leaf = h.leaf; c.n_p2p_leaf = h.n_leaf;
+        c.l2p_cells = h.l2p; c.n_l2p = h.n_l2p;
+        c.sh_t0 = h.t0; c.sh_t1 = h.t1;
+        l2l = h.l2l.data();
+    }
+    cudaError_t e = launch_apply<T>(c, typed, dw, pl->m2m.data(), (int)pl->m2m.size(), l2l,
                                     pl->l2l_par.data(), (int)pl->l2l.size(), q, p, stream, &launches,
                                     pl->profiling ? pl->events : nullptr);
     pl->launches = launches;
@@ -308,9 +322,146 @@ template <typename T> defmm_status apply_impl(defmm_plan_s* pl, Workspace<T>& w,
     return DEFMM_OK;
 }
 
+// Morton-contiguous split of the target leaves into nshards ranges of about
+// equal estimated work: a leaf costs its near-field interactions plus, for
+// every M2L pair of the leaf or an ancestor, 1.3 * N^3 (the measured cost of a
+// pair relative to an interaction), shared among the ancestor's leaves by
+// their points.  Returns the sorted-target range [t0, t1) of shard `shard`.
+void shard_range(const HostPlan& hp, int nshards, int shard, int64_t* t0, int64_t* t1) {
+    const Tree& tt = hp.tt;
+    std::vector<int32_t> leaves;
+    for (int32_t c = 0; c < tt.ncell(); ++c)
+        if (tt.leaf(c) && tt.end[c] > tt.begin[c]) leaves.push_back(c);
+    std::sort(leaves.begin(), leaves.end(), [&](int32_t a, int32_t b) { return tt.begin[a] < tt.begin[b]; });
+    std::vector<double> pairs(tt.ncell(), 0.0);
+    for (const auto& r : hp.m2l) pairs[r[0]] += 1.0;
+    std::vector<double> cost(tt.ncell(), 0.0);   // per leaf cell
+    for (size_t u = 0; u + 1 < hp.p2p_unit_off.size(); ++u) {
+        const int32_t leaf = hp.p2p_leaf[hp.p2p_unit_leaf[u]];
+        double ns = 0;
+        for (int32_t k = hp.p2p_unit_off[u]; k < hp.p2p_unit_off[u + 1]; ++k) ns += hp.p2p_send[k] - hp.p2p_sbeg[k];
+        cost[leaf] += ns * (double)(tt.end[leaf] - tt.begin[leaf]);
+    }
+    const double w = 1.3 * hp.NF;
+    for (int32_t leaf : leaves) {
+        const double np = (double)(tt.end[leaf] - tt.begin[leaf]);
+        for (int32_t a = leaf; a >= 0; a = tt.parent[a])
+            if (pairs[a] > 0) cost[leaf] += w * pairs[a] * np / (double)(tt.end[a] - tt.begin[a]);
+    }
+    double total = 0;
+    for (int32_t leaf : leaves) total += cost[leaf];
+    // boundary k: the first leaf whose preceding work reaches k * total / nshards
+    auto boundary = [&](int k) -> int64_t {
+        if (k <= 0) return 0;
+        if (k >= nshards) return hp.nx;
+        const double goal = total * k / nshards;
+        double acc = 0;
+        for (int32_t leaf : leaves) {
+            if (acc >= goal) return tt.begin[leaf];
+            acc += cost[leaf];
+        }
+        return hp.nx;
+    };
+    *t0 = boundary(shard);
+    *t1 = std::max(*t0, boundary(shard + 1));
+}
+
+// Device lists of the shard: target cells overlapping [t0, t1) (a leaf of the
+// shard or an ancestor of one) select the M2L groups and half-groups with such
+// a member, the L2L entries of such sons, the L2P leaves, the P2P units and
+// leaves.  Everything upward of M2L (P2M, M2M, M2F) stays whole.
+defmm_status build_shard(defmm_plan_s* pl, int nshards, int shard, cudaStream_t stream) {
+    const HostPlan& hp = pl->hp;
+    auto& h = pl->sh;
+    cudaFree(h.arena);
+    h = defmm_plan_s::Shard();
+    h.nshards = nshards;
+    h.shard = shard;
+    if (nshards == 1) return DEFMM_OK;
+    shard_range(hp, nshards, shard, &h.t0, &h.t1);
+    const Tree& tt = hp.tt;
+    auto needed = [&](int32_t c) { return tt.begin[c] < h.t1 && tt.end[c] > h.t0; };
+    std::vector<int32_t> grp, half, unit, leaf, l2p;
+    const size_t ngrp = hp.grp_member_off.size() - 1;
+    for (size_t g = 0; g < ngrp; ++g)
+        for (int32_t m = hp.grp_member_off[g]; m < hp.grp_member_off[g + 1]; ++m)
+            if (needed(hp.l_cell[hp.grp_members[m]])) { grp.push_back((int32_t)g); break; }
+    for (int32_t code : hp.grp_half) {
+        const int32_t g = code >> 1, b = hp.grp_member_off[g] + 4 * (code & 1);
+        const int32_t e = std::min(b + 4, hp.grp_member_off[g + 1]);
+        for (int32_t m = b; m < e; ++m)
+            if (needed(hp.l_cell[hp.grp_members[m]])) { half.push_back(code); break; }
+    }
+    for (size_t u = 0; u < hp.p2p_unit_leaf.size(); ++u)
+        if (needed(hp.p2p_leaf[hp.p2p_unit_leaf[u]])) unit.push_back((int32_t)u);
+    for (size_t li = 0; li < hp.p2p_leaf.size(); ++li)
+        if (needed(hp.p2p_leaf[li])) leaf.push_back((int32_t)li);
+    for (int32_t c : hp.l2p_cells)
+        if (needed(c)) l2p.push_back(c);
+    std::vector<std::vector<int32_t>> l2l(hp.l2l_lvl.size());
+    for (size_t l = 0; l < hp.l2l_lvl.size(); ++l)
+        for (size_t i = 0; i + 3 < hp.l2l_lvl[l].size(); i += 4)
+            if (needed(hp.l_cell[hp.l2l_lvl[l][i]]))
+                l2l[l].insert(l2l[l].end(), hp.l2l_lvl[l].begin() + i, hp.l2l_lvl[l].begin() + i + 4);
+    // one device allocation, 256-byte aligned pieces
+    std::vector<const std::vector<int32_t>*> parts = {&grp, &half, &unit, &leaf, &l2p};
+    for (auto& v : l2l) parts.push_back(&v);
+    std::vector<size_t> off;
+    size_t total = 0;
+    for (auto* v : parts) {
+        off.push_back(total);
+        total += (v->size() * sizeof(int32_t) + 255) / 256 * 256;
+    }
+    if (total == 0) total = 256;
+    std::vector<unsigned char> host(total, 0);
+    for (size_t i = 0; i < parts.size(); ++i)
+        if (!parts[i]->empty()) std::memcpy(host.data() + off[i], parts[i]->data(), parts[i]->size() * sizeof(int32_t));
+    cudaError_t e = cudaMalloc(&h.arena, total);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.arena, host.data(), total, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cudaFree(h.arena);
+        h = defmm_plan_s::Shard();
+        cudaGetLastError();
+        return cuda_fail(e, "shard tables");
+    }
+    auto at = [&](size_t i) { return (const int32_t*)(h.arena + off[i]); };
+    h.grp = at(0); h.n_grp = (int64_t)grp.size();
+    h.half = at(1); h.n_half = (int64_t)half.size();
+    h.unit = at(2); h.n_unit = (int64_t)unit.size();
+    h.leaf = at(3); h.n_leaf = (int64_t)leaf.size();
+    h.l2p = at(4); h.n_l2p = (int64_t)l2p.size();
+    h.l2l.resize(l2l.size());
+    for (size_t l = 0; l < l2l.size(); ++l) h.l2l[l] = {at(5 + l), (int64_t)l2l[l].size() / 4};
+    return DEFMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+defmm_status defmm_plan_shard_range(defmm_plan plan, int nshards, int shard, int64_t* first, int64_t* count) {
+    if (!plan || !first || !count) return fail(DEFMM_ERR_ARG, "plan, first and count must not be NULL");
+    if (nshards < 1 || shard < 0 || shard >= nshards) return fail(DEFMM_ERR_ARG, "need 0 <= shard < nshards");
+    int64_t t0 = 0, t1 = plan->hp.nx;
+    if (nshards > 1) shard_range(plan->hp, nshards, shard, &t0, &t1);
+    *first = t0;
+    *count = t1 - t0;
+    return DEFMM_OK;
+}
+
+defmm_status defmm_plan_set_shard(defmm_plan plan, int nshards, int shard, void* stream) {
+    if (!plan) return fail(DEFMM_ERR_ARG, "plan is NULL");
+    if (nshards < 1 || shard < 0 || shard >= nshards) return fail(DEFMM_ERR_ARG, "need 0 <= shard < nshards");
+    if (plan->host_only) return fail(DEFMM_ERR_UNSUPPORTED, "plan was built with DEFMM_PLAN_HOST_ONLY");
+    std::unique_lock<std::mutex> lk(plan->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(DEFMM_ERR_BUSY, "plan is in use by another thread");
+    // earlier applies may still read the old shard tables
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "set_shard synchronisation");
+    return build_shard(plan, nshards, shard, (cudaStream_t)stream);
+}
 
 void defmm_default_options(defmm_options* opt) {
     if (!opt) return;
@@ -478,6 +629,7 @@ defmm_status defmm_destroy(defmm_plan plan) {
     plan->wf.release();
     plan->wd.release();
     cudaFree(plan->arena);
+    cudaFree(plan->sh.arena);
     delete plan;
     if (e != cudaSuccess) return cuda_fail(e, "destroy");
     return DEFMM_OK;

@@ -108,11 +108,12 @@ __global__ void k_gather(const C* __restrict__ q, C* __restrict__ qs, const int6
 
 template <typename C>
 __global__ void k_scatter(const C* __restrict__ ps, C* __restrict__ p, const int64_t* __restrict__ perm,
-                          int64_t n, int R) {
-    int64_t total = n * R;
+                          int64_t n, int R, int64_t j0, int64_t j1) {
+    // sorted targets j0 <= j < j1 (all of them unless the plan computes one shard)
+    const int64_t m = j1 - j0, total = m * R;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = i / n, j = i - r * n;
-        p[r * n + perm[j]] = ps[i];
+        int64_t r = i / m, j = j0 + (i - r * m);
+        p[r * n + perm[j]] = ps[r * n + j];
     }
 }
 
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
     __shared__ T lx[kSplit ? 128 : 1], ly[kSplit ? 128 : 1], lz[kSplit ? 128 : 1];
     __shared__ C sq[RB][128];
     __shared__ C red[4][64][RB];
-    const int u = blockIdx.x;
+    const int u = c.sh_unit ? c.sh_unit[blockIdx.x] : (int)blockIdx.x;   // work unit (of the shard)
     const int cell = c.p2p_leaf[c.p2p_unit_leaf[u]];
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
     __shared__ float2 sq[RB][128];
     __shared__ float2 red[RB][128];
     __shared__ int rbeg[kP2PRanges], roff[kP2PRanges + 1];
-    const int u = blockIdx.x;
+    const int u = c.sh_unit ? c.sh_unit[blockIdx.x] : (int)blockIdx.x;   // work unit (of the shard)
     const int cell = c.p2p_leaf[c.p2p_unit_leaf[u]];
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
 // the units' source order, into the potentials.
 template <typename C>
 __global__ void __launch_bounds__(128) k_p2p_reduce(DevCommon c, const C* __restrict__ part, C* __restrict__ ps, int R) {
-    const int li = blockIdx.x;
+    const int li = c.sh_leaf ? c.sh_leaf[blockIdx.x] : (int)blockIdx.x;  // leaf (of the shard)
     const int cell = c.p2p_leaf[li];
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int u0 = c.p2p_leaf_off[li], u1 = c.p2p_leaf_off[li + 1];
@@ -790,7 +791,7 @@ __global__ void __launch_bounds__(MAXT) k_m2l(DevCommon c, DevTyped<T> t, const 
     __shared__ __align__(8) uint64_t bars[kM2LMaxStages];
     __shared__ C tws[16];
     __shared__ int stride[6][3];               // N^sigma(a) for each axis permutation
-    const int g = blockIdx.x;
+    const int g = c.sh_grp ? c.sh_grp[blockIdx.x] : (int)blockIdx.x;   // group (of the shard)
     const int mem0 = c.grp_member_off[g], nm = c.grp_member_off[g + 1] - mem0;
     const int ch0 = c.grp_chunk_off[g], nchunks = c.grp_chunk_off[g + 1] - ch0;
     if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
@@ -946,11 +947,13 @@ __global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c,
     __shared__ int stride[6][3];
     __shared__ int abort_store, issued_sh, abort_at;
     volatile int& abort_sh = abort_store;   // written and polled by different warps
-    int g = blockIdx.x, mb = 0;                  // group, first member of this block
-    if (MAXM == 4) {
+    int g = blockIdx.x, mb = 0;                  // group (of the shard), first member of this block
+    if (MAXM == 4) {                             // grp_half holds the shard's half-groups when sharded
         const int code = c.grp_half[blockIdx.x];
         g = code >> 1;
         mb = 4 * (code & 1);
+    } else if (c.sh_grp) {
+        g = c.sh_grp[blockIdx.x];
     }
     const int mem0 = c.grp_member_off[g] + mb;
     const int nm = min(MAXM, c.grp_member_off[g + 1] - mem0);
@@ -1742,7 +1745,7 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
     __shared__ uint32_t taddr_sh;
     __shared__ int fail_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int u = blockIdx.x;
+    const int u = c.sh_unit ? c.sh_unit[blockIdx.x] : (int)blockIdx.x;   // work unit (of the shard)
     const int cell = c.p2p_leaf[c.p2p_unit_leaf[u]];
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
@@ -2206,7 +2209,13 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
-    k_scatter<C><<<sms, 256, 0, stream>>>(w.ps, reinterpret_cast<C*>(p), c.perm_t, c.nx, R);
+    if (c.sh_on) {   // one shard: its targets, zeros elsewhere (the shards' outputs sum to the whole)
+        err = cudaMemsetAsync(p, 0, (size_t)c.nx * R * sizeof(C), stream);
+        if (err != cudaSuccess) return err;
+    }
+    if (!c.sh_on || c.sh_t1 > c.sh_t0)
+        k_scatter<C><<<sms, 256, 0, stream>>>(w.ps, reinterpret_cast<C*>(p), c.perm_t, c.nx, R,
+                                              c.sh_on ? c.sh_t0 : 0, c.sh_on ? c.sh_t1 : c.nx);
     DEFMM_CHECK_LAUNCH();
     DEFMM_MARK();
 #undef DEFMM_CHECK_LAUNCH

@@ -56,6 +56,13 @@ struct DevCommon {
     const int32_t *p2p_leaf, *p2p_leaf_off, *p2p_leaf_units;
     int64_t n_p2p_leaf;
     int* err_flag;           // set by a kernel whose bounded wait gave up (read by defmm_check)
+    // One shard of the targets (sh_on): the M2L groups, P2P units and P2P leaves
+    // to run (indices into the full tables) and the sorted targets written,
+    // [sh_t0, sh_t1).  The L2L / L2P lists and grp_half are swapped for the
+    // shard's own.  Off: every table entry in order.
+    int sh_on;
+    const int32_t *sh_grp, *sh_unit, *sh_leaf;
+    int64_t sh_t0, sh_t1;
 };
 
 // Tables in the arithmetic precision T.

@@ -49,4 +49,13 @@ struct defmm_plan_s {
     bool profiled = false;
     cudaEvent_t events[defmm::kNumPhases + 1] = {};
     std::mutex busy;
+    // the shard this plan's defmm_apply computes (nshards == 1: the whole operator)
+    struct Shard {
+        int nshards = 1, shard = 0;
+        int64_t t0 = 0, t1 = 0;                    // sorted targets written
+        unsigned char* arena = nullptr;            // device copies of the lists below
+        const int32_t *grp = nullptr, *half = nullptr, *unit = nullptr, *leaf = nullptr, *l2p = nullptr;
+        int64_t n_grp = 0, n_half = 0, n_unit = 0, n_leaf = 0, n_l2p = 0;
+        std::vector<defmm::LevelList> l2l;
+    } sh;
 };

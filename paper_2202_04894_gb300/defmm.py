@@ -24,7 +24,8 @@ EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_
             "defmm_destroy", "defmm_plan_info", "defmm_plan_table", "defmm_profile_enable",
             "defmm_profile_read", "defmm_apply_noalloc", "defmm_plan_set_tuning",
             "defmm_plan_get_tuning", "defmm_default_tune_options", "defmm_plan_autotune",
-            "defmm_default_gmres_options", "defmm_gmres", "defmm_last_error"]
+            "defmm_default_gmres_options", "defmm_gmres", "defmm_plan_set_shard", "defmm_plan_shard_range",
+            "defmm_last_error"]
 PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 
 
@@ -129,6 +130,10 @@ def lib():
         L.defmm_gmres.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(GmresOptions), vp,
                                   ctypes.POINTER(GmresResult)]
         L.defmm_gmres.restype = ctypes.c_int
+        L.defmm_plan_set_shard.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+        L.defmm_plan_set_shard.restype = ctypes.c_int
+        L.defmm_plan_shard_range.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.defmm_plan_shard_range.restype = ctypes.c_int
         L.defmm_last_error.argtypes = []
         L.defmm_last_error.restype = ctypes.c_char_p
         _LIB = L
@@ -256,6 +261,16 @@ class Plan:
                                  C64 if bc.dtype == torch.complex64 else C128, ctypes.byref(o),
                                  _stream_handle(stream), ctypes.byref(r)))
         return x, {name: getattr(r, name) for name, _ in GmresResult._fields_}
+
+    def set_shard(self, nshards: int = 1, shard: int = 0, stream=None):
+        """defmm_plan_set_shard: later applies compute shard `shard` of `nshards`."""
+        _check(lib().defmm_plan_set_shard(self._h, int(nshards), int(shard), _stream_handle(stream)))
+
+    def shard_range(self, nshards: int, shard: int):
+        """defmm_plan_shard_range: (first, count) of the shard's targets in sorted order."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().defmm_plan_shard_range(self._h, int(nshards), int(shard), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def table(self, name: str) -> np.ndarray:
         n = ctypes.c_int64()

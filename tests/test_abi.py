@@ -206,3 +206,31 @@ def test_bench_finds_the_row_kernel_source():
     import bench
     h = bench.m2l_rows_source_sha()
     assert len(h) == 16 and int(h, 16) >= 0
+
+
+@pytest.mark.parametrize("kind,n,order", [("sphere", 3000, 4), ("box", 4000, 5)])
+def test_shard_ranges_partition_the_targets(kind, n, order):
+    """Shard ranges are contiguous, cover every target once, start on leaf boundaries,
+    and hold comparable work (here: no shard of 2 or 3 is empty or above 2/3 of the points)."""
+    X = W.points(kind, n, 81)
+    pl = _host_plan(X, kappa=30.0, order=order, leaf_size=24)
+    cells = pl.table("cells_t").reshape(-1, 7)            # level, ix, iy, iz, begin, end, parent
+    parents = set(cells[:, 6].tolist())
+    leaf_begins = {int(c[4]) for i, c in enumerate(cells) if i not in parents}
+    for S in (1, 2, 3, 5):
+        ranges = [pl.shard_range(S, s) for s in range(S)]
+        pos = 0
+        for first, count in ranges:
+            assert first == pos and count >= 0
+            assert first in leaf_begins or first == n
+            pos += count
+        assert pos == n
+        if S in (2, 3):
+            assert all(0 < c < 2 * n / 3 for _, c in ranges)
+    for bad in ((0, 0), (2, 2), (2, -1)):
+        with pytest.raises(defmm.DefmmError) as e:
+            pl.shard_range(*bad)
+        assert e.value.status == 1
+    with pytest.raises(defmm.DefmmError) as e:
+        pl.set_shard(2, 0)
+    assert e.value.status == 5

@@ -48,3 +48,36 @@ def test_reference_arm_other_ranks_exit_quietly():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def _shard_worker(rank, world, port, out, full, ranges):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    first, count = ranges[rank]
+    mine = np.zeros_like(full)
+    mine[first:first + count] = full[first:first + count]     # a shard's output: its rows, zeros elsewhere
+    got = bench.exchange_shards(torch.from_numpy(mine), dist)
+    np.save(out + ".%d.npy" % rank, got.numpy())
+    dist.destroy_process_group()
+
+
+def test_sharded_exchange_with_gloo(tmp_path):
+    """The exchange of the sharded apply: every rank holds its shard's rows and zeros
+    elsewhere; after the all-reduce every rank holds the whole result, unchanged bit for bit."""
+    import numpy as np
+    import torch.multiprocessing as mp
+    from paper_2202_04894_gb300 import defmm, workloads as W
+    X = W.points("sphere", 2000, 91)
+    pl = defmm.Plan(X, kappa=10.0, order=4, leaf_size=24, flags=defmm.PLAN_HOST_ONLY)
+    ranges = [pl.shard_range(2, s) for s in range(2)]
+    rng = np.random.default_rng(3)
+    full = (rng.standard_normal((2000, 3)) + 1j * rng.standard_normal((2000, 3))).astype(np.complex64)
+    out = str(tmp_path / "s")
+    port = 31500 + (os.getpid() % 2000)
+    mp.spawn(_shard_worker, args=(2, port, out, full, ranges), nprocs=2, join=True)
+    for r in range(2):
+        assert np.array_equal(np.load(out + ".%d.npy" % r), full)
