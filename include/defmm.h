@@ -255,7 +255,8 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
  * converged (rel_residual <= tol).  Not converging is not an error.
  * Allocates (n x (restart + 1)) complex values of device scratch per call.
  * Errors: DEFMM_ERR_ARG (NULL pointers, nx != ny, restart outside [1, 1000],
- * max_iter < 0, tol < 0), DEFMM_ERR_UNSUPPORTED (dtype, host-only plan),
+ * max_iter < 0, tol < 0), DEFMM_ERR_UNSUPPORTED (dtype, host-only plan, a plan
+ * set to one shard by defmm_plan_set_shard),
  * DEFMM_ERR_OOM, DEFMM_ERR_CUDA, DEFMM_ERR_BUSY, DEFMM_ERR_TIMEOUT.          */
 typedef struct {
     double shift_re, shift_im; /* sigma */

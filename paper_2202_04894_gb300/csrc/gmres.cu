@@ -295,6 +295,7 @@ defmm_status defmm_gmres(defmm_plan plan, const void* b, void* x, defmm_dtype dt
     if (!(o.tol >= 0.0)) return defmm::set_error(DEFMM_ERR_ARG, "tol must be >= 0");
     if (plan->host_only) return defmm::set_error(DEFMM_ERR_UNSUPPORTED, "plan was built with DEFMM_PLAN_HOST_ONLY");
     if (plan->hp.nx != plan->hp.ny) return defmm::set_error(DEFMM_ERR_ARG, "gmres needs as many targets as sources");
+    if (plan->sh.nshards > 1) return defmm::set_error(DEFMM_ERR_UNSUPPORTED, "gmres needs the whole operator (plan is sharded)");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = plan->hp.nx;
     if (dtype == DEFMM_C64)

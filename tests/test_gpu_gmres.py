@@ -54,3 +54,16 @@ def test_gmres_zero_rhs_and_iteration_cap():
     b = torch.from_numpy(W.charges(1500, 54)[:, 0]).to("cuda")
     x, info = plan.gmres(b, shift=0.01, tol=1e-14, restart=5, max_iter=7)
     assert info["iterations"] == 7 and info["converged"] == 0 and info["rel_residual"] < 1.0
+
+
+def test_gmres_refuses_a_sharded_plan():
+    X = W.points("sphere", 800, 55)
+    plan = defmm.Plan(X, kappa=2.0, order=4, leaf_size=32)
+    plan.set_shard(2, 1)
+    b = torch.ones(800, dtype=torch.complex64, device="cuda")
+    with pytest.raises(defmm.DefmmError) as e:
+        plan.gmres(b)
+    assert e.value.status == 5
+    plan.set_shard(1, 0)
+    _, info = plan.gmres(b, shift=20.0, tol=1e-4)
+    assert info["converged"] == 1
