@@ -107,6 +107,25 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
                                double kappa, int order, int leaf_size,
                                const defmm_options* opt, void* stream, defmm_plan* out);
 
+/* A union of several independent geometries in one plan: geometry g has
+ * nx[g] points X[g] (sources = targets) and wavenumber kappa[g]; order, leaf
+ * size and options are shared.  Each geometry's plan is built as by
+ * defmm_plan_create and the tables are concatenated, so one defmm_apply runs
+ * every phase as one kernel launch over all geometries (per tree level for
+ * M2M and L2L) instead of one per geometry.  q and p hold the geometries'
+ * points one after another (geometry 0 first), in each geometry's own point
+ * order; there is no interaction between geometries, and each geometry's
+ * result equals its own plan's bit for bit.  defmm_plan_info reports sums
+ * over the geometries (nlevels: the deepest tree; d_aabb: the largest box);
+ * cell levels in defmm_plan_table are global level ids (one range per
+ * geometry).  The paper treats one geometry; this batches its application
+ * phase across many.
+ * Errors: DEFMM_ERR_ARG (ngeo < 1, NULL arrays, a geometry without points,
+ * kappa < 0, the errors of defmm_plan_create), DEFMM_ERR_OOM, DEFMM_ERR_CUDA. */
+defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int64_t* nx, const double* kappa,
+                                     int order, int leaf_size, const defmm_options* opt, void* stream,
+                                     defmm_plan* out);
+
 /* One application phase (Sec. 2.2 operators with M2F/F2L of Sec. 4.1.1):
  * P2M -> M2M -> M2F -> Hadamard M2L with permuted spectra -> F2L -> L2L -> L2P,
  * plus P2P over the near pairs of Alg. 1.

@@ -141,8 +141,13 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     // single-precision coordinates as hi + lo pairs relative to the cube centre
     auto split4 = [&](const std::vector<double>& src, int64_t n, const Tree& tr, size_t& oh, size_t& ol) {
         std::vector<float4> hi(n), lo(n);
-        const double c0[3] = {hp.corner[0] + hp.side / 2, hp.corner[1] + hp.side / 2, hp.corner[2] + hp.side / 2};
+        double c0[3] = {hp.corner[0] + hp.side / 2, hp.corner[1] + hp.side / 2, hp.corner[2] + hp.side / 2};
+        int g = 0;   // geometry of sorted point i (a union: relative to that geometry's cube centre)
         for (int64_t i = 0; i < n; ++i) {
+            if (hp.ngeo > 1) {
+                while (i >= hp.geo_point_off[g + 1]) ++g;
+                for (int a = 0; a < 3; ++a) c0[a] = hp.geo_center[3 * g + a];
+            }
             float h[3], l[3];
             for (int a = 0; a < 3; ++a) {
                 double d = src[3 * tr.perm[i] + a] - c0[a];
@@ -166,6 +171,10 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
         for (int32_t c = 0; c < tr.ncell(); ++c) {
             beg[c] = (int32_t)tr.begin[c];
             end[c] = (int32_t)tr.end[c];
+            if (hp.ngeo > 1) {   // a union: each geometry's own cube
+                for (int a = 0; a < 3; ++a) cor[3 * c + a] = hp.cell_corner_u[3 * c + a];
+                continue;
+            }
             double s = hp.lv.side(tr.level[c]);
             cor[3 * c] = hp.corner[0] + s * tr.ix[c];
             cor[3 * c + 1] = hp.corner[1] + s * tr.iy[c];
@@ -179,7 +188,13 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     else cells(ts, o_csb, o_cse, o_csl, o_csc);
     std::vector<double> lside(kNumLevels);
     for (int l = 0; l < kNumLevels; ++l) lside[l] = hp.lv.side(l);
+    if (hp.ngeo > 1) lside = hp.level_side_u;   // global level ids of a union
     size_t o_lside = b.add(lside);
+    size_t o_cgeo = 0, o_gk = 0, o_ge = 0, o_spk = 0;
+    if (hp.ngeo > 1) {
+        o_cgeo = b.add(hp.cell_geo); o_gk = b.add(hp.geo_kappa); o_ge = b.add(hp.geo_eps);
+        o_spk = b.add(hp.spec_kappa);
+    }
     const int32_t zero_flag[4] = {0, 0, 0, 0};
     size_t o_err = b.add(zero_flag, 4);
 
@@ -226,6 +241,11 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     DevCommon& c = pl->common;
     c.p = hp.p; c.N = hp.N; c.NF = hp.NF; c.NFpad = hp.NFpad; c.P3 = hp.P3;
     c.nx = hp.nx; c.ny = hp.ny; c.kappa = hp.kappa; c.eps_self = hp.eps_self; c.damping = hp.damping;
+    if (hp.ngeo > 1) {
+        c.cell_geo = (const int32_t*)P(o_cgeo);
+        c.geo_kappa = (const double*)P(o_gk);
+        c.geo_eps = (const double*)P(o_ge);
+    }
     c.Xs = (const double*)P(o_Xs); c.Ys = (const double*)P(o_Ys);
     c.perm_t = (const int64_t*)P(o_pt); c.perm_s = (const int64_t*)P(o_ps);
     c.Xh = (const float4*)P(o_Xh); c.Xl = (const float4*)P(o_Xl);
@@ -278,7 +298,8 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     pl->tf.spec = (const float2*)P(o_specf);
 
     cudaError_t e = launch_spectra((const int32_t*)P(o_sl), (const int32_t*)P(o_sk), (int)nspec,
-                                   (const double*)P(o_lside), hp.p, hp.N, hp.NFpad, hp.kappa, hp.damping,
+                                   (const double*)P(o_lside), hp.p, hp.N, hp.NFpad, hp.kappa,
+                                   hp.ngeo > 1 ? (const double*)P(o_spk) : nullptr, hp.damping,
                                    (double2*)P(o_specd), (float2*)P(o_specf), stream);
     if (e != cudaSuccess) return cuda_fail(e, "spectra kernel");
     CK(cudaStreamSynchronize(stream), "plan creation");
@@ -540,6 +561,63 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
     pl->hp.damping = o.damping;
     pl->host_only = host_only;
     s = host_only ? DEFMM_OK : upload(pl, hx, hy, (cudaStream_t)stream);
+    if (s != DEFMM_OK) {
+        cudaFree(pl->arena);
+        delete pl;
+        return s;
+    }
+    *out = pl;
+    return DEFMM_OK;
+}
+
+defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int64_t* nx, const double* kappa,
+                                     int order, int leaf_size, const defmm_options* opt, void* stream,
+                                     defmm_plan* out) {
+    if (!out) return fail(DEFMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (ngeo < 1 || !X || !nx || !kappa) return fail(DEFMM_ERR_ARG, "need ngeo >= 1 and X, nx, kappa arrays");
+    for (int g = 0; g < ngeo; ++g) {
+        if (!X[g] || nx[g] < 1) return fail(DEFMM_ERR_ARG, "every geometry needs points (X[g] != NULL, nx[g] >= 1)");
+        if (!(kappa[g] >= 0.0) || !std::isfinite(kappa[g])) return fail(DEFMM_ERR_ARG, "kappa must be finite and >= 0");
+    }
+    defmm_options o;
+    defmm_default_options(&o);
+    if (opt) o = *opt;
+    const bool host_only = (o.flags & DEFMM_PLAN_HOST_ONLY) != 0;
+    if (!host_only) {
+        std::call_once(g_config_once, [] {
+            g_config_err = configure_kernels<float>();
+            if (g_config_err == cudaSuccess) g_config_err = configure_kernels<double>();
+        });
+        if (g_config_err != cudaSuccess) return cuda_fail(g_config_err, "kernel configuration");
+    }
+    if (!(o.damping >= 0.0) || !std::isfinite(o.damping)) return fail(DEFMM_ERR_ARG, "damping must be finite and >= 0");
+    if (o.m2l_chunk_blocks < 0 || o.m2l_chunk_blocks == 1) return fail(DEFMM_ERR_ARG, "m2l_chunk_blocks must be 0 or >= 2");
+    defmm_plan_s* pl = new (std::nothrow) defmm_plan_s;
+    if (!pl) return fail(DEFMM_ERR_OOM, "host allocation");
+    pl->hbm_budget = o.hbm_budget;
+    std::vector<double> all;   // coordinates in the caller's order: geometry 0, then 1, ...
+    try {
+        std::vector<HostPlan> parts(ngeo);
+        for (int g = 0; g < ngeo; ++g) {
+            std::vector<double> hx;
+            defmm_status s = read_points(X[g], nx[g], hx, host_only);
+            if (s != DEFMM_OK) { delete pl; return s; }
+            build_host_plan(hx.data(), nx[g], nullptr, nx[g], kappa[g], order, leaf_size, o.eta, o.hf_kw, o.fft_n,
+                            o.self_eps, o.m2l_chunk_blocks, parts[g]);
+            parts[g].damping = o.damping;
+            all.insert(all.end(), hx.begin(), hx.end());
+        }
+        union_host_plans(parts, pl->hp);
+    } catch (const std::bad_alloc&) {
+        delete pl;
+        return fail(DEFMM_ERR_OOM, "host allocation while building the plan");
+    } catch (const std::exception& ex) {
+        delete pl;
+        return fail(DEFMM_ERR_ARG, ex.what());
+    }
+    pl->host_only = host_only;
+    defmm_status s = host_only ? DEFMM_OK : upload(pl, all, all, (cudaStream_t)stream);
     if (s != DEFMM_OK) {
         cudaFree(pl->arena);
         delete pl;

@@ -95,6 +95,15 @@ constexpr double kInv4Pi = 0.0795774715459476678844418816863;  // 1/(4 pi)
 constexpr double kInv2Pi = 0.159154943091895335768883763373;   // 1/(2 pi)
 constexpr double kLog2E = 1.44269504088896340735992468100;     // log2(e)
 
+// Wavenumber and self-distance of the geometry holding `cell` (a union plan
+// holds several geometries; a plain plan has one).
+__device__ __forceinline__ double kappa_of(const DevCommon& c, int cell) {
+    return c.cell_geo ? c.geo_kappa[c.cell_geo[cell]] : c.kappa;
+}
+__device__ __forceinline__ double eps_of(const DevCommon& c, int cell) {
+    return c.cell_geo ? c.geo_eps[c.cell_geo[cell]] : c.eps_self;
+}
+
 // ------------------------------------------------------------------ gather / scatter
 template <typename C>
 __global__ void k_gather(const C* __restrict__ q, C* __restrict__ qs, const int64_t* __restrict__ perm,
@@ -214,8 +223,9 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
     const double cz = c.ct_corner[3 * cell + 2] + 0.5 * side;
     const int nr = min(RB, R - rb0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const T kpar = kSplit ? (T)(c.kappa * kInv2Pi) : (T)c.kappa;
-    const T eps2 = (T)(c.eps_self * c.eps_self);
+    const double kap = kappa_of(c, cell), eps = eps_of(c, cell);
+    const T kpar = kSplit ? (T)(kap * kInv2Pi) : (T)kap;
+    const T eps2 = (T)(eps * eps);
     const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];
     for (int t0 = tb; t0 < te; t0 += 64) {
         const int ia = t0 + lane, ib = t0 + lane + 32;
@@ -312,8 +322,8 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
     const int nr = min(RB, R - rb0);
-    const float kap2pi = (float)(c.kappa * kInv2Pi);
-    const float eps2 = (float)(c.eps_self * c.eps_self);
+    const float kap2pi = (float)(kappa_of(c, cell) * kInv2Pi);
+    const float eps2 = (float)(eps_of(c, cell) * eps_of(c, cell));
     const float inv4pi = (float)kInv4Pi;
     const float lam2 = (float)(c.damping * kLog2E);     // damping in powers of 2 per unit length
     const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];
@@ -494,7 +504,7 @@ __global__ void __launch_bounds__(128) k_p2m(DevCommon c, DevTyped<T> t, const t
     const double h = side / (p - 1);
     const double cor[3] = {c.cs_corner[3 * cell], c.cs_corner[3 * cell + 1], c.cs_corner[3 * cell + 2]};
     const int nr = min(RB, R - rb0);
-    const T k2pi = (T)(c.kappa * kInv2Pi);
+    const T k2pi = (T)(kappa_of(c, cell) * kInv2Pi);
     const int ex0 = c.m_first[cell], nex = c.m_count[cell];
     for (int e0 = 0; e0 < nex; e0 += epass) {
         const int ne = min(epass, nex - e0);
@@ -1266,7 +1276,7 @@ __global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const t
     const double h = side / (p - 1);
     const double cor[3] = {c.ct_corner[3 * cell], c.ct_corner[3 * cell + 1], c.ct_corner[3 * cell + 2]};
     const int nr = min(RB, R - rb0);
-    const T k2pi = (T)(c.kappa * kInv2Pi);
+    const T k2pi = (T)(kappa_of(c, cell) * kInv2Pi);
     const int ex0 = c.l_first[cell], nex = c.l_count[cell];
     for (int t0 = b; t0 < e; t0 += 128) {
         const int nt = min(128, e - t0);
@@ -1399,7 +1409,7 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_p2m_warp(DevCommon c, DevTy
     const double h = side / (PC - 1);
     const double cx = c.cs_corner[3 * cell], cy = c.cs_corner[3 * cell + 1], cz = c.cs_corner[3 * cell + 2];
     const int nr = min(RB, R - rb0);
-    const T k2pi = (T)(c.kappa * kInv2Pi);
+    const T k2pi = (T)(kappa_of(c, cell) * kInv2Pi);
     const int ex0 = c.m_first[cell], nex = c.m_count[cell];
     for (int e0 = 0; e0 < nex; e0 += epass) {
         const int ne = min(epass, nex - e0);
@@ -1536,7 +1546,7 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_l2p_warp(DevCommon c, DevTy
     const double h = side / (PC - 1);
     const double cx = c.ct_corner[3 * cell], cy = c.ct_corner[3 * cell + 1], cz = c.ct_corner[3 * cell + 2];
     const int nr = min(RB, R - rb0);
-    const T k2pi = (T)(c.kappa * kInv2Pi);
+    const T k2pi = (T)(kappa_of(c, cell) * kInv2Pi);
     const int ex0 = c.l_first[cell], nex = c.l_count[cell];
     for (int t0 = b; t0 < e; t0 += 32) {
         const bool act = t0 + lane < e;
@@ -1625,8 +1635,8 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_l2p_warp(DevCommon c, DevTy
 // with e^{-2 pi i xi.x / N} (unnormalised) along x, y and z.
 __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spec_level, const int32_t* __restrict__ kbar,
                                                  const double* __restrict__ level_side, int p, int N, int NFpad,
-                                                 double kappa, double damping, double2* __restrict__ out_d,
-                                                 float2* __restrict__ out_f) {
+                                                 double kappa0, const double* __restrict__ spec_kappa, double damping,
+                                                 double2* __restrict__ out_d, float2* __restrict__ out_f) {
     extern __shared__ unsigned char smem_raw[];
     const int NF = N * N * N;
     double2* A = reinterpret_cast<double2*>(smem_raw);
@@ -1634,6 +1644,7 @@ __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spe
     __shared__ double2 tw[16];
     const int sid = blockIdx.x;
     const double side = level_side[spec_level[sid]];
+    const double kappa = spec_kappa ? spec_kappa[sid] : kappa0;   // the spectrum's geometry
     const double h = side / (p - 1);
     const double k0 = kbar[3 * sid], k1 = kbar[3 * sid + 1], k2 = kbar[3 * sid + 2];
     if (threadIdx.x < N) {
@@ -1682,12 +1693,14 @@ __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spe
 
 cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
                            const double* level_side, int p, int N, int NFpad, double kappa,
-                           double damping, double2* out_d, float2* out_f, cudaStream_t stream) {
+                           const double* spec_kappa, double damping, double2* out_d, float2* out_f,
+                           cudaStream_t stream) {
     if (nspec == 0) return cudaSuccess;
     size_t smem = 2 * (size_t)N * N * N * sizeof(double2);
     cudaError_t err = cudaFuncSetAttribute(k_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_spectra<<<nspec, 256, smem, stream>>>(spec_level, spec_kbar, level_side, p, N, NFpad, kappa, damping, out_d, out_f);
+    k_spectra<<<nspec, 256, smem, stream>>>(spec_level, spec_kbar, level_side, p, N, NFpad, kappa, spec_kappa, damping,
+                                            out_d, out_f);
     return cudaGetLastError();
 }
 
@@ -1750,8 +1763,8 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
     const int nr = min(32, R - rb0);
-    const float kap2pi = (float)(c.kappa * kInv2Pi);
-    const float eps2 = (float)(c.eps_self * c.eps_self);
+    const float kap2pi = (float)(kappa_of(c, cell) * kInv2Pi);
+    const float eps2 = (float)(eps_of(c, cell) * eps_of(c, cell));
     const float inv4pi = (float)kInv4Pi;
     const float lam2 = (float)(c.damping * kLog2E);
     const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];

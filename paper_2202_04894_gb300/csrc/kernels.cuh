@@ -63,6 +63,11 @@ struct DevCommon {
     int sh_on;
     const int32_t *sh_grp, *sh_unit, *sh_leaf;
     int64_t sh_t0, sh_t1;
+    // A union of several geometries: the geometry of each cell and the
+    // per-geometry wavenumber and self-distance (null for one geometry: kappa,
+    // eps_self above).  Cell levels are global level ids into level_side.
+    const int32_t* cell_geo;
+    const double *geo_kappa, *geo_eps;
 };
 
 // Tables in the arithmetic precision T.
@@ -107,6 +112,7 @@ constexpr int kNumPhases = 9;  // gather p2p p2m m2m m2f m2l l2l l2p scatter
 // Forms the canonical transfer spectra in float64 (Sec. 2.3 Eq. FourierDiagonal).
 cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
                            const double* level_side, int p, int N, int NFpad, double kappa,
-                           double damping, double2* out_d, float2* out_f, cudaStream_t stream);
+                           const double* spec_kappa, double damping, double2* out_d, float2* out_f,
+                           cudaStream_t stream);
 
 }  // namespace defmm

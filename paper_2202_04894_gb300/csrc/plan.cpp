@@ -673,3 +673,164 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
 }
 
 }  // namespace defmm
+
+namespace defmm {
+
+namespace {
+template <typename V> void append(std::vector<V>& dst, const std::vector<V>& src) {
+    dst.insert(dst.end(), src.begin(), src.end());
+}
+// dst += src with v -> v + off for v >= 0 (negative entries mark "none" and stay)
+template <typename V, typename O> void append_off(std::vector<V>& dst, const std::vector<V>& src, O off) {
+    dst.reserve(dst.size() + src.size());
+    for (V v : src) dst.push_back(v >= 0 ? (V)(v + off) : v);
+}
+}  // namespace
+
+void union_host_plans(std::vector<HostPlan>& parts, HostPlan& u) {
+    if (parts.empty()) throw std::runtime_error("union of no geometries");
+    const HostPlan& f = parts[0];
+    for (const HostPlan& h : parts) {
+        if (h.p != f.p || h.N != f.N) throw std::runtime_error("union: geometries need the same order and DFT length");
+        if (!h.same) throw std::runtime_error("union: sources must equal targets");
+    }
+    u = HostPlan();
+    u.same = true;
+    u.p = f.p; u.N = f.N; u.NF = f.NF; u.NFpad = f.NFpad; u.P3 = f.P3;
+    u.eta = f.eta; u.hf_kw = f.hf_kw; u.self_eps_rel = f.self_eps_rel; u.damping = f.damping;
+    u.kappa = f.kappa; u.eps_self = f.eps_self; u.d_aabb = f.d_aabb; u.side = f.side;
+    for (int a = 0; a < 3; ++a) u.corner[a] = f.corner[a];
+    u.lv = f.lv;
+    u.m1 = f.m1;
+    u.tw = f.tw;
+    u.ngeo = (int)parts.size();
+    u.geo_point_off.push_back(0);
+    u.geo_cell_off.push_back(0);
+    u.geo_level_off.push_back(0);
+    u.chk_max_blocks = 0;
+    std::vector<size_t> m2m_levels, l2l_levels;
+    size_t nlev_m2m = 0, nlev_l2l = 0;
+    for (const HostPlan& h : parts) {
+        nlev_m2m = std::max(nlev_m2m, h.m2m_lvl.size());
+        nlev_l2l = std::max(nlev_l2l, h.l2l_lvl.size());
+    }
+    u.m2m_lvl.assign(nlev_m2m, {});
+    u.l2l_lvl.assign(nlev_l2l, {});
+    u.l2l_par.assign(nlev_l2l, {});
+    u.grp_member_off.push_back(0);
+    u.grp_chunk_off.push_back(0);
+    u.chk_blk_off.push_back(0);
+    u.p2p_unit_off.push_back(0);
+    u.p2p_leaf_off.push_back(0);
+    for (HostPlan& h : parts) {
+        const int64_t pb = u.nx;                               // point base
+        const int32_t cb = u.tt.ncell();                       // cell base
+        const int32_t lb = u.geo_level_off.back();             // global level base
+        const int32_t mb = (int32_t)u.m_cell.size();           // multipole base
+        const int32_t eb = (int32_t)u.l_cell.size();           // local expansion base
+        const int32_t sb = (int32_t)u.slot_level.size();       // phase-slot base
+        const int32_t spb = (int32_t)u.spec_level.size();      // spectrum base
+        const int32_t hb = (int32_t)u.m2f_list.size();         // Fourier-multipole base
+        const int32_t gb = (int32_t)u.grp_member_off.size() - 1;
+        const int32_t gmb = (int32_t)u.grp_members.size();
+        const int32_t chb = (int32_t)u.chk_nspec.size();
+        const int32_t bb = (int32_t)u.chk_blk.size();
+        const int32_t ob = (int32_t)u.chk_op.size();
+        const int32_t ub = (int32_t)u.p2p_unit_leaf.size();
+        const int32_t rb = (int32_t)u.p2p_sbeg.size();
+        const int32_t leb = (int32_t)u.p2p_leaf.size();
+        const int32_t lub = (int32_t)u.p2p_leaf_units.size();
+        const int64_t partb = u.p2p_parts;
+        const int nlev = (int)h.tt.level_range.size();
+        // tree (sources = targets)
+        Tree& t = u.tt;
+        append_off(t.perm, h.tt.perm, pb);
+        for (int32_t lv : h.tt.level) t.level.push_back(lv + lb);
+        append(t.ix, h.tt.ix); append(t.iy, h.tt.iy); append(t.iz, h.tt.iz);
+        append_off(t.begin, h.tt.begin, pb); append_off(t.end, h.tt.end, pb);
+        append_off(t.parent, h.tt.parent, cb); append_off(t.first_child, h.tt.first_child, cb);
+        append(t.nchild, h.tt.nchild);
+        for (int32_t c = 0; c < h.tt.ncell(); ++c) {
+            const double s = h.lv.side(h.tt.level[c]);
+            u.cell_corner_u.push_back(h.corner[0] + s * h.tt.ix[c]);
+            u.cell_corner_u.push_back(h.corner[1] + s * h.tt.iy[c]);
+            u.cell_corner_u.push_back(h.corner[2] + s * h.tt.iz[c]);
+            u.cell_geo.push_back((int32_t)u.geo_kappa.size());
+        }
+        for (int l = 0; l < std::max(nlev, 1); ++l) u.level_side_u.push_back(h.lv.side(l));
+        for (auto& r : h.m2l) u.m2l.push_back({r[0] + cb, r[1] + cb, r[2]});
+        for (auto& r : h.p2p) u.p2p.push_back({r[0] + cb, r[1] + cb});
+        // expansions
+        append_off(u.m_cell, h.m_cell, cb); append(u.m_dir, h.m_dir);
+        append_off(u.m_first, h.m_first, mb); append(u.m_count, h.m_count);
+        append_off(u.l_cell, h.l_cell, cb); append(u.l_dir, h.l_dir);
+        append_off(u.l_first, h.l_first, eb); append(u.l_count, h.l_count);
+        append_off(u.m_slot, h.m_slot, sb); append_off(u.l_slot, h.l_slot, sb);
+        for (int32_t lv : h.slot_level) u.slot_level.push_back(lv + lb);
+        append(u.slot_dir, h.slot_dir); append(u.slot_u, h.slot_u);
+        append(u.slot_P, h.slot_P); append(u.slot_Q, h.slot_Q);
+        // spectra
+        for (int32_t lv : h.spec_level) u.spec_level.push_back(lv + lb);
+        append(u.spec_kbar, h.spec_kbar);
+        for (size_t i = 0; i < h.spec_level.size(); ++i) u.spec_kappa.push_back(h.kappa);
+        append_off(u.m2f_list, h.m2f_list, mb);
+        append_off(u.mhat_of_m, h.mhat_of_m, hb);
+        // M2L schedule
+        for (size_t i = 1; i < h.grp_member_off.size(); ++i) u.grp_member_off.push_back(h.grp_member_off[i] + gmb);
+        append_off(u.grp_members, h.grp_members, eb);
+        for (size_t i = 1; i < h.grp_chunk_off.size(); ++i) u.grp_chunk_off.push_back(h.grp_chunk_off[i] + chb);
+        for (int32_t code : h.grp_half) u.grp_half.push_back(((code >> 1) + gb) * 2 + (code & 1));
+        for (size_t i = 1; i < h.chk_blk_off.size(); ++i) u.chk_blk_off.push_back(h.chk_blk_off[i] + bb);
+        append(u.chk_nspec, h.chk_nspec);
+        for (size_t cc = 0; cc < h.chk_nspec.size(); ++cc) {   // spectra first, then Fourier multipoles
+            const int32_t b0 = h.chk_blk_off[cc], b1 = h.chk_blk_off[cc + 1];
+            for (int32_t b = b0; b < b1; ++b)
+                u.chk_blk.push_back(h.chk_blk[b] + (b - b0 < h.chk_nspec[cc] ? spb : hb));
+        }
+        append_off(u.chk_op_off, h.chk_op_off, ob);
+        append(u.chk_op, h.chk_op);
+        u.chk_max_blocks = std::max(u.chk_max_blocks, h.chk_max_blocks);
+        for (int v = 0; v < 3; ++v) u.chk_stage_blocks[v] = std::max(u.chk_stage_blocks[v], h.chk_stage_blocks[v]);
+        // upward / downward lists, by local level
+        for (size_t l = 0; l < h.m2m_lvl.size(); ++l) append_off(u.m2m_lvl[l], h.m2m_lvl[l], mb);
+        for (size_t l = 0; l < h.l2l_lvl.size(); ++l) {
+            const int32_t parb = (int32_t)u.l2l_par[l].size();
+            const auto& e = h.l2l_lvl[l];
+            for (size_t i = 0; i + 3 < e.size(); i += 4) {
+                u.l2l_lvl[l].push_back(e[i] + eb);
+                u.l2l_lvl[l].push_back(e[i + 1]);
+                u.l2l_lvl[l].push_back(e[i + 2] + parb);
+                u.l2l_lvl[l].push_back(e[i + 3]);
+            }
+            append_off(u.l2l_par[l], h.l2l_par[l], eb);
+        }
+        append_off(u.p2m_cells, h.p2m_cells, cb);
+        append_off(u.l2p_cells, h.l2p_cells, cb);
+        // near field
+        append_off(u.p2p_unit_leaf, h.p2p_unit_leaf, leb);
+        for (size_t i = 1; i < h.p2p_unit_off.size(); ++i) u.p2p_unit_off.push_back(h.p2p_unit_off[i] + rb);
+        append_off(u.p2p_sbeg, h.p2p_sbeg, (int32_t)pb);
+        append_off(u.p2p_send, h.p2p_send, (int32_t)pb);
+        append(u.p2p_soff, h.p2p_soff);
+        append_off(u.p2p_part, h.p2p_part, (int32_t)partb);
+        append_off(u.p2p_leaf, h.p2p_leaf, cb);
+        for (size_t i = 1; i < h.p2p_leaf_off.size(); ++i) u.p2p_leaf_off.push_back(h.p2p_leaf_off[i] + lub);
+        append_off(u.p2p_leaf_units, h.p2p_leaf_units, ub);
+        u.p2p_parts += h.p2p_parts;
+        u.p2p_interactions += h.p2p_interactions;
+        // per geometry
+        u.geo_kappa.push_back(h.kappa);
+        u.geo_eps.push_back(h.eps_self);
+        for (int a = 0; a < 3; ++a) u.geo_center.push_back(h.corner[a] + h.side / 2);
+        u.nx += h.nx;
+        u.ny += h.ny;
+        u.geo_point_off.push_back(u.nx);
+        u.geo_cell_off.push_back(u.tt.ncell());
+        u.geo_level_off.push_back(lb + std::max(nlev, 1));
+        u.tt.level_range.resize(std::max(u.tt.level_range.size(), (size_t)nlev));
+        u.d_aabb = std::max(u.d_aabb, h.d_aabb);
+        h = HostPlan();   // release the part
+    }
+}
+
+}  // namespace defmm

@@ -139,7 +139,26 @@ struct HostPlan {
 
     int64_t nM() const { return (int64_t)m_cell.size(); }
     int64_t nL() const { return (int64_t)l_cell.size(); }
+
+    // Union of several geometries (ngeo > 1, see union_host_plans): every table
+    // above is the concatenation of the geometries' own, indices offset; cell
+    // levels are global level ids (geometry g's level l is geo_level_off[g] + l)
+    // and the per-geometry quantities live here.  Empty for one geometry.
+    int ngeo = 1;
+    std::vector<int64_t> geo_point_off;     // ngeo + 1, points (sorted and caller order)
+    std::vector<int32_t> geo_cell_off;      // ngeo + 1, cells
+    std::vector<int32_t> geo_level_off;     // ngeo + 1, global level ids
+    std::vector<double> geo_kappa, geo_eps, geo_center;   // per geometry (center: 3 each)
+    std::vector<double> level_side_u;       // per global level
+    std::vector<double> cell_corner_u;      // 3 per cell
+    std::vector<int32_t> cell_geo;          // per cell
+    std::vector<double> spec_kappa;         // per spectrum
 };
+
+// Concatenates independently built plans (same order, DFT length, options;
+// sources = targets) into one: the application phase of the union runs every
+// phase as one launch over all geometries.  parts are consumed.
+void union_host_plans(std::vector<HostPlan>& parts, HostPlan& out);
 
 // Builds everything above from host coordinates (Y == nullptr: same tree).
 // Throws std::runtime_error with a message on invalid input.

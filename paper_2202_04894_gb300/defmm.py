@@ -25,7 +25,7 @@ EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_
             "defmm_profile_read", "defmm_apply_noalloc", "defmm_plan_set_tuning",
             "defmm_plan_get_tuning", "defmm_default_tune_options", "defmm_plan_autotune",
             "defmm_default_gmres_options", "defmm_gmres", "defmm_plan_set_shard", "defmm_plan_shard_range",
-            "defmm_last_error"]
+            "defmm_plan_create_union", "defmm_last_error"]
 PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 
 
@@ -134,6 +134,10 @@ def lib():
         L.defmm_plan_set_shard.restype = ctypes.c_int
         L.defmm_plan_shard_range.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.defmm_plan_shard_range.restype = ctypes.c_int
+        L.defmm_plan_create_union.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                              ctypes.POINTER(dbl), ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
+        L.defmm_plan_create_union.restype = ctypes.c_int
         L.defmm_last_error.argtypes = []
         L.defmm_last_error.restype = ctypes.c_char_p
         _LIB = L
@@ -355,3 +359,28 @@ def autotune(X, Y=None, kappa=1.0, order=4, nrhs=1, dtype=C64, leaf_range=(16, 6
     plan.nx = Xh.shape[0]
     plan.ny = Xh.shape[0] if Yh is None else Yh.shape[0]
     return plan, {name: getattr(r, name) for name, _ in TuneResult._fields_}
+
+
+def union_plan(geometries, kappas, order=4, leaf_size=64, stream=None, **options):
+    """defmm_plan_create_union: several geometries (sources = targets) in one plan.
+
+    q and p of an apply hold the geometries' points one after another.  Returns
+    a Plan whose nx = ny = the total point count.
+    """
+    pts = [Plan._points(X) for X in geometries]
+    n = len(pts)
+    opt = default_options(**options)
+    xs = (ctypes.c_void_p * n)(*[ctypes.c_void_p(P.data_ptr()) for P in pts])
+    ns = (ctypes.c_int64 * n)(*[P.shape[0] for P in pts])
+    ks = (ctypes.c_double * n)(*[float(k) for k in kappas])
+    if len(kappas) != n:
+        raise ValueError("one kappa per geometry")
+    h = ctypes.c_void_p()
+    _check(lib().defmm_plan_create_union(
+        n, ctypes.cast(xs, ctypes.POINTER(ctypes.c_void_p)), ns, ks, int(order), int(leaf_size),
+        ctypes.byref(opt), None if (opt.flags & PLAN_HOST_ONLY) else _stream_handle(stream), ctypes.byref(h)))
+    plan = Plan.__new__(Plan)
+    plan._h = h
+    plan._keep = None
+    plan.nx = plan.ny = int(sum(P.shape[0] for P in pts))
+    return plan

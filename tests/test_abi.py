@@ -234,3 +234,36 @@ def test_shard_ranges_partition_the_targets(kind, n, order):
     with pytest.raises(defmm.DefmmError) as e:
         pl.set_shard(2, 0)
     assert e.value.status == 5
+
+
+def test_union_plan_tables_are_the_concatenation():
+    """A union of three geometries: its host tables are each geometry's own, offset
+    (points, cells, global levels), and its counts are the sums."""
+    geos = [W.points("sphere", 1500, 111), W.points("box", 2200, 112) * 0.7, W.points("ellipsoid", 900, 113)]
+    kappas = [12.0, 30.0, 5.0]
+    singles = [_host_plan(X, kappa=k, order=4, leaf_size=24) for X, k in zip(geos, kappas)]
+    uni = defmm.union_plan(geos, kappas, order=4, leaf_size=24, flags=defmm.PLAN_HOST_ONLY)
+    assert uni.nx == sum(len(X) for X in geos)
+    perm, cells = uni.table("perm_t"), uni.table("cells_t").reshape(-1, 7)
+    m2l, p2p = uni.table("m2l").reshape(-1, 3), uni.table("p2p").reshape(-1, 2)
+    pb = cb = lb = mb = pp = 0
+    for X, sp in zip(geos, singles):
+        sperm, scells = sp.table("perm_t"), sp.table("cells_t").reshape(-1, 7)
+        assert np.array_equal(perm[pb:pb + len(X)], sperm + pb)
+        uc = cells[cb:cb + len(scells)]
+        assert np.array_equal(uc[:, 0], scells[:, 0] + lb)                       # global level ids
+        assert np.array_equal(uc[:, 1:4], scells[:, 1:4])
+        assert np.array_equal(uc[:, 4:6], scells[:, 4:6] + pb)
+        assert np.array_equal(uc[:, 6], np.where(scells[:, 6] >= 0, scells[:, 6] + cb, scells[:, 6]))
+        sm = sp.table("m2l").reshape(-1, 3)
+        assert np.array_equal(m2l[mb:mb + len(sm)], sm + np.array([cb, cb, 0]))
+        s2 = sp.table("p2p").reshape(-1, 2)
+        assert np.array_equal(p2p[pp:pp + len(s2)], s2 + cb)
+        pb += len(X); cb += len(scells); mb += len(sm); pp += len(s2)
+        lb += int(scells[:, 0].max()) + 1
+    iu = uni.info()
+    for key in ("n_m2l_pairs", "n_p2p_pairs", "n_multipole", "n_local", "n_fourier", "n_spectra", "p2p_interactions"):
+        assert iu[key] == sum(sp.info()[key] for sp in singles), key
+    with pytest.raises(defmm.DefmmError) as e:
+        defmm.union_plan(geos, [1.0, -2.0, 1.0], flags=defmm.PLAN_HOST_ONLY)
+    assert e.value.status == 1
