@@ -50,3 +50,21 @@ def test_union_with_damping_and_shards():
         ps = single.apply(q[off:off + len(X)].to(torch.complex64)).cpu().numpy()
         assert np.array_equal(whole[off:off + len(X)], ps)
         off += len(X)
+
+
+def test_union_in_a_captured_graph():
+    """A union plan in a graph batch: one captured CUDA graph replays the whole
+    multi-geometry apply (the fused launches), bit for bit the plain apply."""
+    from paper_2202_04894_gb300 import serve
+    geos, kappas = _geos()
+    uni = defmm.union_plan(geos, kappas, order=4, leaf_size=32)
+    q = np.concatenate([W.charges(len(X), 150 + i, nrhs=2) for i, X in enumerate(geos)])
+    qd = torch.from_numpy(q).to("cuda").to(torch.complex64)
+    direct = uni.apply(qd).cpu().numpy()
+    b = serve.Batch([uni], [2], torch.complex64)
+    b.inputs()[0].copy_(qd.t())
+    for _ in range(2):
+        b.run()
+        torch.cuda.synchronize()
+        assert np.array_equal(b.outputs()[0].t().cpu().numpy(), direct)
+    assert b.info()["kernel_launches"] > 0
