@@ -1,9 +1,9 @@
-// C ABI of the library (include/defmm.h): plan upload, workspace and calls.
+// C ABI of the library (include/defmm.h): plan creation (one geometry or a
+// union of several), upload, workspaces, applies, tuning and shards.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
-
 #include <cstdio>
 #include <cstring>
 #include <mutex>

@@ -1,7 +1,9 @@
 // Application-phase kernels of the directional equispaced FMM on sm_103a.
 //
 //   gather   q -> Morton order
-//   P2P      near field over the pairs of Alg. 1 (Sec. 2.2, Sec. 5.3)
+//   P2P      near field over the pairs of Alg. 1 (Sec. 2.2, Sec. 5.3); CUDA
+//            cores (1, 4, 8 or 16 columns per pass) or, opt-in for many
+//            columns, tcgen05 tensor cores (k_p2p_tc)
 //   P2M      S_a^u[c](y) = exp(i kappa <y_a - y, u>) S_a[c](y)   (Sec. 2.2)
 //   M2M      D0(v) (x)M^(p) D1(v), tensorised (Sec. 5.2.1, Eq. dlefturight)
 //   M2F      F chi: zero-pad + forward DFT (Sec. 4.1.1)
@@ -13,7 +15,10 @@
 //   scatter  p <- Morton order
 //
 // Every output is produced by exactly one thread block with a fixed
-// summation order (no atomics), so results are deterministic.
+// summation order (no atomics), so results are deterministic.  The kernels
+// take the plan's tables by value (DevCommon); a shard of the targets or a
+// union of several geometries only changes which entries they visit and where
+// a cell's wavenumber comes from.
 #include <cuda_runtime.h>
 
 #include <cstdint>
