@@ -29,6 +29,8 @@
 #include "symmetry.h"
 #include "tcgen05.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace defmm {
 
 __constant__ int kPermDev[6][3] = DEFMM_PERM_TABLE;
@@ -2078,9 +2080,17 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     int nl = 0;
     int phase = 0;
     cudaError_t err;
+    // phase boundaries: NVTX ranges for tracing tools (no-ops without one) and,
+    // when profiling, CUDA events on the apply's stream
+    static const char* const kPhaseName[kNumPhases] = {"defmm gather", "defmm p2p", "defmm p2m", "defmm m2m",
+                                                       "defmm m2f", "defmm m2l+f2l", "defmm l2l", "defmm l2p",
+                                                       "defmm scatter"};
     auto mark = [&]() -> cudaError_t {
+        if (phase > 0) nvtxRangePop();
+        if (phase < kNumPhases) nvtxRangePushA(kPhaseName[phase]);
+        const int k = phase++;
         if (!phase_events) return cudaSuccess;
-        return cudaEventRecord(phase_events[phase++], stream);
+        return cudaEventRecord(phase_events[k], stream);
     };
 #define DEFMM_MARK()                        \
     do {                                    \
