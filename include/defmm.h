@@ -367,6 +367,17 @@ defmm_status defmm_plan_table(defmm_plan plan, const char* name, int64_t* out,
 defmm_status defmm_profile_enable(defmm_plan plan, int enable);
 defmm_status defmm_profile_read(defmm_plan plan, double* ms, int capacity, int* nphase);
 
+/* Self-test of the failure path every pipelined kernel uses (no counterpart
+ * in the paper): one thread block waits on an mbarrier phase that nothing
+ * completes, polls at most `spins` times, raises a device flag and returns,
+ * as the M2L and tensor-core kernels do when a copy never lands (they then
+ * raise the plan's flag, read by defmm_plan_info().device_error and reported
+ * as DEFMM_ERR_TIMEOUT by defmm_apply_host).  Nothing faults or hangs and the
+ * context stays usable.  Returns DEFMM_ERR_TIMEOUT when the flag was raised
+ * (the expected outcome), DEFMM_OK otherwise.
+ * Errors: DEFMM_ERR_ARG (spins outside [1, 2^22]), DEFMM_ERR_CUDA.           */
+defmm_status defmm_selftest_bounded_wait(int spins, void* stream);
+
 const char* defmm_last_error(void);
 
 #ifdef __cplusplus

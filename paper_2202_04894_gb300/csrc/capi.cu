@@ -461,6 +461,20 @@ defmm_status build_shard(defmm_plan_s* pl, int nshards, int shard, cudaStream_t 
 
 extern "C" {
 
+defmm_status defmm_selftest_bounded_wait(int spins, void* stream) {
+    if (spins < 1 || spins > (1 << 22)) return fail(DEFMM_ERR_ARG, "spins must be in [1, 2^22]");
+    int* flag = nullptr;
+    cudaError_t e = cudaMalloc(&flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = launch_wait_probe(flag, spins, (cudaStream_t)stream);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(flag);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+    return h ? fail(DEFMM_ERR_TIMEOUT, "device-side wait gave up (expected: nothing completes the phase)") : DEFMM_OK;
+}
+
 defmm_status defmm_plan_shard_range(defmm_plan plan, int nshards, int shard, int64_t* first, int64_t* count) {
     if (!plan || !first || !count) return fail(DEFMM_ERR_ARG, "plan, first and count must not be NULL");
     if (nshards < 1 || shard < 0 || shard >= nshards) return fail(DEFMM_ERR_ARG, "need 0 <= shard < nshards");

@@ -772,10 +772,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 constexpr int kMaxSpin = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (int it = 0; it < kMaxSpin; ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int spins = kMaxSpin) {
+    for (int it = 0; it < spins; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// Self-test of the bounded wait: one block waits on an mbarrier phase that no
+// arrival completes, gives up after `spins` polls and raises *flag, exactly as
+// the pipelined kernels do when a copy never lands; nothing faults or hangs.
+__global__ void k_wait_probe(int* flag, int spins) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, spins);
+    if (!ok && threadIdx.x == 0) atomicExch(flag, 1);
 }
 
 constexpr int kM2LMaxStages = 3;  // ring depth (runtime S <= this)
@@ -2067,6 +2081,11 @@ cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T
         k_m2l<T, 4, 1024><<<(unsigned)c.n_grp, threads, sm, stream>>>(c, t, w.Mhat, w.L, w.R, S);
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_wait_probe(int* flag, int spins, cudaStream_t stream) {
+    k_wait_probe<<<1, 32, 0, stream>>>(flag, spins);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ orchestration

@@ -109,6 +109,9 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
 
 constexpr int kNumPhases = 9;  // gather p2p p2m m2m m2f m2l l2l l2p scatter
 
+// One block waiting, boundedly, on an mbarrier phase nothing completes; raises *flag.
+cudaError_t launch_wait_probe(int* flag, int spins, cudaStream_t stream);
+
 // Forms the canonical transfer spectra in float64 (Sec. 2.3 Eq. FourierDiagonal).
 cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
                            const double* level_side, int p, int N, int NFpad, double kappa,

@@ -25,7 +25,7 @@ EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_
             "defmm_profile_read", "defmm_apply_noalloc", "defmm_plan_set_tuning",
             "defmm_plan_get_tuning", "defmm_default_tune_options", "defmm_plan_autotune",
             "defmm_default_gmres_options", "defmm_gmres", "defmm_plan_set_shard", "defmm_plan_shard_range",
-            "defmm_plan_create_union", "defmm_last_error"]
+            "defmm_plan_create_union", "defmm_selftest_bounded_wait", "defmm_last_error"]
 PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 
 
@@ -138,6 +138,8 @@ def lib():
                                               ctypes.POINTER(dbl), ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
         L.defmm_plan_create_union.restype = ctypes.c_int
+        L.defmm_selftest_bounded_wait.argtypes = [ctypes.c_int, vp]
+        L.defmm_selftest_bounded_wait.restype = ctypes.c_int
         L.defmm_last_error.argtypes = []
         L.defmm_last_error.restype = ctypes.c_char_p
         _LIB = L
