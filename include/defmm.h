@@ -126,6 +126,24 @@ defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int
                                      int order, int leaf_size, const defmm_options* opt, void* stream,
                                      defmm_plan* out);
 
+/* Plan files.  defmm_plan_save writes the plan's host tables (octree,
+ * traversal lists, expansions, phase tables, schedules) and the coordinates it
+ * was built from to `path`; defmm_plan_load reads such a file and rebuilds the
+ * device tables (the transfer spectra are formed again on the GPU), skipping
+ * the tree construction, traversals and scheduling.  A loaded plan computes
+ * the same results as the saved one, bit for bit.  The format is this
+ * library's own (magic "DEFMMPLN", version 1, native byte order, a 64-bit
+ * FNV-1a checksum at the end); the paper has no counterpart.  Lengths are
+ * checked against the file size and the checksum against the contents, which
+ * catches damaged files; a plan file is otherwise trusted input (its tables
+ * are indexes the kernels follow), like the library itself.  opt: only flags (DEFMM_PLAN_HOST_ONLY) and hbm_budget
+ * apply at load, every other option is the saved plan's.  Tuning and shard
+ * settings are not saved.
+ * Errors: DEFMM_ERR_ARG (NULL arguments, unreadable, truncated or foreign
+ * file, unwritable path), DEFMM_ERR_OOM, DEFMM_ERR_CUDA.                    */
+defmm_status defmm_plan_save(defmm_plan plan, const char* path);
+defmm_status defmm_plan_load(const char* path, const defmm_options* opt, void* stream, defmm_plan* out);
+
 /* One application phase (Sec. 2.2 operators with M2F/F2L of Sec. 4.1.1):
  * P2M -> M2M -> M2F -> Hadamard M2L with permuted spectra -> F2L -> L2L -> L2P,
  * plus P2P over the near pairs of Alg. 1.

@@ -22,6 +22,7 @@ CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I" + INCLUDE]
 
 SOURCES = [
     ("plan.cpp", "g++"),
+    ("persist.cpp", "g++"),
     ("kernels.cu", "nvcc"),
     ("capi.cu", "nvcc"),
     ("noalloc.cu", "nvcc"),

@@ -580,6 +580,8 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
         delete pl;
         return s;
     }
+    pl->X = std::move(hx);
+    pl->Y = std::move(hy);
     *out = pl;
     return DEFMM_OK;
 }
@@ -632,6 +634,54 @@ defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int
     }
     pl->host_only = host_only;
     defmm_status s = host_only ? DEFMM_OK : upload(pl, all, all, (cudaStream_t)stream);
+    if (s != DEFMM_OK) {
+        cudaFree(pl->arena);
+        delete pl;
+        return s;
+    }
+    pl->X = std::move(all);
+    *out = pl;
+    return DEFMM_OK;
+}
+
+defmm_status defmm_plan_save(defmm_plan plan, const char* path) {
+    if (!plan || !path) return fail(DEFMM_ERR_ARG, "plan and path must not be NULL");
+    try {
+        save_plan_file(path, plan->hp, plan->X, plan->Y);
+    } catch (const std::exception& ex) {
+        return fail(DEFMM_ERR_ARG, ex.what());
+    }
+    return DEFMM_OK;
+}
+
+defmm_status defmm_plan_load(const char* path, const defmm_options* opt, void* stream, defmm_plan* out) {
+    if (!out || !path) return fail(DEFMM_ERR_ARG, "path and out must not be NULL");
+    *out = nullptr;
+    defmm_options o;
+    defmm_default_options(&o);
+    if (opt) o = *opt;
+    const bool host_only = (o.flags & DEFMM_PLAN_HOST_ONLY) != 0;
+    if (!host_only) {
+        std::call_once(g_config_once, [] {
+            g_config_err = configure_kernels<float>();
+            if (g_config_err == cudaSuccess) g_config_err = configure_kernels<double>();
+        });
+        if (g_config_err != cudaSuccess) return cuda_fail(g_config_err, "kernel configuration");
+    }
+    defmm_plan_s* pl = new (std::nothrow) defmm_plan_s;
+    if (!pl) return fail(DEFMM_ERR_OOM, "host allocation");
+    pl->hbm_budget = o.hbm_budget;
+    try {
+        load_plan_file(path, pl->hp, pl->X, pl->Y);
+    } catch (const std::bad_alloc&) {
+        delete pl;
+        return fail(DEFMM_ERR_OOM, "host allocation while reading the plan file");
+    } catch (const std::exception& ex) {
+        delete pl;
+        return fail(DEFMM_ERR_ARG, ex.what());
+    }
+    pl->host_only = host_only;
+    defmm_status s = host_only ? DEFMM_OK : upload(pl, pl->X, pl->hp.same ? pl->X : pl->Y, (cudaStream_t)stream);
     if (s != DEFMM_OK) {
         cudaFree(pl->arena);
         delete pl;

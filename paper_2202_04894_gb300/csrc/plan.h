@@ -160,6 +160,12 @@ struct HostPlan {
 // phase as one launch over all geometries.  parts are consumed.
 void union_host_plans(std::vector<HostPlan>& parts, HostPlan& out);
 
+// Plan files (persist.cpp): the host plan and the coordinates it was built
+// from (caller order; Y empty when sources = targets).  Throw on failure.
+void save_plan_file(const std::string& path, const HostPlan& hp, const std::vector<double>& X,
+                    const std::vector<double>& Y);
+void load_plan_file(const std::string& path, HostPlan& hp, std::vector<double>& X, std::vector<double>& Y);
+
 // Builds everything above from host coordinates (Y == nullptr: same tree).
 // Throws std::runtime_error with a message on invalid input.
 void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa,

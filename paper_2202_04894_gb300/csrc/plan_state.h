@@ -49,6 +49,7 @@ struct defmm_plan_s {
     bool profiled = false;
     cudaEvent_t events[defmm::kNumPhases + 1] = {};
     std::mutex busy;
+    std::vector<double> X, Y;   // the coordinates the plan was built from (caller order; for plan files)
     // the shard this plan's defmm_apply computes (nshards == 1: the whole operator)
     struct Shard {
         int nshards = 1, shard = 0;

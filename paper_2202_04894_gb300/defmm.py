@@ -25,7 +25,8 @@ EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_
             "defmm_profile_read", "defmm_apply_noalloc", "defmm_plan_set_tuning",
             "defmm_plan_get_tuning", "defmm_default_tune_options", "defmm_plan_autotune",
             "defmm_default_gmres_options", "defmm_gmres", "defmm_plan_set_shard", "defmm_plan_shard_range",
-            "defmm_plan_create_union", "defmm_selftest_bounded_wait", "defmm_last_error"]
+            "defmm_plan_create_union", "defmm_selftest_bounded_wait", "defmm_plan_save", "defmm_plan_load",
+            "defmm_last_error"]
 PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
 
 
@@ -140,6 +141,10 @@ def lib():
         L.defmm_plan_create_union.restype = ctypes.c_int
         L.defmm_selftest_bounded_wait.argtypes = [ctypes.c_int, vp]
         L.defmm_selftest_bounded_wait.restype = ctypes.c_int
+        L.defmm_plan_save.argtypes = [vp, ctypes.c_char_p]
+        L.defmm_plan_save.restype = ctypes.c_int
+        L.defmm_plan_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
+        L.defmm_plan_load.restype = ctypes.c_int
         L.defmm_last_error.argtypes = []
         L.defmm_last_error.restype = ctypes.c_char_p
         _LIB = L
@@ -277,6 +282,24 @@ class Plan:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().defmm_plan_shard_range(self._h, int(nshards), int(shard), ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def save(self, path):
+        """defmm_plan_save: the plan's host tables and coordinates to a file."""
+        _check(lib().defmm_plan_save(self._h, os.fsencode(path)))
+
+    @staticmethod
+    def load(path, stream=None, **options):
+        """defmm_plan_load: a plan from a file written by save()."""
+        opt = default_options(**options)
+        h = ctypes.c_void_p()
+        _check(lib().defmm_plan_load(os.fsencode(path), ctypes.byref(opt),
+                                     None if (opt.flags & PLAN_HOST_ONLY) else _stream_handle(stream), ctypes.byref(h)))
+        plan = Plan.__new__(Plan)
+        plan._h = h
+        plan._keep = None
+        info = plan.info()
+        plan.nx, plan.ny = int(info["nx"]), int(info["ny"])
+        return plan
 
     def table(self, name: str) -> np.ndarray:
         n = ctypes.c_int64()

@@ -267,3 +267,48 @@ def test_union_plan_tables_are_the_concatenation():
     with pytest.raises(defmm.DefmmError) as e:
         defmm.union_plan(geos, [1.0, -2.0, 1.0], flags=defmm.PLAN_HOST_ONLY)
     assert e.value.status == 1
+
+
+def test_plan_file_round_trip(tmp_path):
+    """A plan written by save() and read by load() has the same tables and counts;
+    truncated, foreign and missing files are argument errors."""
+    X = W.points("sphere", 1800, 121)
+    Y = W.points("box", 1300, 122) * 0.8
+    for src in (None, Y):
+        pl = _host_plan(X, src, kappa=9.0, order=5, leaf_size=20, damping=0.25)
+        path = tmp_path / ("same.plan" if src is None else "xy.plan")
+        pl.save(path)
+        back = defmm.Plan.load(path, flags=defmm.PLAN_HOST_ONLY)
+        a, b = pl.info(), back.info()
+        for key in a:
+            if key not in ("plan_bytes", "workspace_bytes"):
+                assert a[key] == b[key], key
+        for name in ("perm_t", "perm_s", "cells_t", "cells_s", "m2l", "p2p", "mult", "local"):
+            assert np.array_equal(pl.table(name), back.table(name)), name
+    geos = [W.points("sphere", 700, 123), W.points("ellipsoid", 500, 124)]
+    uni = defmm.union_plan(geos, [4.0, 7.0], order=4, leaf_size=24, flags=defmm.PLAN_HOST_ONLY)
+    uni.save(tmp_path / "u.plan")
+    ub = defmm.Plan.load(tmp_path / "u.plan", flags=defmm.PLAN_HOST_ONLY)
+    assert ub.nx == ub.ny == 1200
+    for name in ("perm_t", "cells_t", "m2l", "p2p"):
+        assert np.array_equal(uni.table(name), ub.table(name)), name
+    raw = (tmp_path / "xy.plan").read_bytes()
+    flipped = bytearray(raw)
+    flipped[len(raw) // 3] ^= 0x10
+    huge = bytearray(raw)
+    ylen = len(raw) - 8 - 3 * len(Y) * 8 - 8            # Y's length field, before Y and the checksum
+    assert int.from_bytes(raw[ylen:ylen + 8], "little") == 3 * len(Y)
+    huge[ylen:ylen + 8] = (1 << 62).to_bytes(8, "little")
+    for bad, content in (("short.plan", raw[: len(raw) // 2]), ("foreign.plan", b"NOTAPLAN" + raw[8:]),
+                         ("empty.plan", b""), ("flipped.plan", bytes(flipped)), ("huge.plan", bytes(huge)),
+                         ("long.plan", raw + b"\0")):
+        (tmp_path / bad).write_bytes(content)
+        with pytest.raises(defmm.DefmmError) as e:
+            defmm.Plan.load(tmp_path / bad, flags=defmm.PLAN_HOST_ONLY)
+        assert e.value.status == 1
+    with pytest.raises(defmm.DefmmError) as e:
+        defmm.Plan.load(tmp_path / "missing.plan", flags=defmm.PLAN_HOST_ONLY)
+    assert e.value.status == 1
+    with pytest.raises(defmm.DefmmError) as e:
+        pl.save(tmp_path / "no_such_dir" / "x.plan")
+    assert e.value.status == 1
