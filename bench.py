@@ -57,16 +57,21 @@ SAMPLE_N = 16000          # cpu_baseline: ~10-20 s of single-core oracle work
 ORACLE_S_PER_POINT = 6e-4  # measured oracle cost on this recipe, used to size samples
 
 
-M2L_BEGIN = "// The same group schedule with rows of samples"
-M2L_END = "// Ring depth S and the dynamic shared memory of the per-sample M2L kernel"
+# the row M2L kernel and its launch (which blocks serve which groups)
+M2L_REGIONS = [("// The same group schedule with rows of samples",
+                "// Ring depth S and the dynamic shared memory of the per-sample M2L kernel"),
+               ("// The Hadamard M2L + F2L of one apply", "cudaError_t launch_wait_probe")]
 
 
 def m2l_rows_source_sha():
-    """sha256 (first 16 hex) of the row M2L kernel's source text in kernels.cu."""
+    """sha256 (first 16 hex) of the row M2L kernel's and its launch's source text in kernels.cu."""
     import hashlib
     src = open(os.path.join(ROOT, "paper_2202_04894_gb300", "csrc", "kernels.cu")).read()
-    a, b = src.index(M2L_BEGIN), src.index(M2L_END)
-    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for begin, end in M2L_REGIONS:
+        a = src.index(begin)
+        h.update(src[a:src.index(end, a)].encode())
+    return h.hexdigest()[:16]
 
 
 def _recorded_traffic_per_pair():

@@ -201,16 +201,22 @@ defmm_status defmm_apply_noalloc(defmm_plan plan, const void* q, void* p, int nr
  *                   the measured workloads; defmm_plan_autotune times both.
  *                   The two kernels round differently (both within
  *                   single-precision accuracy of the same sum).
- *  m2l_members_per_block - sibling targets per M2L thread block, 4 or 8
- *                   (0 = the library's choice: 4 for N = 9 with one column per
- *                   pass, else 8).  With 4, groups of more siblings take two
- *                   blocks, each staging the group's chunks; smaller blocks fit
- *                   more per SM.  Kernels without a 4-member variant use 8.
+ *  m2l_members_per_block - sibling targets per M2L thread block: 4, 8, or by
+ *                   group size, 12 or 14 (0 = the library's choice: 12 for
+ *                   N = 7 with one column per pass, 4 for N = 9 with one
+ *                   column per pass, else 8).  With 4, groups of more siblings
+ *                   take two blocks, each staging the group's chunks; smaller
+ *                   blocks fit more per SM.  With 12 (order 4, N = 7, one
+ *                   column per pass) groups of more than 4 siblings run in
+ *                   blocks of 8 and the others whole in blocks of 4, two
+ *                   launches, so few member warps idle; 14 adds blocks of 6
+ *                   for groups of 5 or 6 (three launches).  Elsewhere 12 and 14
+ *                   act as 4.  Kernels without a 4-member variant use 8.
  *                   No output depends on it (bit for bit).
  * The setting applies to applies enqueued after the call; CUDA graphs
  * captured earlier keep the value they were captured with.
  * Errors: DEFMM_ERR_ARG (NULL plan or tuning, m2l_rhs_block not in
- * {0, 1, 2, 4}, p2p_tc_min_rhs < 0, m2l_members_per_block not in {0, 4, 8}). */
+ * {0, 1, 2, 4}, p2p_tc_min_rhs < 0, m2l_members_per_block not in {0, 4, 8, 12, 14}). */
 typedef struct {
     int m2l_rhs_block;
     int p2p_tc_min_rhs;
@@ -230,7 +236,7 @@ defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning);
  *  - right-hand sides per M2L pass (1, 2, 4) when nrhs > 1 and complex64,
  *  - the tensor-core near field on or off when nrhs >= 8 and complex64
  *    (defmm_tuning.p2p_tc_min_rhs),
- *  - 8 or 4 sibling targets per M2L block for complex64
+ *  - 8, 4 or by-group-size sibling targets per M2L block for complex64
  *    (defmm_tuning.m2l_members_per_block).
  * A smaller Ncrit changes the tree and so the approximation (within the
  * order's accuracy); the tensor-core near field changes rounding only; the
@@ -263,7 +269,7 @@ typedef struct {
 typedef struct {
     int leaf_size, fft_n, m2l_rhs_block; /* the choice (fft_n 0: 2p-1) */
     int p2p_tensor_cores;                /* 1: tensor-core near field chosen */
-    int m2l_members_per_block;           /* 8, 4 (0 for complex128: the default) */
+    int m2l_members_per_block;           /* 8, 4, 12, 14 (0 for complex128: the default) */
     double ms;                           /* its median apply time when timed */
     int candidates;                      /* configurations timed (0 from the cache) */
     int from_cache;                      /* 1 if the choice came from cache_path */
@@ -369,7 +375,16 @@ defmm_status defmm_plan_info(defmm_plan plan, defmm_info* out);
  *       "cells_t", "cells_s" (per cell: level, ix, iy, iz, begin, end, parent),
  *       "m2l" (per pair: target cell, source cell, best direction or -1),
  *       "p2p" (per pair: target cell, source cell),
- *       "mult", "local" (per effective expansion: cell, direction or -1).
+ *       "mult", "local" (per effective expansion: cell, direction or -1),
+ *       "m2f_list" (Fourier-multipole slot -> multipole expansion id),
+ *       "spectra" (per canonical spectrum: level, kbar x, y, z),
+ *       the M2L schedule: "grp_member_off", "grp_members" (CSR: group ->
+ *       local expansion ids), "grp_chunk_off" (CSR: group -> chunks),
+ *       "chk_blk_off", "chk_nspec", "chk_blk" (CSR: chunk -> staged blocks,
+ *       its first chk_nspec are spectrum ids, the rest Fourier-multipole
+ *       slots), "chk_op_off" (9 per chunk: op ranges of members 0..7, end),
+ *       "chk_op" (spectrum block | multipole block << 8 | symmetry code << 16;
+ *       code bit a negates axis a, code >> 3 names the axis permutation).
  * Copies min(count, capacity) int64 values to out (host) and sets *count to
  * the full length.  out may be NULL to query the length.                    */
 defmm_status defmm_plan_table(defmm_plan plan, const char* name, int64_t* out,

@@ -204,6 +204,15 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     size_t o_m2f = b.add(hp.m2f_list);
     size_t o_gmo = b.add(hp.grp_member_off), o_gm = b.add(hp.grp_members), o_gco = b.add(hp.grp_chunk_off);
     size_t o_ghf = b.add(hp.grp_half);
+    std::vector<int32_t> gbig, gsmall, gmid, glarge;   // the splits by group size
+    for (size_t g = 0; g + 1 < hp.grp_member_off.size(); ++g) {
+        const int nm = hp.grp_member_off[g + 1] - hp.grp_member_off[g];
+        if (nm > 4) gbig.push_back((int32_t)g);
+        else gsmall.push_back((int32_t)(2 * g));
+        if (nm > 6) glarge.push_back((int32_t)g);
+        else if (nm > 4) gmid.push_back((int32_t)g);
+    }
+    size_t o_gbig = b.add(gbig), o_gsmall = b.add(gsmall), o_gmid = b.add(gmid), o_glarge = b.add(glarge);
     size_t o_cbo = b.add(hp.chk_blk_off), o_cns = b.add(hp.chk_nspec), o_cb = b.add(hp.chk_blk);
     size_t o_coo = b.add(hp.chk_op_off), o_co = b.add(hp.chk_op);
     size_t o_p2m = b.add(hp.p2m_cells), o_l2p = b.add(hp.l2p_cells);
@@ -264,6 +273,10 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.grp_chunk_off = (const int32_t*)P(o_gco);
     c.n_grp = (int64_t)hp.grp_member_off.size() - 1;
     c.grp_half = (const int32_t*)P(o_ghf); c.n_grp_half = (int64_t)hp.grp_half.size();
+    c.grp_big = (const int32_t*)P(o_gbig); c.n_grp_big = (int64_t)gbig.size();
+    c.grp_small = (const int32_t*)P(o_gsmall); c.n_grp_small = (int64_t)gsmall.size();
+    c.grp_mid = (const int32_t*)P(o_gmid); c.n_grp_mid = (int64_t)gmid.size();
+    c.grp_large = (const int32_t*)P(o_glarge); c.n_grp_large = (int64_t)glarge.size();
     c.chk_blk_off = (const int32_t*)P(o_cbo); c.chk_nspec = (const int32_t*)P(o_cns); c.chk_blk = (const int32_t*)P(o_cb);
     c.chk_op_off = (const int32_t*)P(o_coo); c.chk_op = (const int32_t*)P(o_co);
     c.chk_max_blocks = hp.chk_max_blocks;
@@ -328,6 +341,10 @@ template <typename T> defmm_status apply_impl(defmm_plan_s* pl, Workspace<T>& w,
         c.sh_on = 1;
         c.sh_grp = h.grp; c.n_grp = h.n_grp;
         c.grp_half = h.half; c.n_grp_half = h.n_half;
+        c.grp_big = h.big; c.n_grp_big = h.n_big;
+        c.grp_small = h.small; c.n_grp_small = h.n_small;
+        c.grp_mid = h.mid; c.n_grp_mid = h.n_mid;
+        c.grp_large = h.large; c.n_grp_large = h.n_large;
         c.sh_unit = h.unit; c.n_p2p_units = h.n_unit;
         c.sh_leaf = h.leaf; c.n_p2p_leaf = h.n_leaf;
         c.l2p_cells = h.l2p; c.n_l2p = h.n_l2p;
@@ -402,11 +419,19 @@ defmm_status build_shard(defmm_plan_s* pl, int nshards, int shard, cudaStream_t 
     shard_range(hp, nshards, shard, &h.t0, &h.t1);
     const Tree& tt = hp.tt;
     auto needed = [&](int32_t c) { return tt.begin[c] < h.t1 && tt.end[c] > h.t0; };
-    std::vector<int32_t> grp, half, unit, leaf, l2p;
+    std::vector<int32_t> grp, half, unit, leaf, l2p, big, small, mid, large;
     const size_t ngrp = hp.grp_member_off.size() - 1;
     for (size_t g = 0; g < ngrp; ++g)
         for (int32_t m = hp.grp_member_off[g]; m < hp.grp_member_off[g + 1]; ++m)
-            if (needed(hp.l_cell[hp.grp_members[m]])) { grp.push_back((int32_t)g); break; }
+            if (needed(hp.l_cell[hp.grp_members[m]])) {
+                grp.push_back((int32_t)g);
+                const int nm = hp.grp_member_off[g + 1] - hp.grp_member_off[g];
+                if (nm > 4) big.push_back((int32_t)g);
+                else small.push_back((int32_t)(2 * g));
+                if (nm > 6) large.push_back((int32_t)g);
+                else if (nm > 4) mid.push_back((int32_t)g);
+                break;
+            }
     for (int32_t code : hp.grp_half) {
         const int32_t g = code >> 1, b = hp.grp_member_off[g] + 4 * (code & 1);
         const int32_t e = std::min(b + 4, hp.grp_member_off[g + 1]);
@@ -425,7 +450,7 @@ defmm_status build_shard(defmm_plan_s* pl, int nshards, int shard, cudaStream_t 
             if (needed(hp.l_cell[hp.l2l_lvl[l][i]]))
                 l2l[l].insert(l2l[l].end(), hp.l2l_lvl[l].begin() + i, hp.l2l_lvl[l].begin() + i + 4);
     // one device allocation, 256-byte aligned pieces
-    std::vector<const std::vector<int32_t>*> parts = {&grp, &half, &unit, &leaf, &l2p};
+    std::vector<const std::vector<int32_t>*> parts = {&grp, &half, &unit, &leaf, &l2p, &big, &small, &mid, &large};
     for (auto& v : l2l) parts.push_back(&v);
     std::vector<size_t> off;
     size_t total = 0;
@@ -452,8 +477,12 @@ defmm_status build_shard(defmm_plan_s* pl, int nshards, int shard, cudaStream_t 
     h.unit = at(2); h.n_unit = (int64_t)unit.size();
     h.leaf = at(3); h.n_leaf = (int64_t)leaf.size();
     h.l2p = at(4); h.n_l2p = (int64_t)l2p.size();
+    h.big = at(5); h.n_big = (int64_t)big.size();
+    h.small = at(6); h.n_small = (int64_t)small.size();
+    h.mid = at(7); h.n_mid = (int64_t)mid.size();
+    h.large = at(8); h.n_large = (int64_t)large.size();
     h.l2l.resize(l2l.size());
-    for (size_t l = 0; l < l2l.size(); ++l) h.l2l[l] = {at(5 + l), (int64_t)l2l[l].size() / 4};
+    for (size_t l = 0; l < l2l.size(); ++l) h.l2l[l] = {at(9 + l), (int64_t)l2l[l].size() / 4};
     return DEFMM_OK;
 }
 
@@ -518,7 +547,8 @@ defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning) 
     if (rb != 0 && rb != 1 && rb != 2 && rb != 4) return fail(DEFMM_ERR_ARG, "m2l_rhs_block must be 0, 1, 2 or 4");
     if (tuning->p2p_tc_min_rhs < 0) return fail(DEFMM_ERR_ARG, "p2p_tc_min_rhs must be >= 0");
     const int mb = tuning->m2l_members_per_block;
-    if (mb != 0 && mb != 4 && mb != 8) return fail(DEFMM_ERR_ARG, "m2l_members_per_block must be 0, 4 or 8");
+    if (mb != 0 && mb != 4 && mb != 8 && mb != 12 && mb != 14)
+        return fail(DEFMM_ERR_ARG, "m2l_members_per_block must be 0, 4, 8, 12 or 14");
     std::lock_guard<std::mutex> g(plan->busy);
     plan->common.m2l_rb = rb;
     plan->common.p2p_tc_min_rhs = tuning->p2p_tc_min_rhs;
@@ -822,6 +852,18 @@ defmm_status defmm_plan_table(defmm_plan plan, const char* name, int64_t* out, i
     else if (n == "p2p") for (auto& r : hp.p2p) v.insert(v.end(), {r[0], r[1]});
     else if (n == "mult") for (size_t e = 0; e < hp.m_cell.size(); ++e) v.insert(v.end(), {hp.m_cell[e], hp.m_dir[e]});
     else if (n == "local") for (size_t e = 0; e < hp.l_cell.size(); ++e) v.insert(v.end(), {hp.l_cell[e], hp.l_dir[e]});
+    else if (n == "m2f_list") v.assign(hp.m2f_list.begin(), hp.m2f_list.end());
+    else if (n == "spectra")
+        for (size_t e = 0; e < hp.spec_level.size(); ++e)
+            v.insert(v.end(), {hp.spec_level[e], hp.spec_kbar[e][0], hp.spec_kbar[e][1], hp.spec_kbar[e][2]});
+    else if (n == "grp_member_off") v.assign(hp.grp_member_off.begin(), hp.grp_member_off.end());
+    else if (n == "grp_members") v.assign(hp.grp_members.begin(), hp.grp_members.end());
+    else if (n == "grp_chunk_off") v.assign(hp.grp_chunk_off.begin(), hp.grp_chunk_off.end());
+    else if (n == "chk_blk_off") v.assign(hp.chk_blk_off.begin(), hp.chk_blk_off.end());
+    else if (n == "chk_nspec") v.assign(hp.chk_nspec.begin(), hp.chk_nspec.end());
+    else if (n == "chk_blk") v.assign(hp.chk_blk.begin(), hp.chk_blk.end());
+    else if (n == "chk_op_off") v.assign(hp.chk_op_off.begin(), hp.chk_op_off.end());
+    else if (n == "chk_op") v.assign(hp.chk_op.begin(), hp.chk_op.end());
     else return fail(DEFMM_ERR_ARG, "unknown table " + n);
     *count = (int64_t)v.size();
     if (out) std::memcpy(out, v.data(), sizeof(int64_t) * std::min<int64_t>(capacity, (int64_t)v.size()));

@@ -2023,15 +2023,50 @@ __host__ void rows_launch(const DevCommon& c, const DevTyped<T>& t, const DevWor
 // samples; N <= 8: 64 threads per member, N = 9: 96, N = 10..12: 64 threads
 // with two rows each), the per-sample kernel beyond.
 template <typename T>
-cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w, cudaStream_t stream) {
+cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T>& w, cudaStream_t stream,
+                       int* nlaunch) {
     constexpr bool F = sizeof(T) == 4;
     const int N = c.N, p = c.p;
     bool fits = false;
+    *nlaunch = 1;
     if (N <= 8) {
         if constexpr (F) {
             const int rb = m2l_pick_rb(c, w.R);
             if (p == 4 && N == 7) {
-                if (rb == 1 && c.m2l_members == 4) rows_launch<T, 8, 64, 1, 1, 4, 4, 7, 4>(c, t, w, stream, &fits);
+                if (rb == 1 && (c.m2l_members == 0 || c.m2l_members == 12 || c.m2l_members == 14)) {
+                    // by group size (the default): groups of more than 4 siblings in
+                    // blocks of 8 (14: 5-6 siblings in blocks of 6, 7-8 in blocks of 8),
+                    // the others whole in blocks of 4, so few member warps idle
+                    bool fb = true, fs = true;
+                    *nlaunch = 0;
+                    if (c.m2l_members != 14 && c.n_grp_big > 0) {
+                        DevCommon cb = c;
+                        cb.sh_grp = c.grp_big; cb.n_grp = c.n_grp_big;
+                        rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(cb, t, w, stream, &fb);
+                        ++*nlaunch;
+                    }
+                    if (c.m2l_members == 14 && c.n_grp_large > 0) {
+                        DevCommon cb = c;
+                        cb.sh_grp = c.grp_large; cb.n_grp = c.n_grp_large;
+                        rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(cb, t, w, stream, &fb);
+                        ++*nlaunch;
+                    }
+                    if (c.m2l_members == 14 && fb && c.n_grp_mid > 0) {
+                        DevCommon cb = c;
+                        cb.sh_grp = c.grp_mid; cb.n_grp = c.n_grp_mid;
+                        rows_launch<T, 8, 64, 1, 1, 4, 4, 7, 6>(cb, t, w, stream, &fb);
+                        ++*nlaunch;
+                    }
+                    if (fb && c.n_grp_small > 0) {
+                        DevCommon cs = c;
+                        cs.grp_half = c.grp_small; cs.n_grp_half = c.n_grp_small;
+                        rows_launch<T, 8, 64, 1, 1, 4, 4, 7, 4>(cs, t, w, stream, &fs);
+                        ++*nlaunch;
+                    }
+                    fits = fb && fs;
+                    if (!fits) *nlaunch = 1;   // nothing launched: the fallback below runs alone
+                }
+                else if (rb == 1 && c.m2l_members == 4) rows_launch<T, 8, 64, 1, 1, 4, 4, 7, 4>(c, t, w, stream, &fits);
                 else if (rb == 1) rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(c, t, w, stream, &fits);
                 else if (rb == 2) rows_launch<T, 8, 64, 1, 2, 2, 4, 7>(c, t, w, stream, &fits);
                 else rows_launch<T, 8, 64, 1, 4, 1, 4, 7>(c, t, w, stream, &fits);
@@ -2220,8 +2255,10 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     err = cudaMemsetAsync(w.L, 0, (size_t)w.nL * R * c.P3 * sizeof(C), stream);
     if (err != cudaSuccess) return err;
     if (c.n_grp > 0) {
-        err = launch_m2l<T>(c, t, w, stream);
+        int k = 1;
+        err = launch_m2l<T>(c, t, w, stream, &k);
         if (err != cudaSuccess) return err;
+        nl += k - 1;
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
@@ -2290,6 +2327,7 @@ cudaError_t configure_kernels() {
         if ((e = rows_config<T, 8, 64, 1, 4, 1, 0, 0>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 9, 96, 1, 2, 1, 5, 9>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 8, 64, 1, 1, 4, 4, 7, 4>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 1, 4, 4, 7, 6>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 9, 96, 1, 2, 2, 5, 9, 4>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 9, 96, 1, 1, 2, 5, 9, 4>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 12, 64, 2, 1, 2, 6, 11, 4>()) != cudaSuccess) return e;

@@ -56,7 +56,8 @@ struct defmm_plan_s {
         int64_t t0 = 0, t1 = 0;                    // sorted targets written
         unsigned char* arena = nullptr;            // device copies of the lists below
         const int32_t *grp = nullptr, *half = nullptr, *unit = nullptr, *leaf = nullptr, *l2p = nullptr;
-        int64_t n_grp = 0, n_half = 0, n_unit = 0, n_leaf = 0, n_l2p = 0;
+        const int32_t *big = nullptr, *small = nullptr, *mid = nullptr, *large = nullptr;
+        int64_t n_grp = 0, n_half = 0, n_unit = 0, n_leaf = 0, n_l2p = 0, n_big = 0, n_small = 0, n_mid = 0, n_large = 0;
         std::vector<defmm::LevelList> l2l;
     } sh;
 };

@@ -69,7 +69,7 @@ bool cache_lookup(const char* path, uint64_t key, Choice* c) {
         if (std::sscanf(line, "defmm-tune %" SCNx64 " %d %d %d %d %d %lf", &k, &v.leaf, &v.fft_n, &v.rb, &v.tc, &v.mem,
                         &v.ms) == 7 &&
             k == key && v.leaf >= 1 && v.fft_n >= 0 && (v.rb == 0 || v.rb == 1 || v.rb == 2 || v.rb == 4) &&
-            (v.tc == 0 || v.tc == 1) && (v.mem == 0 || v.mem == 4 || v.mem == 8)) {
+            (v.tc == 0 || v.tc == 1) && (v.mem == 0 || v.mem == 4 || v.mem == 8 || v.mem == 12 || v.mem == 14)) {
             *c = v;   // the last matching line wins
             found = true;
         }
@@ -198,7 +198,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
     std::vector<int> tcs = {0};
     if (t.nrhs >= 8 && t.dtype == DEFMM_C64) tcs = {0, 1};
     std::vector<int> mems = {0};
-    if (t.dtype == DEFMM_C64) mems = {8, 4};
+    if (t.dtype == DEFMM_C64) mems = {12, 8, 4, 14};
     struct Launch { int tc, mem, rb; };   // apply-time choices timed on every candidate plan
     std::vector<Launch> launches;
     for (int tc : tcs)

@@ -98,7 +98,10 @@ def test_tuning_values():
         pl.set_tuning(m2l_rhs_block=v, p2p_tc_min_rhs=v, m2l_members_per_block=v if v in (0, 4) else 8)
         assert pl.tuning() == {"m2l_rhs_block": v, "p2p_tc_min_rhs": v,
                                "m2l_members_per_block": v if v in (0, 4) else 8}
-    for v in (2, 6, -4):
+    for v in (12, 14):
+        pl.set_tuning(m2l_members_per_block=v)
+        assert pl.tuning()["m2l_members_per_block"] == v
+    for v in (2, 6, -4, 16):
         with pytest.raises(defmm.DefmmError) as e:
             pl.set_tuning(m2l_members_per_block=v)
         assert e.value.status == 1
@@ -312,3 +315,45 @@ def test_plan_file_round_trip(tmp_path):
     with pytest.raises(defmm.DefmmError) as e:
         pl.save(tmp_path / "no_such_dir" / "x.plan")
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("kind,n,kd,order", [("sphere", 4000, 40.0, 4), ("box", 4000, 8.0, 5), ("ellipsoid", 3000, 0.0, 4)])
+def test_m2l_schedule_covers_every_pair_once(kind, n, kd, order):
+    """The M2L work schedule (groups of sibling targets, chunks of staged blocks, pair
+    ops) names every M2L pair of the traversal exactly once: the op's member is the
+    pair's target expansion, its staged multipole the source's expansion in the same
+    direction, and its staged spectrum the canonical one of the same level whose
+    offset is the pair's offset t - s under the op's symmetry (Sec. 4.3)."""
+    X = W.points(kind, n, 131)
+    D = float(np.max(X.max(0) - X.min(0)))
+    pl = _host_plan(X, kappa=kd / D, order=order, leaf_size=24)
+    t = {k: pl.table(k) for k in ("m2l", "mult", "local", "m2f_list", "spectra", "grp_member_off", "grp_members",
+                                  "grp_chunk_off", "chk_blk_off", "chk_nspec", "chk_blk", "chk_op_off", "chk_op",
+                                  "cells_t")}
+    m2l, mult, loc = t["m2l"].reshape(-1, 3), t["mult"].reshape(-1, 2), t["local"].reshape(-1, 2)
+    cells, spec = t["cells_t"].reshape(-1, 7), t["spectra"].reshape(-1, 4)
+    goff, gch, boff, ooff = t["grp_member_off"], t["grp_chunk_off"], t["chk_blk_off"], t["chk_op_off"].reshape(-1, 9)
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]     # sigma of each code >> 3
+    assert len(t["chk_op"]) == len(m2l) == pl.info()["n_m2l_pairs"] > 0
+    seen = {}
+    for g in range(len(goff) - 1):
+        nm = goff[g + 1] - goff[g]
+        assert 1 <= nm <= 8
+        for ch in range(gch[g], gch[g + 1]):
+            assert np.all(np.diff(ooff[ch]) >= 0) and np.all(ooff[ch][nm:] == ooff[ch][nm])
+            nb, ns = boff[ch + 1] - boff[ch], t["chk_nspec"][ch]
+            for m in range(nm):
+                tc, td = loc[t["grp_members"][goff[g] + m]]
+                for op in t["chk_op"][ooff[ch][m]:ooff[ch][m + 1]]:
+                    bs, bm, code = op & 255, (op >> 8) & 255, op >> 16
+                    assert bs < ns <= bm < nb
+                    sc, sd = mult[t["m2f_list"][t["chk_blk"][boff[ch] + bm]]]
+                    lev, kbar = spec[t["chk_blk"][boff[ch] + bs], 0], spec[t["chk_blk"][boff[ch] + bs], 1:]
+                    k = cells[tc, 1:4] - cells[sc, 1:4]
+                    sigma = perms[code >> 3]
+                    for a in range(3):
+                        assert kbar[sigma[a]] == (-k[a] if (code >> a) & 1 else k[a])
+                    assert lev == cells[tc, 0] and sd == td
+                    assert (tc, sc) not in seen
+                    seen[(int(tc), int(sc))] = int(td)
+    assert seen == {(int(a), int(b)): int(d) for a, b, d in m2l}     # every pair once, in its direction

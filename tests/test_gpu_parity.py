@@ -131,7 +131,7 @@ def test_tensor_core_near_field_many_columns():
 @pytest.mark.parametrize("order", [4, 5, 6])
 def test_m2l_rhs_blocks_are_bitwise_identical(order):
     """1, 2 and 4 right-hand sides per M2L pass (with a ragged last pass: 5 columns),
-    blocks of 8 or 4 members and a smaller chunk budget give the same bits, and equal
+    blocks of 8 or 4 members or split by group size and a smaller chunk budget give the same bits, and equal
     the oracle; N = 7, 9 (blocks of at most 2 columns) and 11 (one column per pass)."""
     X = W.points("sphere", 3000, 61)
     q = W.charges(3000, 62, nrhs=5)
@@ -139,7 +139,7 @@ def test_m2l_rhs_blocks_are_bitwise_identical(order):
     plan = defmm.Plan(X, kappa=kappa, order=order, leaf_size=24)
     outs = []
     for rb in (1, 2, 4, 0):
-        for members in (8, 4):
+        for members in (8, 4, 12, 14):
             plan.set_tuning(m2l_rhs_block=rb, m2l_members_per_block=members)
             outs.append(_gpu(plan, q, torch.complex64))
             outs.append(_gpu(plan, q[:, 3], torch.complex64)[:, None])   # one column alone

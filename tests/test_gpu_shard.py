@@ -42,6 +42,14 @@ def test_shards_sum_to_the_whole(kind, n, kd, order, nrhs, dtype):
         assert plan.info()["device_error"] == 0
     plan.set_shard(1, 0)
     assert np.array_equal(_apply(plan, q, dtype), whole)
+    # M2L blocks split by group size (two launches over per-shard lists): the same bits
+    plan.set_tuning(m2l_members_per_block=12)
+    assert np.array_equal(_apply(plan, q, dtype), whole)
+    acc = np.zeros_like(whole)
+    for s in range(3):
+        plan.set_shard(3, s)
+        acc += _apply(plan, q, dtype)
+    assert np.array_equal(acc, whole)
 
 
 def test_shard_with_host_buffers_and_more_shards_than_leaves():
