@@ -197,13 +197,24 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
     if (t.nrhs > 1 && t.dtype == DEFMM_C64) rbs = {1, 2, 4};
     std::vector<int> tcs = {0};
     if (t.nrhs >= 8 && t.dtype == DEFMM_C64) tcs = {0, 1};
-    std::vector<int> mems = {0};
-    if (t.dtype == DEFMM_C64) mems = {12, 8, 4, 14};
     struct Launch { int tc, mem, rb; };   // apply-time choices timed on every candidate plan
-    std::vector<Launch> launches;
-    for (int tc : tcs)
-        for (int mem : mems)
-            for (int rb : rbs) launches.push_back({tc, mem, rb});
+    // members per M2L block: complex64 only; the splits by group size (12, 14)
+    // exist for N = 7 with one column per pass
+    auto launches_for = [&](int fft) {
+        const int N = fft ? fft : 2 * order - 1;
+        std::vector<Launch> v;
+        for (int tc : tcs)
+            for (int rb : rbs) {
+                std::vector<int> mems = {0};
+                if (t.dtype == DEFMM_C64) {
+                    const bool one = rb == 1 || (rb == 0 && t.nrhs == 1);
+                    if (order == 4 && N == 7 && one) mems = {12, 8, 4, 14};
+                    else mems = {8, 4};
+                }
+                for (int mem : mems) v.push_back({tc, mem, rb});
+            }
+        return v;
+    };
 
     // cache key: coordinates (host or device), sizes, parameters
     Fnv key;
@@ -281,6 +292,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
     bc.ms = 1e300;
     int timed = 0;
     for (int fft : ffts) {
+        const std::vector<Launch> launches = launches_for(fft);
         for (int leaf : leaves) {
             defmm_options oc = o;
             oc.fft_n = fft;

@@ -25,7 +25,9 @@ def test_autotune_choice_cache_and_results(tmp_path):
     assert choice["leaf_size"] in (24, 32, 48, 64)
     assert choice["fft_n"] in (0, 8)
     assert choice["m2l_rhs_block"] in (1, 2, 4)
-    assert choice["candidates"] == 4 * 2 * 3 * 2
+    # per leaf: N = 7 times 1 column per pass with 4 block splits, 2 and 4 columns with 2;
+    # N = 8 times 3 column counts with 2
+    assert choice["candidates"] == 4 * ((4 + 2 + 2) + 3 * 2)
     assert choice["m2l_members_per_block"] in (4, 8, 12, 14)
     assert choice["ms"] > 0
     assert plan.tuning()["m2l_rhs_block"] == choice["m2l_rhs_block"]
@@ -52,12 +54,12 @@ def test_autotune_choice_cache_and_results(tmp_path):
     # another nrhs is another key: tuned again, a second line appended
     _, c3 = defmm.autotune(X, kappa=kappa, order=4, nrhs=1, leaf_range=(48, 64), reps=2,
                            tune_fft_n=False, cache_path=str(cache))
-    assert c3["from_cache"] == 0 and c3["candidates"] == 2 * 2 and c3["m2l_rhs_block"] == 0
+    assert c3["from_cache"] == 0 and c3["candidates"] == 2 * 4 and c3["m2l_rhs_block"] == 0
     assert c3["p2p_tensor_cores"] == 0
     assert len(cache.read_text().splitlines()) == 2
 
     # 8 columns: the tensor-core near field is a candidate too
     p8, c4 = defmm.autotune(X, kappa=kappa, order=4, nrhs=8, leaf_range=(64, 64), reps=2,
                             tune_fft_n=False, cache_path=str(cache))
-    assert c4["candidates"] == 2 * 3 * 2 and c4["p2p_tensor_cores"] in (0, 1)
+    assert c4["candidates"] == 2 * (4 + 2 + 2) and c4["p2p_tensor_cores"] in (0, 1)
     assert p8.tuning()["p2p_tc_min_rhs"] == (1 if c4["p2p_tensor_cores"] else 0)
