@@ -202,16 +202,17 @@ defmm_status defmm_apply_noalloc(defmm_plan plan, const void* q, void* p, int nr
  *                   The two kernels round differently (both within
  *                   single-precision accuracy of the same sum).
  *  m2l_members_per_block - sibling targets per M2L thread block: 4, 8, or by
- *                   group size, 12 or 14 (0 = the library's choice: 12 for
+ *                   group size, 12 or 14 (0 = the library's choice: 14 for
  *                   N = 7 with one column per pass, 4 for N = 9 with one
  *                   column per pass, else 8).  With 4, groups of more siblings
  *                   take two blocks, each staging the group's chunks; smaller
- *                   blocks fit more per SM.  With 12 (order 4, N = 7, one
- *                   column per pass) groups of more than 4 siblings run in
- *                   blocks of 8 and the others whole in blocks of 4, two
- *                   launches, so few member warps idle; 14 adds blocks of 6
- *                   for groups of 5 or 6 (three launches).  Elsewhere 12 and 14
- *                   act as 4.  Kernels without a 4-member variant use 8.
+ *                   blocks fit more per SM.  By group size (order 4, N = 7, one
+ *                   column per pass) each group runs whole in a block of its
+ *                   size class, one launch per class, so few member warps
+ *                   idle: 14 = at most 4 siblings in blocks of 4, 5-7 in
+ *                   blocks of 7, 8 in blocks of 8; 12 = at most 4 in blocks
+ *                   of 4, more in blocks of 8.  Elsewhere 12 and 14 act as 4.
+ *                   Kernels without a 4-member variant use 8.
  *                   No output depends on it (bit for bit).
  * The setting applies to applies enqueued after the call; CUDA graphs
  * captured earlier keep the value they were captured with.

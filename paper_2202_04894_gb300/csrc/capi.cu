@@ -209,7 +209,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
         const int nm = hp.grp_member_off[g + 1] - hp.grp_member_off[g];
         if (nm > 4) gbig.push_back((int32_t)g);
         else gsmall.push_back((int32_t)(2 * g));
-        if (nm > 6) glarge.push_back((int32_t)g);
+        if (nm > 7) glarge.push_back((int32_t)g);
         else if (nm > 4) gmid.push_back((int32_t)g);
     }
     size_t o_gbig = b.add(gbig), o_gsmall = b.add(gsmall), o_gmid = b.add(gmid), o_glarge = b.add(glarge);
@@ -428,7 +428,7 @@ defmm_status build_shard(defmm_plan_s* pl, int nshards, int shard, cudaStream_t 
                 const int nm = hp.grp_member_off[g + 1] - hp.grp_member_off[g];
                 if (nm > 4) big.push_back((int32_t)g);
                 else small.push_back((int32_t)(2 * g));
-                if (nm > 6) large.push_back((int32_t)g);
+                if (nm > 7) large.push_back((int32_t)g);
                 else if (nm > 4) mid.push_back((int32_t)g);
                 break;
             }

@@ -2034,33 +2034,35 @@ cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T
             const int rb = m2l_pick_rb(c, w.R);
             if (p == 4 && N == 7) {
                 if (rb == 1 && (c.m2l_members == 0 || c.m2l_members == 12 || c.m2l_members == 14)) {
-                    // by group size (the default): groups of more than 4 siblings in
-                    // blocks of 8 (14: 5-6 siblings in blocks of 6, 7-8 in blocks of 8),
-                    // the others whole in blocks of 4, so few member warps idle
+                    // by group size: groups of at most 4 siblings whole in blocks of
+                    // 4 (five per SM), 5-7 in blocks of 7 and 8 in blocks of 8 (three
+                    // per SM; 0 and 14, the default), or more than 4 in blocks of 8
+                    // (12), so few member warps idle
+                    const bool three = c.m2l_members != 12;
                     bool fb = true, fs = true;
                     *nlaunch = 0;
-                    if (c.m2l_members != 14 && c.n_grp_big > 0) {
+                    if (!three && c.n_grp_big > 0) {
                         DevCommon cb = c;
                         cb.sh_grp = c.grp_big; cb.n_grp = c.n_grp_big;
                         rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(cb, t, w, stream, &fb);
                         ++*nlaunch;
                     }
-                    if (c.m2l_members == 14 && c.n_grp_large > 0) {
+                    if (three && c.n_grp_large > 0) {
                         DevCommon cb = c;
                         cb.sh_grp = c.grp_large; cb.n_grp = c.n_grp_large;
                         rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(cb, t, w, stream, &fb);
                         ++*nlaunch;
                     }
-                    if (c.m2l_members == 14 && fb && c.n_grp_mid > 0) {
+                    if (three && fb && c.n_grp_mid > 0) {
                         DevCommon cb = c;
                         cb.sh_grp = c.grp_mid; cb.n_grp = c.n_grp_mid;
-                        rows_launch<T, 8, 64, 1, 1, 4, 4, 7, 6>(cb, t, w, stream, &fb);
+                        rows_launch<T, 8, 64, 1, 1, 3, 4, 7, 7>(cb, t, w, stream, &fb);
                         ++*nlaunch;
                     }
                     if (fb && c.n_grp_small > 0) {
                         DevCommon cs = c;
                         cs.grp_half = c.grp_small; cs.n_grp_half = c.n_grp_small;
-                        rows_launch<T, 8, 64, 1, 1, 4, 4, 7, 4>(cs, t, w, stream, &fs);
+                        rows_launch<T, 8, 64, 1, 1, 5, 4, 7, 4>(cs, t, w, stream, &fs);
                         ++*nlaunch;
                     }
                     fits = fb && fs;
@@ -2327,7 +2329,8 @@ cudaError_t configure_kernels() {
         if ((e = rows_config<T, 8, 64, 1, 4, 1, 0, 0>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 9, 96, 1, 2, 1, 5, 9>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 8, 64, 1, 1, 4, 4, 7, 4>()) != cudaSuccess) return e;
-        if ((e = rows_config<T, 8, 64, 1, 1, 4, 4, 7, 6>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 1, 5, 4, 7, 4>()) != cudaSuccess) return e;
+        if ((e = rows_config<T, 8, 64, 1, 1, 3, 4, 7, 7>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 9, 96, 1, 2, 2, 5, 9, 4>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 9, 96, 1, 1, 2, 5, 9, 4>()) != cudaSuccess) return e;
         if ((e = rows_config<T, 12, 64, 2, 1, 2, 6, 11, 4>()) != cudaSuccess) return e;

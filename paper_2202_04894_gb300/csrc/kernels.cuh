@@ -41,18 +41,18 @@ struct DevCommon {
     // M2L schedule: groups of sibling targets, chunks of staged blocks and pair ops
     const int32_t *grp_member_off, *grp_members, *grp_chunk_off;  int64_t n_grp;
     const int32_t* grp_half;  int64_t n_grp_half;   // blocks of <= 4 members: group * 2 + half
-    // split by group size (members per block 12 or 0): groups of more than 4
+    // split by group size (members per block 12): groups of more than 4
     // members (ids) and the half-codes 2g of groups of at most 4
     const int32_t* grp_big;  int64_t n_grp_big;
     const int32_t* grp_small;  int64_t n_grp_small;
-    // three classes (members per block 14): 5-6 members and 7-8 members
+    // three classes (members per block 14 or 0): 5-7 members and 8 members
     const int32_t* grp_mid;  int64_t n_grp_mid;
     const int32_t* grp_large;  int64_t n_grp_large;
     const int32_t *chk_blk_off, *chk_nspec, *chk_blk, *chk_op_off, *chk_op;
     int chk_max_blocks;
     int chk_stage_blocks[3];  // largest stage (blocks) for 1, 2, 4 right-hand sides per pass
     int m2l_rb;               // right-hand sides per M2L pass (0: chosen from nrhs and N)
-    int m2l_members;          // members per M2L block: 4, 8, 12 (4 or 8 by group size), 14 (4, 6
+    int m2l_members;          // members per M2L block: 4, 8, 12 (4 or 8 by group size), 14 (4, 7
                               // or 8 by group size), 0 (default)
     int p2p_tc_min_rhs;       // complex64 applies with at least this many columns use the
                               // tensor-core near field (0: never)

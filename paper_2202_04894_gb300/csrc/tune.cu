@@ -208,7 +208,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
                 std::vector<int> mems = {0};
                 if (t.dtype == DEFMM_C64) {
                     const bool one = rb == 1 || (rb == 0 && t.nrhs == 1);
-                    if (order == 4 && N == 7 && one) mems = {12, 8, 4, 14};
+                    if (order == 4 && N == 7 && one) mems = {14, 12, 8, 4};
                     else mems = {8, 4};
                 }
                 for (int mem : mems) v.push_back({tc, mem, rb});
