@@ -284,6 +284,28 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.m2l_rb = 0;
     c.m2l_members = 0;
     c.p2p_tc_min_rhs = 0;
+    // Largest near-field phase in turns, kappa |x - y| / (2 pi), over the P2P cell
+    // pairs: |x - y| is at most the largest distance between the two cells' boxes.
+    {
+        auto corner = [&](const Tree& tr, int32_t cell, int a) {
+            if (hp.ngeo > 1) return hp.cell_corner_u[3 * (size_t)cell + a];
+            const int32_t i = a == 0 ? tr.ix[cell] : (a == 1 ? tr.iy[cell] : tr.iz[cell]);
+            return hp.corner[a] + lside[tr.level[cell]] * i;
+        };
+        double turns = 0;
+        for (const auto& pr : hp.p2p) {
+            const double st = lside[tt.level[pr[0]]], ss = lside[ts.level[pr[1]]];
+            double d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const double ta = corner(tt, pr[0], a), sa = corner(ts, pr[1], a);
+                const double far = std::max(std::fabs(ta + st - sa), std::fabs(sa + ss - ta));
+                d2 += far * far;
+            }
+            const double kap = hp.ngeo > 1 ? hp.geo_kappa[hp.cell_geo[pr[0]]] : hp.kappa;
+            turns = std::max(turns, kap * std::sqrt(d2) / (2 * M_PI));
+        }
+        c.p2p_short_phase = turns < 0.45 ? 1 : 0;
+    }
     c.p2m_cells = (const int32_t*)P(o_p2m); c.n_p2m = (int64_t)hp.p2m_cells.size();
     c.l2p_cells = (const int32_t*)P(o_l2p); c.n_l2p = (int64_t)hp.l2p_cells.size();
     c.p2p_unit_leaf = (const int32_t*)P(o_pul); c.p2p_unit_off = (const int32_t*)P(o_puo);

@@ -313,10 +313,13 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
 // to the cube centre and every difference is formed from both parts: a
 // single float per coordinate, even relative to the leaf, loses too much for
 // near-coincident pairs.  Charges are pre-scaled by 1/(4 pi) when staged;
-// partial sums are reduced over the splits in a fixed order.
+// partial sums are reduced over the splits in a fixed order.  REDUCE = false
+// serves plans whose near-field phases all stay below half a turn (kappa = 0,
+// or leaves small against the wavelength): there the phase reduction returns
+// its input unchanged, so skipping it gives the same bits.
 constexpr int kP2PRanges = kP2PUnitRanges;   // ranges of a work unit, held in shared memory
 
-template <int RB, bool DAMP = false>
+template <int RB, bool DAMP = false, bool REDUCE = true>
 __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __restrict__ qs,
                                                  float2* __restrict__ part, int R, int rb0) {
     __shared__ float4 sa[128];   // hi x, y, z and Re q / (4 pi)   (RB == 1)
@@ -412,7 +415,8 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
                             float rinv = rsqrt_hw(r2);
                             rinv = r2 > eps2 ? rinv : 0.f;
                             float sn, cs;
-                            turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                            if (REDUCE) turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                            else sincos_hw(6.28318530717958647692f * (r2 * rinv * kap2pi), &sn, &cs);
                             if (DAMP) rinv *= ex2_hw(-lam2 * (r2 * rinv));
                             ga = make_float2(cs * rinv, sn * rinv);
                         }
@@ -424,7 +428,8 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
                             float rinv = rsqrt_hw(r2);
                             rinv = r2 > eps2 ? rinv : 0.f;
                             float sn, cs;
-                            turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                            if (REDUCE) turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
+                            else sincos_hw(6.28318530717958647692f * (r2 * rinv * kap2pi), &sn, &cs);
                             if (DAMP) rinv *= ex2_hw(-lam2 * (r2 * rinv));
                             gb = make_float2(cs * rinv, sn * rinv);
                         }
@@ -2188,12 +2193,14 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         if constexpr (std::is_same<T, float>::value) {
             const unsigned nu = (unsigned)c.n_p2p_units;
             if (c.damping > 0.0) {
-                if (R == 1) k_p2p_f32<1, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                if (R == 1 && c.p2p_short_phase) k_p2p_f32<1, true, false><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                else if (R == 1) k_p2p_f32<1, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else if (p2p_rb == 16) k_p2p_f32<16, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else if (p2p_rb == 8) k_p2p_f32<8, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else k_p2p_f32<4, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
             } else {
-                if (R == 1) k_p2p_f32<1><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                if (R == 1 && c.p2p_short_phase) k_p2p_f32<1, false, false><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                else if (R == 1) k_p2p_f32<1><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else if (p2p_rb == 16) k_p2p_f32<16><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else if (p2p_rb == 8) k_p2p_f32<8><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
                 else k_p2p_f32<4><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
