@@ -11,6 +11,9 @@
 #include <type_traits>
 #include <vector>
 
+#include <sys/stat.h>
+#include <unistd.h>
+
 #include "plan.h"
 
 namespace defmm {
@@ -138,7 +141,14 @@ template <typename A, typename H> void plan_fields(A& a, H& h) {
 
 void save_plan_file(const std::string& path, const HostPlan& hp, const std::vector<double>& X,
                     const std::vector<double>& Y) {
-    FILE* f = std::fopen(path.c_str(), "wb");
+    // A regular (or new) file is written under a temporary name in the same
+    // directory and renamed over `path` once complete, so a failed save leaves
+    // neither a partial file nor a damaged earlier one.  Anything else (a
+    // device, a pipe) is written in place and never renamed or removed.
+    struct stat st;
+    const bool in_place = ::stat(path.c_str(), &st) == 0 && !S_ISREG(st.st_mode);
+    const std::string tmp = in_place ? path : path + ".tmp" + std::to_string((long)::getpid());
+    FILE* f = std::fopen(tmp.c_str(), "wb");
     if (!f) throw std::runtime_error("plan file: cannot open " + path + " for writing");
     try {
         Writer w{f, {}};
@@ -152,9 +162,17 @@ void save_plan_file(const std::string& path, const HostPlan& hp, const std::vect
         w.raw(h);
     } catch (...) {
         std::fclose(f);
+        if (!in_place) std::remove(tmp.c_str());
         throw;
     }
-    if (std::fclose(f) != 0) throw std::runtime_error("plan file: write failed");
+    if (std::fclose(f) != 0) {
+        if (!in_place) std::remove(tmp.c_str());
+        throw std::runtime_error("plan file: write failed");
+    }
+    if (!in_place && std::rename(tmp.c_str(), path.c_str()) != 0) {
+        std::remove(tmp.c_str());
+        throw std::runtime_error("plan file: cannot rename the written file to " + path);
+    }
 }
 
 void load_plan_file(const std::string& path, HostPlan& hp, std::vector<double>& X, std::vector<double>& Y) {

@@ -315,6 +315,10 @@ def test_plan_file_round_trip(tmp_path):
     with pytest.raises(defmm.DefmmError) as e:
         pl.save(tmp_path / "no_such_dir" / "x.plan")
     assert e.value.status == 1
+    # saving over an existing plan file replaces it whole; no temporary file stays behind
+    uni.save(tmp_path / "xy.plan")
+    assert defmm.Plan.load(tmp_path / "xy.plan", flags=defmm.PLAN_HOST_ONLY).nx == 1200
+    assert not [f for f in tmp_path.iterdir() if ".tmp" in f.name]
 
 
 @pytest.mark.parametrize("kind,n,kd,order", [("sphere", 4000, 40.0, 4), ("box", 4000, 8.0, 5), ("ellipsoid", 3000, 0.0, 4)])
