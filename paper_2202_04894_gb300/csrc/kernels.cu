@@ -950,9 +950,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // The same group schedule with rows of samples and a warp-specialised
-// pipeline.  A block takes the MAXM (8 or 4) members of a group or, with
-// MAXM = 4, one half of a larger group (its own pass over the group's chunks,
-// using the ops of its members only).  Consumer thread (member m, lane l) of
+// pipeline.  A block takes the members of a group (at most MAXM: 8, 7 or 4;
+// the group list of the launch, c.sh_grp, picks the groups) or, with MAXM =
+// 4, one half of a larger group (its own pass over the group's chunks, using
+// the ops of its members only).  Consumer thread (member m, lane l) of
 // the first MAXM*TPM threads owns the x-rows l + j*TPM (j < ROWS) of member m; row (y, z) = (l mod N,
 // l div N) holds the N samples xi = x + N*row.  Under a pair's symmetry
 // (sigma, s) a row's permuted indices are base(y, z) + x*step (with a wrap
