@@ -132,7 +132,7 @@ defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int
  * device tables (the transfer spectra are formed again on the GPU), skipping
  * the tree construction, traversals and scheduling.  A loaded plan computes
  * the same results as the saved one, bit for bit.  The format is this
- * library's own (magic "DEFMMPLN", version 1, native byte order, a 64-bit
+ * library's own (magic "DEFMMPLN", version 2, native byte order, a 64-bit
  * FNV-1a checksum at the end); the paper has no counterpart.  Lengths are
  * checked against the file size and the checksum against the contents, which
  * catches damaged files; a plan file is otherwise trusted input (its tables

@@ -1,7 +1,9 @@
 // Plan files: a HostPlan and the point coordinates it was built from, in a
 // plain binary layout (magic, version, then every field in a fixed order:
-// scalars as raw bytes, vectors as a 64-bit length followed by their
-// elements, then a 64-bit FNV-1a checksum of the fields).  Loading rebuilds the device tables (and the transfer spectra)
+// scalars and arrays of scalars as raw bytes, structs field by field so that
+// no padding byte is written, vectors as a 64-bit length followed by their
+// elements, then a 64-bit FNV-1a checksum of the fields).  The same plan
+// always gives the same file.  Loading rebuilds the device tables (and the transfer spectra)
 // from these, skipping the octree, traversals and schedules.
 #include <cstdint>
 #include <cstdio>
@@ -21,7 +23,7 @@ namespace defmm {
 namespace {
 
 constexpr char kMagic[8] = {'D', 'E', 'F', 'M', 'M', 'P', 'L', 'N'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;   // 2: Levels field by field (no padding bytes)
 
 // 64-bit FNV-1a over every byte after the header, stored at the end of the
 // file: a damaged plan file is refused instead of handing the kernels
@@ -112,7 +114,8 @@ template <typename A, typename H> void plan_fields(A& a, H& h) {
     a.raw(h.nx); a.raw(h.ny); a.raw(h.same); a.raw(h.kappa); a.raw(h.damping);
     a.raw(h.p); a.raw(h.N); a.raw(h.NF); a.raw(h.NFpad); a.raw(h.P3);
     a.raw(h.eta); a.raw(h.hf_kw); a.raw(h.self_eps_rel); a.raw(h.eps_self); a.raw(h.d_aabb); a.raw(h.side);
-    a.raw(h.corner); a.raw(h.lv);
+    a.raw(h.corner);
+    a.raw(h.lv.side0); a.raw(h.lv.kappa); a.raw(h.lv.eta); a.raw(h.lv.hf_kw); a.raw(h.lv.hf); a.raw(h.lv.l_hf);
     tree_fields(a, h.tt);
     tree_fields(a, h.ts_own);
     a.vec(h.m2l); a.vec(h.p2p); a.vecvec(h.marks_t); a.vecvec(h.marks_s);

@@ -103,11 +103,11 @@ static const int kPerms[6][3] = DEFMM_PERM_TABLE;
 
 Canon canonical(int64_t kx, int64_t ky, int64_t kz) {
     int64_t k[3] = {kx, ky, kz};
+    const int64_t mag[3] = {kx < 0 ? -kx : kx, ky < 0 ? -ky : ky, kz < 0 ? -kz : kz};
     int order[3] = {0, 1, 2};
-    std::stable_sort(order, order + 3, [&](int a, int b) {
-        int64_t va = k[a] < 0 ? -k[a] : k[a], vb = k[b] < 0 ? -k[b] : k[b];
-        return va > vb;
-    });
+    // stable insertion sort of the axes by decreasing |k_i| (equal entries keep their order)
+    for (int i = 1; i < 3; ++i)
+        for (int j = i; j > 0 && mag[order[j - 1]] < mag[order[j]]; --j) std::swap(order[j - 1], order[j]);
     Canon c;
     for (int j = 0; j < 3; ++j) {
         int64_t v = k[order[j]];
@@ -431,7 +431,14 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
             hp.mhat_of_m[e] = (int32_t)hp.m2f_list.size();
             hp.m2f_list.push_back((int32_t)e);
         }
-    std::stable_sort(recs.begin(), recs.end(), [](const PairRec& a, const PairRec& b) { return a.tgt < b.tgt; });
+    {   // stable counting sort of the pair records by target expansion
+        std::vector<int64_t> at(hp.l_cell.size() + 1, 0);
+        for (const PairRec& r : recs) ++at[(size_t)r.tgt + 1];
+        for (size_t e = 1; e < at.size(); ++e) at[e] += at[e - 1];
+        std::vector<PairRec> by_tgt(recs.size());
+        for (const PairRec& r : recs) by_tgt[(size_t)at[r.tgt]++] = r;
+        recs.swap(by_tgt);
+    }
 
     // ---- M2L groups and chunks (sibling targets sharing a father and a direction)
     {
@@ -445,28 +452,33 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         std::unordered_map<int64_t, int32_t> group_of;   // (father cell, direction) -> group
         std::vector<std::vector<int32_t>> members;        // local expansion ids
         std::vector<std::vector<Op>> gops;
+        // group and member slot of each target expansion, fixed at its first pair
+        // (records come sorted by target, so groups and members are numbered in
+        // the order their first pair appears)
+        std::vector<int32_t> grp_of_te(hp.l_cell.size(), -1), slot_of_te(hp.l_cell.size(), -1);
         for (size_t i = 0; i < recs.size(); ++i) {
             const int32_t te = recs[i].tgt;
-            const int32_t t = hp.l_cell[te], u = hp.l_dir[te];
-            const int64_t key = (int64_t)tt.parent[t] * (1LL << 32) + (int64_t)(u + 1);
-            auto it = group_of.find(key);
-            int32_t g;
-            if (it == group_of.end()) {
-                g = (int32_t)members.size();
-                group_of[key] = g;
-                members.push_back({});
-                gops.push_back({});
-            } else {
-                g = it->second;
+            if (grp_of_te[te] < 0) {
+                const int32_t t = hp.l_cell[te], u = hp.l_dir[te];
+                const int64_t key = (int64_t)tt.parent[t] * (1LL << 32) + (int64_t)(u + 1);
+                auto it = group_of.find(key);
+                int32_t g;
+                if (it == group_of.end()) {
+                    g = (int32_t)members.size();
+                    group_of[key] = g;
+                    members.push_back({});
+                    gops.push_back({});
+                } else {
+                    g = it->second;
+                }
+                if (members[g].size() >= 8) throw std::runtime_error("internal: more than 8 siblings in an M2L group");
+                grp_of_te[te] = g;
+                slot_of_te[te] = (int32_t)members[g].size();
+                members[g].push_back(te);
             }
-            auto& mem = members[g];
-            int32_t m = -1;
-            for (size_t q = 0; q < mem.size(); ++q)
-                if (mem[q] == te) m = (int32_t)q;
-            if (m < 0) { m = (int32_t)mem.size(); mem.push_back(te); }
-            if (m >= 8) throw std::runtime_error("internal: more than 8 siblings in an M2L group");
             const int32_t s_cell = hp.m_cell[recs[i].src];
-            gops[g].push_back({m, ts.parent[s_cell], hp.mhat_of_m[recs[i].src], recs[i].spec, recs[i].code});
+            gops[grp_of_te[te]].push_back({slot_of_te[te], ts.parent[s_cell], hp.mhat_of_m[recs[i].src], recs[i].spec,
+                                           recs[i].code});
         }
         // heaviest groups first
         std::vector<int32_t> gorder(members.size());

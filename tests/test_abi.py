@@ -288,6 +288,11 @@ def test_plan_file_round_trip(tmp_path):
                 assert a[key] == b[key], key
         for name in ("perm_t", "perm_s", "cells_t", "cells_s", "m2l", "p2p", "mult", "local"):
             assert np.array_equal(pl.table(name), back.table(name)), name
+        # the same plan always gives the same bytes (no padding or other indeterminate bytes)
+        again = _host_plan(X, src, kappa=9.0, order=5, leaf_size=20, damping=0.25)
+        again.save(tmp_path / "again.plan")
+        back.save(tmp_path / "back.plan")
+        assert path.read_bytes() == (tmp_path / "again.plan").read_bytes() == (tmp_path / "back.plan").read_bytes()
     geos = [W.points("sphere", 700, 123), W.points("ellipsoid", 500, 124)]
     uni = defmm.union_plan(geos, [4.0, 7.0], order=4, leaf_size=24, flags=defmm.PLAN_HOST_ONLY)
     uni.save(tmp_path / "u.plan")
