@@ -487,6 +487,10 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         hp.grp_member_off.push_back(0);
         hp.grp_chunk_off.push_back(0);
         hp.chk_blk_off.push_back(0);
+        hp.chk_op.reserve(recs.size());
+        std::vector<int32_t> specs, srcs;   // a chunk's distinct blocks, in first-use order
+        struct ChunkOp { int32_t member, code, sb, mb; };   // an op with its block positions
+        std::vector<ChunkOp> chunk, by_member;
         for (int32_t g : gorder) {
             for (int32_t te : members[g]) hp.grp_members.push_back(te);
             hp.grp_member_off.push_back((int32_t)hp.grp_members.size());
@@ -499,17 +503,22 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
             });
             size_t i = 0;
             while (i < ops.size()) {
-                std::vector<int32_t> specs, srcs;
-                std::vector<Op> chunk;
+                specs.clear();
+                srcs.clear();
+                chunk.clear();
                 while (i < ops.size()) {
                     const Op& o = ops[i];
-                    const bool new_sp = std::find(specs.begin(), specs.end(), o.spec) == specs.end();
-                    const bool new_src = std::find(srcs.begin(), srcs.end(), o.src) == srcs.end();
+                    const auto sp = std::find(specs.begin(), specs.end(), o.spec);
+                    const bool new_sp = sp == specs.end();
+                    // ops are sorted by (source father, source) and a source has one
+                    // father, so each source's ops form one run
+                    const bool new_src = srcs.empty() || srcs.back() != o.src;
                     const int need = (int)specs.size() + (int)srcs.size() + (new_sp ? 1 : 0) + (new_src ? 1 : 0);
                     if (!chunk.empty() && need > max_blocks) break;
+                    const int32_t sb = (int32_t)(sp - specs.begin());
                     if (new_sp) specs.push_back(o.spec);
                     if (new_src) srcs.push_back(o.src);
-                    chunk.push_back(o);
+                    chunk.push_back({o.member, o.code, sb, (int32_t)srcs.size() - 1});
                     ++i;
                 }
                 const int32_t nsp = (int32_t)specs.size();
@@ -519,16 +528,19 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
                 hp.chk_blk.insert(hp.chk_blk.end(), specs.begin(), specs.end());
                 hp.chk_blk.insert(hp.chk_blk.end(), srcs.begin(), srcs.end());
                 hp.chk_blk_off.push_back((int32_t)hp.chk_blk.size());
-                std::stable_sort(chunk.begin(), chunk.end(), [](const Op& a, const Op& b) { return a.member < b.member; });
+                // ops by member, in chunk order within a member (a stable bucket sort)
+                int32_t at[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                for (const ChunkOp& o : chunk) ++at[o.member + 1];
+                for (int m = 0; m < 8; ++m) at[m + 1] += at[m];
+                by_member.resize(chunk.size());
+                for (const ChunkOp& o : chunk) by_member[at[o.member]++] = o;
                 int32_t base = (int32_t)hp.chk_op.size();
                 size_t k = 0;
                 for (int m = 0; m < 8; ++m) {
                     hp.chk_op_off.push_back(base + (int32_t)k);
-                    while (k < chunk.size() && chunk[k].member == m) {
-                        const Op& o = chunk[k];
-                        const int32_t sb = (int32_t)(std::find(specs.begin(), specs.end(), o.spec) - specs.begin());
-                        const int32_t mb = nsp + (int32_t)(std::find(srcs.begin(), srcs.end(), o.src) - srcs.begin());
-                        hp.chk_op.push_back(sb | (mb << 8) | (o.code << 16));
+                    while (k < by_member.size() && by_member[k].member == m) {
+                        const ChunkOp& o = by_member[k];
+                        hp.chk_op.push_back(o.sb | ((nsp + o.mb) << 8) | (o.code << 16));
                         ++k;
                     }
                 }
