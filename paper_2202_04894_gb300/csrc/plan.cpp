@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <functional>
 #include <numeric>
 #include <stdexcept>
@@ -278,22 +279,27 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         dir_memo[key] = u;
         return u;
     };
-    std::function<void(int32_t, int32_t)> visit = [&](int32_t t, int32_t s) {
+    // depth first from (root, root) with an explicit stack; son pairs are
+    // pushed in reverse so that they are visited in (a, b) order
+    std::vector<std::array<int32_t, 2>> stack = {{0, 0}};
+    while (!stack.empty()) {
+        const int32_t t = stack.back()[0], s = stack.back()[1];
+        stack.pop_back();
         int l = tt.level[t];
         int64_t kx = (int64_t)tt.ix[t] - ts.ix[s], ky = (int64_t)tt.iy[t] - ts.iy[s],
                 kz = (int64_t)tt.iz[t] - ts.iz[s];
         if (lv.mac(l, kx, ky, kz)) {
             hp.m2l.push_back({t, s, pair_dir(l, kx, ky, kz)});
-            return;
+            continue;
         }
         if (tt.leaf(t) || ts.leaf(s)) {
             hp.p2p.push_back({t, s});
-            return;
+            continue;
         }
-        for (int32_t a = 0; a < tt.nchild[t]; ++a)
-            for (int32_t b = 0; b < ts.nchild[s]; ++b) visit(tt.first_child[t] + a, ts.first_child[s] + b);
-    };
-    visit(0, 0);
+        for (int32_t a = tt.nchild[t] - 1; a >= 0; --a)
+            for (int32_t b = ts.nchild[s] - 1; b >= 0; --b)
+                stack.push_back({tt.first_child[t] + a, ts.first_child[s] + b});
+    }
 
     // ---- Alg. 2 marks + Alg. 3 blank downward pass on both trees
     hp.marks_t.assign(tt.ncell(), {});
@@ -401,29 +407,57 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
     std::vector<PairRec> recs;
     recs.reserve(hp.m2l.size());
     std::vector<int32_t> is_src(hp.m_cell.size(), 0);
+    // spectrum and transform code of an offset: found once per (level, offset)
+    // and kept in a dense per-level table while that stays small
+    auto spectrum_of = [&](int l, int64_t kx, int64_t ky, int64_t kz, int32_t* code) {
+        const Canon cn = canonical(kx, ky, kz);
+        const int64_t key = (((int64_t)l * 4096 + cn.kbar[0]) * 4096 + cn.kbar[1]) * 4096 + cn.kbar[2];
+        *code = transform_code(cn);
+        auto it = spec_of.find(key);
+        if (it != spec_of.end()) return it->second;
+        const int32_t sid = (int32_t)hp.spec_level.size();
+        spec_of[key] = sid;
+        hp.spec_level.push_back(l);
+        hp.spec_kbar.push_back({cn.kbar[0], cn.kbar[1], cn.kbar[2]});
+        return sid;
+    };
+    std::vector<int64_t> kmax(kNumLevels + 1, -1);
+    for (const auto& pr : hp.m2l) {
+        const int l = tt.level[pr[0]];
+        const int64_t k = std::max({std::llabs((int64_t)tt.ix[pr[0]] - ts.ix[pr[1]]),
+                                    std::llabs((int64_t)tt.iy[pr[0]] - ts.iy[pr[1]]),
+                                    std::llabs((int64_t)tt.iz[pr[0]] - ts.iz[pr[1]])});
+        kmax[l] = std::max(kmax[l], k);
+    }
+    std::vector<std::vector<int32_t>> by_offset(kNumLevels + 1);   // sid * 64 + code, -1: not yet seen
+    for (int l = 0; l <= kNumLevels; ++l) {
+        const int64_t w = 2 * kmax[l] + 1;
+        if (kmax[l] >= 0 && w * w * w <= (int64_t(1) << 22)) by_offset[l].assign((size_t)(w * w * w), -1);
+    }
     for (size_t i = 0; i < hp.m2l.size(); ++i) {
         auto& pr = hp.m2l[i];
         int32_t t = pr[0], s = pr[1], u = pr[2];
         int l = tt.level[t];
         int64_t kx = (int64_t)tt.ix[t] - ts.ix[s], ky = (int64_t)tt.iy[t] - ts.iy[s],
                 kz = (int64_t)tt.iz[t] - ts.iz[s];
-        Canon cn = canonical(kx, ky, kz);
-        int64_t key = (((int64_t)l * 4096 + cn.kbar[0]) * 4096 + cn.kbar[1]) * 4096 + cn.kbar[2];
-        int32_t sid;
-        auto it = spec_of.find(key);
-        if (it == spec_of.end()) {
-            sid = (int32_t)hp.spec_level.size();
-            spec_of[key] = sid;
-            hp.spec_level.push_back(l);
-            hp.spec_kbar.push_back({cn.kbar[0], cn.kbar[1], cn.kbar[2]});
+        int32_t sid, code;
+        if (!by_offset[l].empty()) {
+            const int64_t K = kmax[l], w = 2 * K + 1;
+            int32_t& v = by_offset[l][(size_t)(((kx + K) * w + (ky + K)) * w + (kz + K))];
+            if (v < 0) {
+                sid = spectrum_of(l, kx, ky, kz, &code);
+                v = sid * 64 + code;
+            }
+            sid = v >> 6;
+            code = v & 63;
         } else {
-            sid = it->second;
+            sid = spectrum_of(l, kx, ky, kz, &code);
         }
         int32_t te = find_exp(hp.l_dir, hp.l_first[t], hp.l_count[t], u);
         int32_t se = find_exp(hp.m_dir, hp.m_first[s], hp.m_count[s], u);
         if (te < 0 || se < 0) throw std::runtime_error("internal: M2L expansion missing");
         is_src[se] = 1;
-        recs.push_back({te, se, sid, transform_code(cn), (int32_t)i});
+        recs.push_back({te, se, sid, code, (int32_t)i});
     }
     hp.mhat_of_m.assign(hp.m_cell.size(), -1);
     for (size_t e = 0; e < hp.m_cell.size(); ++e)
