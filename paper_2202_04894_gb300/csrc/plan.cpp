@@ -7,9 +7,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <exception>
 #include <functional>
 #include <numeric>
 #include <stdexcept>
+#include <thread>
 #include <unordered_map>
 
 namespace defmm {
@@ -518,69 +520,124 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         std::vector<int32_t> gorder(members.size());
         std::iota(gorder.begin(), gorder.end(), 0);
         std::stable_sort(gorder.begin(), gorder.end(), [&](int32_t a, int32_t b) { return gops[a].size() > gops[b].size(); });
+        // Chunks of each group, built by several threads over contiguous slices of
+        // the group order into their own arrays (block and op offsets relative to
+        // the slice), then concatenated in order: the same tables as one pass.
+        struct Slice {
+            std::vector<int32_t> members, member_n, chunk_n;           // per group
+            std::vector<int32_t> nspec, blk, blk_end, op, op_off;      // per chunk (ends relative)
+            int32_t stage[3] = {0, 0, 0};
+        };
+        auto build_slice = [&](size_t q0, size_t q1, Slice& out) {
+            std::vector<int32_t> specs, srcs;   // a chunk's distinct blocks, in first-use order
+            struct ChunkOp { int32_t member, code, sb, mb; };   // an op with its block positions
+            std::vector<ChunkOp> chunk, by_member;
+            for (size_t q = q0; q < q1; ++q) {
+                const int32_t g = gorder[q];
+                out.members.insert(out.members.end(), members[g].begin(), members[g].end());
+                out.member_n.push_back((int32_t)members[g].size());
+                auto& ops = gops[g];
+                // sources grouped by their father: a chunk then covers about one father's sons
+                std::stable_sort(ops.begin(), ops.end(), [](const Op& a, const Op& b) {
+                    if (a.src_parent != b.src_parent) return a.src_parent < b.src_parent;
+                    if (a.src != b.src) return a.src < b.src;
+                    return a.member < b.member;
+                });
+                int32_t nchunk = 0;
+                size_t i = 0;
+                while (i < ops.size()) {
+                    specs.clear();
+                    srcs.clear();
+                    chunk.clear();
+                    while (i < ops.size()) {
+                        const Op& o = ops[i];
+                        const auto sp = std::find(specs.begin(), specs.end(), o.spec);
+                        const bool new_sp = sp == specs.end();
+                        // ops are sorted by (source father, source) and a source has one
+                        // father, so each source's ops form one run
+                        const bool new_src = srcs.empty() || srcs.back() != o.src;
+                        const int need = (int)specs.size() + (int)srcs.size() + (new_sp ? 1 : 0) + (new_src ? 1 : 0);
+                        if (!chunk.empty() && need > max_blocks) break;
+                        const int32_t sb = (int32_t)(sp - specs.begin());
+                        if (new_sp) specs.push_back(o.spec);
+                        if (new_src) srcs.push_back(o.src);
+                        chunk.push_back({o.member, o.code, sb, (int32_t)srcs.size() - 1});
+                        ++i;
+                    }
+                    const int32_t nsp = (int32_t)specs.size();
+                    for (int v = 0; v < 3; ++v)   // stage size when 1, 2, 4 right-hand sides share it
+                        out.stage[v] = std::max(out.stage[v], nsp + (1 << v) * (int32_t)srcs.size());
+                    out.nspec.push_back(nsp);
+                    out.blk.insert(out.blk.end(), specs.begin(), specs.end());
+                    out.blk.insert(out.blk.end(), srcs.begin(), srcs.end());
+                    out.blk_end.push_back((int32_t)out.blk.size());
+                    // ops by member, in chunk order within a member (a stable bucket sort)
+                    int32_t at[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                    for (const ChunkOp& o : chunk) ++at[o.member + 1];
+                    for (int m = 0; m < 8; ++m) at[m + 1] += at[m];
+                    by_member.resize(chunk.size());
+                    for (const ChunkOp& o : chunk) by_member[at[o.member]++] = o;
+                    const int32_t base = (int32_t)out.op.size();
+                    size_t k = 0;
+                    for (int m = 0; m < 8; ++m) {
+                        out.op_off.push_back(base + (int32_t)k);
+                        while (k < by_member.size() && by_member[k].member == m) {
+                            const ChunkOp& o = by_member[k];
+                            out.op.push_back(o.sb | ((nsp + o.mb) << 8) | (o.code << 16));
+                            ++k;
+                        }
+                    }
+                    out.op_off.push_back(base + (int32_t)k);
+                    ++nchunk;
+                }
+                out.chunk_n.push_back(nchunk);
+            }
+        };
+        // slices of about equal op counts; one thread for small plans
+        const size_t ng = gorder.size();
+        int nthreads = (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency()));
+        if (recs.size() < (size_t)1 << 20) nthreads = 1;
+        std::vector<size_t> cut(1, 0);
+        {
+            size_t acc = 0, k = 1;
+            for (size_t q = 0; q < ng && (int)k < nthreads; ++q) {
+                acc += gops[gorder[q]].size();
+                if (acc * nthreads >= recs.size() * k) { cut.push_back(q + 1); ++k; }
+            }
+            cut.push_back(ng);
+        }
+        std::vector<Slice> slices(cut.size() - 1);
+        {
+            std::vector<std::exception_ptr> failed(slices.size());
+            auto run = [&](size_t j) {   // an exception (allocation) is carried back to this thread
+                try {
+                    build_slice(cut[j], cut[j + 1], slices[j]);
+                } catch (...) {
+                    failed[j] = std::current_exception();
+                }
+            };
+            std::vector<std::thread> pool;
+            for (size_t j = 1; j < slices.size(); ++j) pool.emplace_back(run, j);
+            run(0);
+            for (auto& th : pool) th.join();
+            for (auto& e : failed)
+                if (e) std::rethrow_exception(e);
+        }
         hp.grp_member_off.push_back(0);
         hp.grp_chunk_off.push_back(0);
         hp.chk_blk_off.push_back(0);
         hp.chk_op.reserve(recs.size());
-        std::vector<int32_t> specs, srcs;   // a chunk's distinct blocks, in first-use order
-        struct ChunkOp { int32_t member, code, sb, mb; };   // an op with its block positions
-        std::vector<ChunkOp> chunk, by_member;
-        for (int32_t g : gorder) {
-            for (int32_t te : members[g]) hp.grp_members.push_back(te);
-            hp.grp_member_off.push_back((int32_t)hp.grp_members.size());
-            auto& ops = gops[g];
-            // sources grouped by their father: a chunk then covers about one father's sons
-            std::stable_sort(ops.begin(), ops.end(), [](const Op& a, const Op& b) {
-                if (a.src_parent != b.src_parent) return a.src_parent < b.src_parent;
-                if (a.src != b.src) return a.src < b.src;
-                return a.member < b.member;
-            });
-            size_t i = 0;
-            while (i < ops.size()) {
-                specs.clear();
-                srcs.clear();
-                chunk.clear();
-                while (i < ops.size()) {
-                    const Op& o = ops[i];
-                    const auto sp = std::find(specs.begin(), specs.end(), o.spec);
-                    const bool new_sp = sp == specs.end();
-                    // ops are sorted by (source father, source) and a source has one
-                    // father, so each source's ops form one run
-                    const bool new_src = srcs.empty() || srcs.back() != o.src;
-                    const int need = (int)specs.size() + (int)srcs.size() + (new_sp ? 1 : 0) + (new_src ? 1 : 0);
-                    if (!chunk.empty() && need > max_blocks) break;
-                    const int32_t sb = (int32_t)(sp - specs.begin());
-                    if (new_sp) specs.push_back(o.spec);
-                    if (new_src) srcs.push_back(o.src);
-                    chunk.push_back({o.member, o.code, sb, (int32_t)srcs.size() - 1});
-                    ++i;
-                }
-                const int32_t nsp = (int32_t)specs.size();
-                for (int v = 0; v < 3; ++v)   // stage size when 1, 2, 4 right-hand sides share it
-                    hp.chk_stage_blocks[v] = std::max(hp.chk_stage_blocks[v], nsp + (1 << v) * (int32_t)srcs.size());
-                hp.chk_nspec.push_back(nsp);
-                hp.chk_blk.insert(hp.chk_blk.end(), specs.begin(), specs.end());
-                hp.chk_blk.insert(hp.chk_blk.end(), srcs.begin(), srcs.end());
-                hp.chk_blk_off.push_back((int32_t)hp.chk_blk.size());
-                // ops by member, in chunk order within a member (a stable bucket sort)
-                int32_t at[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-                for (const ChunkOp& o : chunk) ++at[o.member + 1];
-                for (int m = 0; m < 8; ++m) at[m + 1] += at[m];
-                by_member.resize(chunk.size());
-                for (const ChunkOp& o : chunk) by_member[at[o.member]++] = o;
-                int32_t base = (int32_t)hp.chk_op.size();
-                size_t k = 0;
-                for (int m = 0; m < 8; ++m) {
-                    hp.chk_op_off.push_back(base + (int32_t)k);
-                    while (k < by_member.size() && by_member[k].member == m) {
-                        const ChunkOp& o = by_member[k];
-                        hp.chk_op.push_back(o.sb | ((nsp + o.mb) << 8) | (o.code << 16));
-                        ++k;
-                    }
-                }
-                hp.chk_op_off.push_back(base + (int32_t)k);
-            }
-            hp.grp_chunk_off.push_back((int32_t)hp.chk_nspec.size());
+        for (const Slice& sl : slices) {
+            hp.grp_members.insert(hp.grp_members.end(), sl.members.begin(), sl.members.end());
+            for (int32_t n : sl.member_n) hp.grp_member_off.push_back(hp.grp_member_off.back() + n);
+            for (int32_t n : sl.chunk_n) hp.grp_chunk_off.push_back(hp.grp_chunk_off.back() + n);
+            const int32_t blk0 = (int32_t)hp.chk_blk.size(), op0 = (int32_t)hp.chk_op.size();
+            hp.chk_nspec.insert(hp.chk_nspec.end(), sl.nspec.begin(), sl.nspec.end());
+            hp.chk_blk.insert(hp.chk_blk.end(), sl.blk.begin(), sl.blk.end());
+            for (int32_t e : sl.blk_end) hp.chk_blk_off.push_back(blk0 + e);
+            hp.chk_op.insert(hp.chk_op.end(), sl.op.begin(), sl.op.end());
+            for (int32_t o : sl.op_off) hp.chk_op_off.push_back(op0 + o);
+            for (int v = 0; v < 3; ++v) hp.chk_stage_blocks[v] = std::max(hp.chk_stage_blocks[v], sl.stage[v]);
         }
         // the same groups cut into blocks of at most 4 members (heaviest first)
         for (size_t gi = 0; gi + 1 < hp.grp_member_off.size(); ++gi) {
