@@ -366,3 +366,46 @@ def test_m2l_schedule_covers_every_pair_once(kind, n, kd, order):
                     assert (tc, sc) not in seen
                     seen[(int(tc), int(sc))] = int(td)
     assert seen == {(int(a), int(b)): int(d) for a, b, d in m2l}     # every pair once, in its direction
+
+
+def test_m2l_schedule_of_a_large_plan():
+    """The same schedule checks, vectorised, on a plan of more than 2^20 M2L pairs (whose
+    chunks are built by several threads over slices of the group order, then concatenated):
+    op ranges are contiguous, every op names blocks of its own chunk, and the ops cover
+    every M2L pair once with the right expansions, level and symmetry."""
+    X = W.points("sphere", 100000, 7)
+    D = float(np.max(X.max(0) - X.min(0)))
+    pl = _host_plan(X, kappa=60.0 / D, order=4, leaf_size=32)
+    t = {k: pl.table(k) for k in ("m2l", "mult", "local", "m2f_list", "spectra", "grp_member_off", "grp_members",
+                                  "grp_chunk_off", "chk_blk_off", "chk_nspec", "chk_blk", "chk_op_off", "chk_op",
+                                  "cells_t")}
+    m2l, mult, loc = t["m2l"].reshape(-1, 3), t["mult"].reshape(-1, 2), t["local"].reshape(-1, 2)
+    cells, spec = t["cells_t"].reshape(-1, 7), t["spectra"].reshape(-1, 4)
+    goff, gch, boff, nspec = t["grp_member_off"], t["grp_chunk_off"], t["chk_blk_off"], t["chk_nspec"]
+    ooff, ops = t["chk_op_off"].reshape(-1, 9), t["chk_op"]
+    assert len(m2l) > 1 << 20
+    nch = len(nspec)
+    assert gch[0] == 0 and gch[-1] == nch and len(boff) == nch + 1 and len(ooff) == nch
+    assert ooff[0, 0] == 0 and ooff[-1, 8] == len(ops) and np.all(ooff[1:, 0] == ooff[:-1, 8])
+    counts = np.diff(ooff, axis=1)
+    assert np.all(counts >= 0)
+    chunk = np.repeat(np.arange(nch), ooff[:, 8] - ooff[:, 0])
+    member = np.repeat(np.tile(np.arange(8), nch), counts.ravel())
+    group = np.repeat(np.arange(len(goff) - 1), np.diff(gch))[chunk]
+    assert np.all(member < (goff[group + 1] - goff[group]))
+    te = t["grp_members"][goff[group] + member]
+    bs, bm, code = ops & 255, (ops >> 8) & 255, ops >> 16
+    assert np.all(bs < nspec[chunk]) and np.all(nspec[chunk] <= bm) and np.all(bm < (boff[chunk + 1] - boff[chunk]))
+    sid, slot = t["chk_blk"][boff[chunk] + bs], t["chk_blk"][boff[chunk] + bm]
+    tc, td = loc[te, 0], loc[te, 1]
+    sc, sd = mult[t["m2f_list"][slot], 0], mult[t["m2f_list"][slot], 1]
+    assert np.all(td == sd) and np.all(spec[sid, 0] == cells[tc, 0])
+    k = cells[tc, 1:4] - cells[sc, 1:4]
+    perms = np.array([(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)])
+    sigma = perms[code >> 3]
+    for a in range(3):
+        sign = np.where((code >> a) & 1, -1, 1)
+        assert np.all(spec[sid, 1 + sigma[:, a]] == sign * k[:, a])
+    got = np.lexsort((td, sc, tc))
+    want = np.lexsort((m2l[:, 2], m2l[:, 1], m2l[:, 0]))
+    assert np.array_equal(np.stack([tc, sc, td], 1)[got], m2l[want])
