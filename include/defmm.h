@@ -130,8 +130,9 @@ defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int
  * traversal lists, expansions, phase tables, schedules) and the coordinates it
  * was built from to `path`; defmm_plan_load reads such a file and rebuilds the
  * device tables (the transfer spectra are formed again on the GPU), skipping
- * the tree construction, traversals and scheduling.  A loaded plan computes
- * the same results as the saved one, bit for bit.  The format is this
+ * the tree construction, traversals and scheduling.  With the same tuning
+ * and shard settings (which are not saved) a loaded plan computes the same
+ * results as the saved one, bit for bit.  The format is this
  * library's own (magic "DEFMMPLN", version 2, native byte order, a 64-bit
  * FNV-1a checksum at the end); the paper has no counterpart.  Lengths are
  * checked against the file size and the checksum against the contents, which
@@ -171,7 +172,8 @@ defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host,
  * counterpart: it is a property of this library's memory management.
  * The scratch comes from a fixed 64 MiB array linked into the library (held
  * by every GPU that loads it until exit); the call makes no cudaMalloc or
- * cudaFree.  Arguments, layouts and results are those of defmm_apply.
+ * cudaFree.  Arguments, layouts and results are those of defmm_apply,
+ * bit for bit, including a plan set to one shard (defmm_plan_set_shard).
  *  - Plans whose scratch for nrhs exceeds 64 MiB are rejected with
  *    DEFMM_ERR_UNSUPPORTED (the message gives both sizes).
  *  - The first call on a device looks the array's address up

@@ -356,23 +356,8 @@ template <typename T> defmm_status apply_impl(defmm_plan_s* pl, Workspace<T>& w,
     dw.part = w.part;
     const DevTyped<T>& typed = typed_tables(pl, (T*)nullptr);
     int launches = 0;
-    DevCommon c = pl->common;
-    const LevelList* l2l = pl->l2l.data();
-    if (pl->sh.nshards > 1) {   // this plan's shard of the targets
-        const auto& h = pl->sh;
-        c.sh_on = 1;
-        c.sh_grp = h.grp; c.n_grp = h.n_grp;
-        c.grp_half = h.half; c.n_grp_half = h.n_half;
-        c.grp_big = h.big; c.n_grp_big = h.n_big;
-        c.grp_small = h.small; c.n_grp_small = h.n_small;
-        c.grp_mid = h.mid; c.n_grp_mid = h.n_mid;
-        c.grp_large = h.large; c.n_grp_large = h.n_large;
-        c.sh_unit = h.unit; c.n_p2p_units = h.n_unit;
-        c.sh_leaf = h.leaf; c.n_p2p_leaf = h.n_leaf;
-        c.l2p_cells = h.l2p; c.n_l2p = h.n_l2p;
-        c.sh_t0 = h.t0; c.sh_t1 = h.t1;
-        l2l = h.l2l.data();
-    }
+    const LevelList* l2l = nullptr;
+    const DevCommon c = apply_tables(pl, &l2l);
     cudaError_t e = launch_apply<T>(c, typed, dw, pl->m2m.data(), (int)pl->m2m.size(), l2l,
                                     pl->l2l_par.data(), (int)pl->l2l.size(), q, p, stream, &launches,
                                     pl->profiling ? pl->events : nullptr);

@@ -100,7 +100,9 @@ defmm_status apply_static(defmm_plan_s* pl, const void* q, void* p, int R, cudaS
     w.nL = hp.nL();
     const defmm::DevTyped<T>& typed = typed_tables(pl, (T*)nullptr);
     int launches = 0;
-    cudaError_t e = defmm::launch_apply<T>(pl->common, typed, w, pl->m2m.data(), (int)pl->m2m.size(), pl->l2l.data(),
+    const defmm::LevelList* l2l = nullptr;
+    const defmm::DevCommon c = defmm::apply_tables(pl, &l2l);
+    cudaError_t e = defmm::launch_apply<T>(c, typed, w, pl->m2m.data(), (int)pl->m2m.size(), l2l,
                                            pl->l2l_par.data(), (int)pl->l2l.size(), q, p, stream, &launches,
                                            pl->profiling ? pl->events : nullptr);
     pl->launches = launches;

@@ -597,6 +597,10 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         const size_t ng = gorder.size();
         int nthreads = (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency()));
         if (recs.size() < (size_t)1 << 20) nthreads = 1;
+        if (const char* env = std::getenv("DEFMM_PLAN_THREADS")) {   // explicit count (1..8), any plan size
+            const int v = std::atoi(env);
+            if (v >= 1) nthreads = std::min(v, 8);
+        }
         std::vector<size_t> cut(1, 0);
         {
             size_t acc = 0, k = 1;
@@ -616,9 +620,15 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
                     failed[j] = std::current_exception();
                 }
             };
+            // slices whose thread cannot be created run here, after slice 0
             std::vector<std::thread> pool;
-            for (size_t j = 1; j < slices.size(); ++j) pool.emplace_back(run, j);
+            size_t started = 1;
+            try {
+                for (; started < slices.size(); ++started) pool.emplace_back(run, started);
+            } catch (...) {
+            }
             run(0);
+            for (size_t j = started; j < slices.size(); ++j) run(j);
             for (auto& th : pool) th.join();
             for (auto& e : failed)
                 if (e) std::rethrow_exception(e);

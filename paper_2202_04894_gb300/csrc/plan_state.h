@@ -61,3 +61,33 @@ struct defmm_plan_s {
         std::vector<defmm::LevelList> l2l;
     } sh;
 };
+
+namespace defmm {
+
+// The device tables an apply of this plan launches with: the whole operator,
+// or, after defmm_plan_set_shard with more than one shard, the shard's target
+// groups, near-field units and leaves, L2P cells, L2L lists and target range.
+// Every apply entry point (plan scratch, caller workspace, static scratch)
+// goes through this, so all of them compute the same shard.
+inline DevCommon apply_tables(const defmm_plan_s* pl, const LevelList** l2l) {
+    DevCommon c = pl->common;
+    *l2l = pl->l2l.data();
+    if (pl->sh.nshards > 1) {
+        const auto& h = pl->sh;
+        c.sh_on = 1;
+        c.sh_grp = h.grp; c.n_grp = h.n_grp;
+        c.grp_half = h.half; c.n_grp_half = h.n_half;
+        c.grp_big = h.big; c.n_grp_big = h.n_big;
+        c.grp_small = h.small; c.n_grp_small = h.n_small;
+        c.grp_mid = h.mid; c.n_grp_mid = h.n_mid;
+        c.grp_large = h.large; c.n_grp_large = h.n_large;
+        c.sh_unit = h.unit; c.n_p2p_units = h.n_unit;
+        c.sh_leaf = h.leaf; c.n_p2p_leaf = h.n_leaf;
+        c.l2p_cells = h.l2p; c.n_l2p = h.n_l2p;
+        c.sh_t0 = h.t0; c.sh_t1 = h.t1;
+        *l2l = h.l2l.data();
+    }
+    return c;
+}
+
+}  // namespace defmm

@@ -155,6 +155,43 @@ def test_plan_tables_equal_oracle(case):
     assert info["n_spectra"] == len(op.spectra)
 
 
+def _rows(a):
+    """Rows of a 2-D integer array in lexicographic order."""
+    a = np.asarray(a, dtype=np.int64)
+    return a[np.lexsort(a.T[::-1])]
+
+
+def test_plan_tables_equal_oracle_above_2_20_pairs(monkeypatch):
+    """A plan of more than 2^20 M2L pairs (its chunks built by several threads): tree, DTT
+    pairs with directions and effective expansions equal the oracle's (Sec. 4.2.1, Alg. 1-3)
+    bit for bit, and the schedule tables are the same whether one thread or eight build them."""
+    X = W.points("sphere", 60000, 7)
+    D = float(np.max(X.max(0) - X.min(0)))
+    kw = dict(kappa=60.0 / D, order=4, leaf_size=32)
+    monkeypatch.setenv("DEFMM_PLAN_THREADS", "8")
+    pl = _host_plan(X, **kw)
+    op = oracle_fmm.make_plan(X, None, kappa=kw["kappa"], order=4, leaf=32)
+    m2l = np.array([(t, s, u) for (t, s), u in zip(op.m2l_pairs, op.pair_dir)], dtype=np.int64)
+    assert len(m2l) > 1 << 20
+    cells = np.stack([op.tt.level, op.tt.coords[:, 0], op.tt.coords[:, 1], op.tt.coords[:, 2],
+                      op.tt.begin, op.tt.end, op.tt.parent], 1)
+    assert np.array_equal(pl.table("perm_t"), op.tt.perm)
+    assert np.array_equal(pl.table("cells_t").reshape(-1, 7), cells)
+    assert np.array_equal(_rows(pl.table("m2l").reshape(-1, 3)), _rows(m2l))
+    assert np.array_equal(_rows(pl.table("p2p").reshape(-1, 2)), _rows(np.array(op.p2p_pairs)))
+    mult = np.array([(c, u) for c in range(op.ts.ncell) for u in op.marks_s[c]])
+    loc = np.array([(c, u) for c in range(op.tt.ncell) for u in op.marks_t[c]])
+    assert np.array_equal(pl.table("mult").reshape(-1, 2), mult)
+    assert np.array_equal(pl.table("local").reshape(-1, 2), loc)
+    names = ("grp_member_off", "grp_members", "grp_chunk_off", "chk_blk_off", "chk_nspec", "chk_blk",
+             "chk_op_off", "chk_op")
+    threaded = {k: pl.table(k) for k in names}
+    monkeypatch.setenv("DEFMM_PLAN_THREADS", "1")
+    one = _host_plan(X, **kw)
+    for k in names:
+        assert np.array_equal(one.table(k), threaded[k]), k
+
+
 def test_degenerate_inputs_host_plan():
     one = np.array([[0.1, 0.2, 0.3]])
     pl = _host_plan(one, kappa=3.0, order=4, leaf_size=4)

@@ -136,3 +136,36 @@ def test_blank_passes_supply_every_needed_expansion():
             for v in plan.marks_s[c]:
                 want = -1 if (v < 0 or not lv.hf[l + 1]) else dirs.father(lv.E(l), v)
                 assert want in plan.marks_s[c2]
+
+
+@pytest.mark.parametrize("other", [None, ("ellipsoid", 2500)])
+def test_blank_passes_on_both_trees_exact(other):
+    """Alg. 2 and Alg. 3 on the target tree as well as the source tree, with one tree
+    and with two different trees: every HF cell's marks are exactly the directions of
+    its own M2L pairs plus Father(u) of its father's marks (nothing missing, nothing
+    extra), and every LF cell has the single non-directional expansion."""
+    X = W.points("sphere", 3000, 4)
+    Y = None if other is None else 0.9 * W.points(other[0], other[1], 5)
+    plan = fmm.make_plan(X, Y, kappa=24.0, order=3, leaf=16)
+    lv = plan.levels
+    assert lv.l_hf >= 2
+    for tree, marks, side in ((plan.tt, plan.marks_t, 0), (plan.ts, plan.marks_s, 1)):
+        own = [set() for _ in range(tree.ncell)]
+        for pair, u in zip(plan.m2l_pairs, plan.pair_dir):
+            if u >= 0:
+                own[pair[side]].add(u)
+        parent_of = {}
+        for c in range(tree.ncell):
+            for c2 in tree.children(c):
+                parent_of[c2] = c
+        for c in range(tree.ncell):
+            l = int(tree.level[c])
+            if not lv.hf[l]:
+                assert marks[c] == [-1]
+                continue
+            want = set(own[c])
+            f = parent_of.get(c)
+            if f is not None and lv.hf[l - 1]:
+                want |= {dirs.father(lv.E(l - 1), v) for v in marks[f]}
+            assert set(marks[c]) == want, (side, c)
+            assert marks[c] == sorted(marks[c])
