@@ -197,30 +197,67 @@ def cpu_sample(n=SAMPLE_N):
     return X, q, kappa, w["order"], w["leaf"], desc
 
 
-def time_oracle(steps, warmup, n=SAMPLE_N):
+def time_oracle(steps, warmup, n=SAMPLE_N, out_path=None, ready_dir=None, nready=0):
+    """Times the oracle's apply (plan excluded) on the sample; saves the last result to
+    out_path (.npy) if given.  With ready_dir, waits after building the plan until nready
+    processes have done so, so that concurrent copies time overlapping applies."""
     from oracle import fmm
     X, q, kappa, order, leaf, desc = cpu_sample(n)
     plan = fmm.make_plan(X, kappa=kappa, order=order, leaf=leaf)
+    if ready_dir:
+        open(os.path.join(ready_dir, "ready.%d" % os.getpid()), "w").close()
+        t_wait = time.perf_counter()
+        while len(os.listdir(ready_dir)) < nready and time.perf_counter() - t_wait < 600:
+            time.sleep(0.01)
     for _ in range(warmup):
         fmm.apply(plan, X, q)
     ts = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        fmm.apply(plan, X, q)
+        p = fmm.apply(plan, X, q)
         ts.append(time.perf_counter() - t0)
+    if out_path:
+        np.save(out_path, p)
     sec = sum(ts) / len(ts)
     return len(X) * q.shape[1] / sec / 1e6, sec, desc
 
 
-def oracle_subprocess(steps, warmup, n, timeout=1800):
-    """Runs time_oracle in a fresh single-threaded interpreter (BLAS pinned to 1 thread)."""
+def _oracle_cmd(steps, warmup, n, out_path=None, ready_dir=None, nready=0):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.time_oracle(%d, %d, %d)))" % (ROOT, steps, warmup, n))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
+            "print(json.dumps(bench.time_oracle(%d, %d, %d, %r, %r, %d)))"
+            % (ROOT, steps, warmup, n, out_path, ready_dir, nready))
+    return [sys.executable, "-c", code], env
+
+
+def oracle_subprocess(steps, warmup, n, timeout=1800, out_path=None):
+    """Runs time_oracle in a fresh single-threaded interpreter (BLAS pinned to 1 thread)."""
+    cmd, env = _oracle_cmd(steps, warmup, n, out_path)
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-400:])
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_all_cores(n, timeout=900):
+    """One single-threaded oracle process per host core, each applying the same sample at
+    the same time (they start timing together); returns (aggregate Mpoints*RHS/s, cores,
+    slowest apply in s).  The oracle itself is unchanged: this is nproc copies of it."""
+    import tempfile
+    cores = os.cpu_count() or 1
+    with tempfile.TemporaryDirectory() as ready:
+        procs = []
+        for _ in range(cores):
+            cmd, env = _oracle_cmd(1, 0, n, None, ready, cores)
+            procs.append(subprocess.Popen(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+        secs = []
+        for pr in procs:
+            out, err = pr.communicate(timeout=timeout)
+            if pr.returncode != 0:
+                raise RuntimeError(err[-400:])
+            secs.append(json.loads(out.strip().splitlines()[-1])[1])
+    slowest = max(secs)
+    return cores * n / slowest / 1e6, cores, slowest
 
 
 def reference_arm(args):
@@ -383,18 +420,19 @@ def main():
     dominant = max(kernel_phases, key=kernel_phases.get)
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     # P2P, one right-hand side: 3 SFU operations (rsqrt, sin, cos) per
-    # interaction; 16 SFU results per clock per SM on 152 SMs.  Several
+    # interaction; 16 SFU results per clock per SM (SM count queried).  Several
     # right-hand sides: 4 FP32 FMA per interaction and column (complex
     # multiply-add) against 128 FMA per clock per SM.
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     inter = info["p2p_interactions"] * R
     p2p_achieved = inter / (phase_avg["p2p"] * 1e-3) / 1e9
     if R == 1:
-        p2p_peak = 152 * 16 / 3 * sm_max * 1e6 / 1e9
-        p2p_src = "SFU: 152 SMs x 16/clk / 3 per interaction at %.0f MHz" % sm_max
+        p2p_peak = sms * 16 / 3 * sm_max * 1e6 / 1e9
+        p2p_src = "SFU: %d SMs x 16/clk / 3 per interaction at %.0f MHz" % (sms, sm_max)
         p2p_unit = "Ginteractions/s"
     else:
-        p2p_peak = 152 * 128 / 4 * sm_max * 1e6 / 1e9
-        p2p_src = "FP32 FMA: 152 SMs x 128/clk / 4 per interaction and column at %.0f MHz" % sm_max
+        p2p_peak = sms * 128 / 4 * sm_max * 1e6 / 1e9
+        p2p_src = "FP32 FMA: %d SMs x 128/clk / 4 per interaction and column at %.0f MHz" % (sms, sm_max)
         p2p_unit = "Ginteraction-columns/s"
     p2p_roof = {"kernel": "p2p", "bound": "alu", "achieved": p2p_achieved, "peak": p2p_peak,
                 "unit": p2p_unit, "frac": p2p_achieved / p2p_peak, "traffic": None, "peak_source": p2p_src}
@@ -406,11 +444,27 @@ def main():
                 "traffic_source": "profiles/m2l_rows_sphere300k_kD128_p4.md, DRAM bytes per pair x pairs"}
     roof = p2p_roof if dominant == "p2p" else m2l_roof
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    cpu, vs_oracle = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD and not args.n:
+        import tempfile
         try:
-            v, s, d = oracle_subprocess(1, 0, SAMPLE_N)
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": d, "seconds": s}
+            with tempfile.TemporaryDirectory() as tmp:
+                ref_path = os.path.join(tmp, "oracle.npy")
+                v1, s1, d = oracle_subprocess(1, 0, SAMPLE_N, out_path=ref_path)
+                ref = np.load(ref_path)
+            vall, cores, sall = oracle_all_cores(SAMPLE_N)
+            cpu = {"value": vall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": d + "; %d single-threaded oracle processes applying it at once" % cores,
+                   "seconds": sall, "value_1core": v1, "seconds_1core": s1}
+            # the timed form (complex64, same plan options) on the oracle's own sample
+            Xs, qs_, ks, os_, ls, _ = cpu_sample(SAMPLE_N)
+            sp = defmm.Plan(Xs, kappa=ks, order=os_, leaf_size=ls)
+            got = sp.apply(torch.from_numpy(np.ascontiguousarray(qs_[:, 0])).to("cuda").to(cdt)).cpu().numpy()
+            sp.close()
+            ref = ref.reshape(got.shape)
+            vs_oracle = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                         "max_rel": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+                         "dtype": dtype, "sample": d}
         except Exception as ex:  # reported, never fatal
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(ex)[:200]}
 
@@ -431,7 +485,8 @@ def main():
                         "d2h_bytes_per_step": len(X) * R * csz, "ms_per_step": statistics.mean(e2e_ms)},
                 "clocks": clk, "gpu_launches": launches_per_apply * args.steps,
                 "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
-                "rel_l2_c64_vs_c128": rel, "phase_ms": phase_avg, "plan_s": plan_s,
+                "rel_l2_c64_vs_c128": rel, "rel_l2_vs_oracle": vs_oracle and vs_oracle["rel_l2"],
+                "vs_oracle": vs_oracle, "phase_ms": phase_avg, "plan_s": plan_s,
                 "fp64_gpu_apply": {"ms": fp64_ms, "value": units / (fp64_ms * 1e-3) / 1e6, "unit": UNIT,
                                    "speedup_of_c64": fp64_ms / ms_per_step},
                 "plan": {k: info[k] for k in ("n_m2l_pairs", "n_p2p_pairs", "n_multipole", "n_local", "n_fourier",

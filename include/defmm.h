@@ -334,8 +334,9 @@ defmm_status defmm_gmres(defmm_plan plan, const void* b, void* x, defmm_dtype dt
  * this plan compute shard `shard` of `nshards` (nshards = 1: the whole
  * operator, the default): p receives the shard's potentials in the caller's
  * order and zeros elsewhere, so summing the nshards outputs (an all-reduce
- * across GPUs) gives the whole result, bit for bit.  Workspace, batch,
- * server and no-allocation applies always compute the whole operator.  The
+ * across GPUs) gives the whole result, bit for bit.  defmm_apply_noalloc
+ * follows the setting too; workspace, batch and server applies
+ * (defmm_serve.h) always compute the whole operator.  The
  * call synchronises `stream` and the device, builds the shard's tables (one
  * device allocation held by the plan) and returns.
  * defmm_plan_shard_range gives the shard's targets in Morton (sorted) order:
@@ -387,7 +388,11 @@ defmm_status defmm_plan_info(defmm_plan plan, defmm_info* out);
  *       its first chk_nspec are spectrum ids, the rest Fourier-multipole
  *       slots), "chk_op_off" (9 per chunk: op ranges of members 0..7, end),
  *       "chk_op" (spectrum block | multipole block << 8 | symmetry code << 16;
- *       code bit a negates axis a, code >> 3 names the axis permutation).
+ *       code bit a negates axis a, code >> 3 names the axis permutation),
+ *       the near-field work units: "p2p_leaf" (near-field target leaf cells),
+ *       "p2p_unit_leaf" (unit -> index into p2p_leaf), "p2p_unit_off" (CSR:
+ *       unit -> source ranges), "p2p_unit_ranges" (per range: first, end
+ *       sorted source position).
  * Copies min(count, capacity) int64 values to out (host) and sets *count to
  * the full length.  out may be NULL to query the length.                    */
 defmm_status defmm_plan_table(defmm_plan plan, const char* name, int64_t* out,

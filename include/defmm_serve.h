@@ -61,7 +61,9 @@ defmm_status defmm_workspace_destroy(defmm_workspace ws);
  * with distinct workspaces may run at the same time on different streams or
  * threads; a workspace must not be used by two applies at once (not
  * checked).  No phase events are recorded (defmm_profile_* see only
- * defmm_apply).  Results equal defmm_apply's bit for bit.
+ * defmm_apply).  It always computes the whole operator, whatever the plan's
+ * shard setting (defmm_plan_set_shard); results equal those of defmm_apply
+ * on a plan that is not sharded, bit for bit.
  * Errors: DEFMM_ERR_ARG (NULL, foreign workspace, nrhs out of range, dtype
  * mismatch), DEFMM_ERR_CUDA (launch failure).                                */
 defmm_status defmm_apply_ws(defmm_plan plan, defmm_workspace ws, const void* q, void* p, int nrhs,

@@ -871,6 +871,11 @@ defmm_status defmm_plan_table(defmm_plan plan, const char* name, int64_t* out, i
     else if (n == "chk_blk") v.assign(hp.chk_blk.begin(), hp.chk_blk.end());
     else if (n == "chk_op_off") v.assign(hp.chk_op_off.begin(), hp.chk_op_off.end());
     else if (n == "chk_op") v.assign(hp.chk_op.begin(), hp.chk_op.end());
+    else if (n == "p2p_unit_leaf") v.assign(hp.p2p_unit_leaf.begin(), hp.p2p_unit_leaf.end());
+    else if (n == "p2p_unit_off") v.assign(hp.p2p_unit_off.begin(), hp.p2p_unit_off.end());
+    else if (n == "p2p_unit_ranges")
+        for (size_t k = 0; k < hp.p2p_sbeg.size(); ++k) v.insert(v.end(), {hp.p2p_sbeg[k], hp.p2p_send[k]});
+    else if (n == "p2p_leaf") v.assign(hp.p2p_leaf.begin(), hp.p2p_leaf.end());
     else return fail(DEFMM_ERR_ARG, "unknown table " + n);
     *count = (int64_t)v.size();
     if (out) std::memcpy(out, v.data(), sizeof(int64_t) * std::min<int64_t>(capacity, (int64_t)v.size()));

@@ -153,7 +153,7 @@ defmm_status gmres_impl(defmm_plan plan, int64_t n, const C* b, C* x, defmm_dtyp
     if (e != cudaSuccess) { cudaGetLastError(); return cuda_status(e, "scratch"); }
     C* V = static_cast<C*>(s.V);
     C* w = static_cast<C*>(s.w);
-    const int eb = 152 * 4;
+    const int eb = defmm::sm_count() * 4;
     std::vector<double2> hbuf(m + 1);
 
     // conj(V_i) . v for i < k, read back to the host

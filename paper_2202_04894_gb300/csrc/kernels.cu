@@ -19,6 +19,7 @@
 // take the plan's tables by value (DevCommon); a shard of the targets or a
 // union of several geometries only changes which entries they visit and where
 // a cell's wavenumber comes from.
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -2126,6 +2127,21 @@ cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T
     return cudaSuccess;
 }
 
+int sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 152;
+        }
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 cudaError_t launch_wait_probe(int* flag, int spins, cudaStream_t stream) {
     k_wait_probe<<<1, 32, 0, stream>>>(flag, spins);
     return cudaGetLastError();
@@ -2168,7 +2184,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
             return err;                           \
         }                                         \
     } while (0)
-    const int sms = 152 * 8;
+    const int sms = sm_count() * 8;
     DEFMM_MARK();
     // gather charges into Morton order
     k_gather<C><<<sms, 256, 0, stream>>>(reinterpret_cast<const C*>(q), w.qs, c.perm_s, c.ny, R);

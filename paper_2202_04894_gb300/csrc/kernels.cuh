@@ -123,6 +123,9 @@ constexpr int kNumPhases = 9;  // gather p2p p2m m2m m2f m2l l2l l2p scatter
 // One block waiting, boundedly, on an mbarrier phase nothing completes; raises *flag.
 cudaError_t launch_wait_probe(int* flag, int spins, cudaStream_t stream);
 
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
+
 // Forms the canonical transfer spectra in float64 (Sec. 2.3 Eq. FourierDiagonal).
 cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
                            const double* level_side, int p, int N, int NFpad, double kappa,

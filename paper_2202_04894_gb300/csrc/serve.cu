@@ -98,9 +98,8 @@ cudaError_t apply_with(defmm_plan pl, defmm_workspace ws, const void* q, void* p
     w.nL = pl->hp.nL();
     const defmm::DevTyped<T>& typed = typed_tables(pl, (T*)nullptr);
     int launches = 0;
-    const defmm::LevelList* l2l = nullptr;
-    const defmm::DevCommon c = defmm::apply_tables(pl, &l2l);
-    cudaError_t e = defmm::launch_apply<T>(c, typed, w, pl->m2m.data(), (int)pl->m2m.size(), l2l,
+    // the whole operator whatever the plan's shard setting (documented in defmm_serve.h)
+    cudaError_t e = defmm::launch_apply<T>(pl->common, typed, w, pl->m2m.data(), (int)pl->m2m.size(), pl->l2l.data(),
                                            pl->l2l_par.data(), (int)pl->l2l.size(), q, p, stream, &launches, nullptr);
     ws->launches = launches;
     return e;

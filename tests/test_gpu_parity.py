@@ -245,3 +245,58 @@ def test_box500k_order5_32rhs_sampled_against_direct():
     assert max(errs) <= 2e-3
     one = _gpu(plan, q[:, 17], torch.complex64)
     assert _rel(one, p64[:, 17]) <= TOL64          # a column alone equals the column in the batch
+
+
+def _check_close(got, ref, rel_tol, max_tol, what):
+    rel = _rel(got, ref)
+    worst = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    print("%s: rel-L2 %.3e, max|d|/max|ref| %.3e" % (what, rel, worst))
+    assert rel <= rel_tol, (what, rel)
+    assert worst <= max_tol, (what, worst)
+
+
+SCALE_CASES = [
+    # kind, n, order, leaf: the benchmark's recipe (kappa*D scaled by sqrt(n / 10^6), so the
+    # points per wavelength^2 are the 10^6-point workload's)
+    ("sphere", 40000, 4, 64),
+    ("cube", 12000, 4, 32),
+]
+
+
+@pytest.mark.parametrize("case", SCALE_CASES)
+def test_oracle_parity_at_scale(case):
+    """Tens of thousands of points against the oracle FMM, element by element, on plans
+    large enough to take the paths small cases miss: near-field work units cut at 4,096
+    sources, M2L groups with more chunks than the ring has stages, and M2L blocks of all
+    three size classes (groups of <= 4, 5-7 and 8 siblings)."""
+    kind, n, order, leaf = case
+    X = W.points(kind, n, 2)
+    D = float(np.max(X.max(0) - X.min(0)))
+    kappa = 128.0 * (n / 1e6) ** 0.5 / D
+    q = W.charges(n, 2, nrhs=1)[:, 0]
+    plan = defmm.Plan(X, kappa=kappa, order=order, leaf_size=leaf)
+    ref = oracle_fmm.fmm(X, q, kappa, order=order, leaf=leaf)
+    # the paths this case is there for
+    ul, uo = plan.table("p2p_unit_leaf"), plan.table("p2p_unit_off")
+    rr = plan.table("p2p_unit_ranges").reshape(-1, 2)
+    per_unit = np.add.reduceat(rr[:, 1] - rr[:, 0], uo[:-1])
+    sizes = np.diff(plan.table("grp_member_off"))
+    chunks = np.diff(plan.table("grp_chunk_off"))
+    assert chunks.max() > 3                                  # longer than any ring
+    if kind == "sphere":
+        assert len(ul) > len(np.unique(ul)) and per_unit.max() == 4096   # leaves split into units
+        assert np.any(sizes <= 4) and np.any((sizes >= 5) & (sizes <= 7))
+    else:
+        assert np.any(sizes == 8) and np.any(sizes <= 4)
+    p128 = _gpu(plan, q, torch.complex128)
+    _check_close(p128, ref, TOL128, 1e-11, "%s %d c128" % (kind, n))
+    p64 = _gpu(plan, q, torch.complex64)
+    _check_close(p64, ref, TOL64, 1e-4, "%s %d c64" % (kind, n))
+    # two columns (right-hand-side blocks in M2L, several columns per near-field pass):
+    # the second column is (1 + 2i) q, whose exact image is (1 + 2i) ref
+    q2 = np.stack([q, (1 + 2j) * q], 1)
+    p2 = _gpu(plan, q2, torch.complex64)
+    _check_close(p2[:, 0], ref, TOL64, 1e-4, "%s %d c64 column 0 of 2" % (kind, n))
+    _check_close(p2[:, 1], (1 + 2j) * ref, TOL64, 1e-4, "%s %d c64 column 1 of 2" % (kind, n))
+    assert plan.info()["device_error"] == 0
+    plan.close()
