@@ -216,14 +216,25 @@ defmm_status defmm_apply_noalloc(defmm_plan plan, const void* q, void* p, int nr
  *                   of 4, more in blocks of 8.  Elsewhere 12 and 14 act as 4.
  *                   Kernels without a 4-member variant use 8.
  *                   No output depends on it (bit for bit).
+ *  p2p_reduce_phase - 1: the complex64 near field reduces every phase
+ *                   kappa r / (2 pi) exactly to [-1/2, 1/2] turns before the
+ *                   hardware sine and cosine.  0 (the default): it does so
+ *                   only when some near-field phase of the plan may exceed
+ *                   90 pi (bounded on the host from the near cell pairs), and
+ *                   otherwise gives kappa r to the hardware sine and cosine
+ *                   directly (documented to 2^-20.5 absolute error on
+ *                   [-100 pi, 100 pi]).  Both are single-precision accurate;
+ *                   they round differently.
  * The setting applies to applies enqueued after the call; CUDA graphs
  * captured earlier keep the value they were captured with.
  * Errors: DEFMM_ERR_ARG (NULL plan or tuning, m2l_rhs_block not in
- * {0, 1, 2, 4}, p2p_tc_min_rhs < 0, m2l_members_per_block not in {0, 4, 8, 12, 14}). */
+ * {0, 1, 2, 4}, p2p_tc_min_rhs < 0, m2l_members_per_block not in {0, 4, 8, 12, 14},
+ * p2p_reduce_phase not 0 or 1). */
 typedef struct {
     int m2l_rhs_block;
     int p2p_tc_min_rhs;
     int m2l_members_per_block;
+    int p2p_reduce_phase;
 } defmm_tuning;
 
 defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning);

@@ -304,7 +304,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
             const double kap = hp.ngeo > 1 ? hp.geo_kappa[hp.cell_geo[pr[0]]] : hp.kappa;
             turns = std::max(turns, kap * std::sqrt(d2) / (2 * M_PI));
         }
-        c.p2p_short_phase = turns < 0.45 ? 1 : 0;
+        c.p2p_direct_phase = turns <= 45.0 ? 1 : 0;   // kappa r <= 90 pi
     }
     c.p2m_cells = (const int32_t*)P(o_p2m); c.n_p2m = (int64_t)hp.p2m_cells.size();
     c.l2p_cells = (const int32_t*)P(o_l2p); c.n_l2p = (int64_t)hp.l2p_cells.size();
@@ -553,6 +553,8 @@ defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning) 
     const int rb = tuning->m2l_rhs_block;
     if (rb != 0 && rb != 1 && rb != 2 && rb != 4) return fail(DEFMM_ERR_ARG, "m2l_rhs_block must be 0, 1, 2 or 4");
     if (tuning->p2p_tc_min_rhs < 0) return fail(DEFMM_ERR_ARG, "p2p_tc_min_rhs must be >= 0");
+    if (tuning->p2p_reduce_phase != 0 && tuning->p2p_reduce_phase != 1)
+        return fail(DEFMM_ERR_ARG, "p2p_reduce_phase must be 0 or 1");
     const int mb = tuning->m2l_members_per_block;
     if (mb != 0 && mb != 4 && mb != 8 && mb != 12 && mb != 14)
         return fail(DEFMM_ERR_ARG, "m2l_members_per_block must be 0, 4, 8, 12 or 14");
@@ -560,6 +562,7 @@ defmm_status defmm_plan_set_tuning(defmm_plan plan, const defmm_tuning* tuning) 
     plan->common.m2l_rb = rb;
     plan->common.p2p_tc_min_rhs = tuning->p2p_tc_min_rhs;
     plan->common.m2l_members = mb;
+    plan->common.p2p_reduce_phase = tuning->p2p_reduce_phase;
     return DEFMM_OK;
 }
 
@@ -568,6 +571,7 @@ defmm_status defmm_plan_get_tuning(defmm_plan plan, defmm_tuning* tuning) {
     tuning->m2l_rhs_block = plan->common.m2l_rb;
     tuning->p2p_tc_min_rhs = plan->common.p2p_tc_min_rhs;
     tuning->m2l_members_per_block = plan->common.m2l_members;
+    tuning->p2p_reduce_phase = plan->common.p2p_reduce_phase;
     return DEFMM_OK;
 }
 

@@ -310,21 +310,63 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
 // The leaf's source ranges are read as one concatenated sequence cut into
 // full tiles of 128 (a thread finds its source by binary search in the
 // ranges' prefix offsets), and the next tile is loaded into registers while
-// the current one is consumed.  Coordinates are hi + lo float pairs relative
-// to the cube centre and every difference is formed from both parts: a
-// single float per coordinate, even relative to the leaf, loses too much for
-// near-coincident pairs.  Charges are pre-scaled by 1/(4 pi) when staged;
-// partial sums are reduced over the splits in a fixed order.  REDUCE = false
-// serves plans whose near-field phases all stay below half a turn (kappa = 0,
-// or leaves small against the wavelength): there the phase reduction returns
-// its input unchanged, so skipping it gives the same bits.
+// the current one is consumed.
+// Coordinates: every point is staged relative to a local origin o (the
+// leaf's first target) as a single float v' = (hi - o_hi) + (lo - o_lo), from
+// the hi + lo float pairs relative to the cube centre.  A difference
+// t' - s' then carries an error of about 2^-24 (|t'| + |s'|), small against
+// the distance r except for near-coincident pairs.  Those pairs, 64 r^2 <=
+// |t'|^2 + |s'|^2 (r below about a sixth of |t'| + |s'|, so the single-float
+// difference would keep fewer than about 21 bits), are formed again from the
+// hi + lo pairs, where the difference is accurate to the precision of the
+// difference itself (random clouds hold pairs far closer than the mean
+// spacing, whose 1/r dominates the near field).  Coincident points (r^2 <=
+// eps_self^2, Sec. 5.3) always take that branch (eps_self^2 is folded into
+// the test) and get r^2 = 2^100: their term is below 2^-50 of the charge (zero
+// once damped), nothing at single precision, without a select on every pair.
+// Phase: with REDUCE the phase kappa r / (2 pi) is reduced exactly to
+// [-1/2, 1/2] turns before the hardware sine and cosine on [-pi, pi]; without
+// it (plans whose near-field phases are all below 90 pi, bounded on the host
+// from the cell pairs) the hardware sine and cosine take kappa r directly:
+// PTX documents sin.approx / cos.approx to 2^-20.5 absolute error on
+// [-100 pi, 100 pi], and the rounding of the argument is the same as that of
+// the reduced form.  Charges are pre-scaled by 1/(4 pi) when staged; partial
+// sums are reduced over the splits in a fixed order.
 constexpr int kP2PRanges = kP2PUnitRanges;   // ranges of a work unit, held in shared memory
 
+// v - o for hi + lo pairs, as one float
+__device__ __forceinline__ float3 local_coords(float4 h, float4 l, float4 oh, float4 ol) {
+    return make_float3((h.x - oh.x) + (l.x - ol.x), (h.y - oh.y) + (l.y - ol.y), (h.z - oh.z) + (l.z - ol.z));
+}
+
+// e^{i kappa r} / r (times a staged 1/(4 pi) in the charges) for r^2; kph is
+// kappa / (2 pi) with REDUCE (phase in turns), else kappa (phase in radians)
+template <bool DAMP, bool REDUCE>
+__device__ __forceinline__ float2 near_kernel(float r2, float kph, float lam2) {
+    float rinv = rsqrt_hw(r2);
+    const float r = r2 * rinv;
+    float sn, cs;
+    if (REDUCE) turns_sincos(r * kph, &sn, &cs);
+    else sincos_hw(r * kph, &sn, &cs);
+    if (DAMP) rinv *= ex2_hw(-lam2 * r);
+    return make_float2(cs * rinv, sn * rinv);
+}
+
+// r^2 of a near-coincident pair from the hi + lo pairs; 2^100 for coincident points
+__device__ __forceinline__ float exact_r2(float4 th, float4 tl, float4 sh, float4 sl, float eps2) {
+    const float dx = (th.x - sh.x) + (tl.x - sl.x);
+    const float dy = (th.y - sh.y) + (tl.y - sl.y);
+    const float dz = (th.z - sh.z) + (tl.z - sl.z);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    return r2 > eps2 ? r2 : 0x1p100f;
+}
+
 template <int RB, bool DAMP = false, bool REDUCE = true>
-__global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __restrict__ qs,
+__global__ void __launch_bounds__(128, RB == 1 ? 8 : 1) k_p2p_f32(DevCommon c, const float2* __restrict__ qs,
                                                  float2* __restrict__ part, int R, int rb0) {
-    __shared__ float4 sa[128];   // hi x, y, z and Re q / (4 pi)   (RB == 1)
-    __shared__ float4 sb[128];   // lo x, y, z and Im q / (4 pi)
+    __shared__ float4 sa[128];   // source relative to the local origin; w: |s'|^2 + 64 eps_self^2
+    __shared__ float4 sh[128];   // hi x, y, z relative to the cube centre
+    __shared__ float4 sl[128];   // lo x, y, z
     __shared__ float2 sq[RB][128];
     __shared__ float2 red[RB][128];
     __shared__ int rbeg[kP2PRanges], roff[kP2PRanges + 1];
@@ -333,10 +375,12 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
     const int nr = min(RB, R - rb0);
-    const float kap2pi = (float)(kappa_of(c, cell) * kInv2Pi);
+    const float kph = (float)(REDUCE ? kappa_of(c, cell) * kInv2Pi : kappa_of(c, cell));
     const float eps2 = (float)(eps_of(c, cell) * eps_of(c, cell));
+    const float e64 = 64.f * eps2;
     const float inv4pi = (float)kInv4Pi;
     const float lam2 = (float)(c.damping * kLog2E);     // damping in powers of 2 per unit length
+    const float4 oh = c.Xh[tb], ol = c.Xl[tb];          // local origin: the leaf's first target
     const int r0 = c.p2p_unit_off[u], r1 = c.p2p_unit_off[u + 1];
     for (int t0 = tb; t0 < te; t0 += 256) {
         // two targets per thread: target pairs (2i, 2i+1) x source splits
@@ -347,12 +391,13 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
         const bool active = sj < splits;
         const int ia = 2 * ti, ib = 2 * ti + 1;
         const bool has_b = ib < nt;
-        float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh, yh = xh, yl = xh;
+        float3 ta = make_float3(0.f, 0.f, 0.f), tb3 = ta;
         if (active) {
-            xh = c.Xh[t0 + ia]; xl = c.Xl[t0 + ia];
-            if (has_b) { yh = c.Xh[t0 + ib]; yl = c.Xl[t0 + ib]; }
-            else { yh = xh; yl = xl; }
+            ta = local_coords(c.Xh[t0 + ia], c.Xl[t0 + ia], oh, ol);
+            tb3 = has_b ? local_coords(c.Xh[t0 + ib], c.Xl[t0 + ib], oh, ol) : ta;
         }
+        const float na2 = fmaf(ta.x, ta.x, fmaf(ta.y, ta.y, ta.z * ta.z));
+        const float nb2 = fmaf(tb3.x, tb3.x, fmaf(tb3.y, tb3.y, tb3.z * tb3.z));
         float2 acc[RB], bcc[RB];
 #pragma unroll
         for (int r = 0; r < RB; ++r) { acc[r] = make_float2(0.f, 0.f); bcc[r] = make_float2(0.f, 0.f); }
@@ -374,13 +419,13 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
                 }
                 return rbeg[lo] + (f - roff[lo]);
             };
-            float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+            float4 nh = make_float4(0.f, 0.f, 0.f, 0.f), nl = nh;
             float2 nq[RB];
             auto fetch = [&](int f0) {
                 if (f0 + (int)threadIdx.x < total) {
                     const int64_t j = source_of(f0 + threadIdx.x);
-                    na = c.Yh[j];
-                    nb = c.Yl[j];
+                    nh = c.Yh[j];
+                    nl = c.Yl[j];
 #pragma unroll
                     for (int r = 0; r < RB; ++r)
                         nq[r] = r < nr ? qs[(int64_t)(rb0 + r) * c.ny + j] : make_float2(0.f, 0.f);
@@ -391,63 +436,43 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
                 const int ns = min(128, total - f0);
                 __syncthreads();                 // previous tile consumed
                 if (threadIdx.x < ns) {
-                    float4 a = na, b = nb;
-                    if (RB == 1) {
-                        a.w = nq[0].x * inv4pi;
-                        b.w = nq[0].y * inv4pi;
-                    } else {
+                    const float3 s = local_coords(nh, nl, oh, ol);
+                    sa[threadIdx.x] = make_float4(s.x, s.y, s.z, fmaf(s.x, s.x, fmaf(s.y, s.y, fmaf(s.z, s.z, e64))));
+                    sh[threadIdx.x] = nh;
+                    sl[threadIdx.x] = nl;
 #pragma unroll
-                        for (int r = 0; r < RB; ++r) sq[r][threadIdx.x] = make_float2(nq[r].x * inv4pi, nq[r].y * inv4pi);
-                    }
-                    sa[threadIdx.x] = a;
-                    sb[threadIdx.x] = b;
+                    for (int r = 0; r < RB; ++r) sq[r][threadIdx.x] = make_float2(nq[r].x * inv4pi, nq[r].y * inv4pi);
                 }
                 __syncthreads();
                 if (f0 + 128 < total) fetch(f0 + 128);   // in flight during the compute below
                 if (active) {
                     for (int k = sj; k < ns; k += splits) {
-                        const float4 a = sa[k], b = sb[k];
-                        float2 ga, gb;
+                        const float4 s = sa[k];
+                        float ra, rb;
                         {
-                            const float dx = (xh.x - a.x) + (xl.x - b.x);
-                            const float dy = (xh.y - a.y) + (xl.y - b.y);
-                            const float dz = (xh.z - a.z) + (xl.z - b.z);
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            float rinv = rsqrt_hw(r2);
-                            rinv = r2 > eps2 ? rinv : 0.f;
-                            float sn, cs;
-                            if (REDUCE) turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
-                            else sincos_hw(6.28318530717958647692f * (r2 * rinv * kap2pi), &sn, &cs);
-                            if (DAMP) rinv *= ex2_hw(-lam2 * (r2 * rinv));
-                            ga = make_float2(cs * rinv, sn * rinv);
+                            const float dx = ta.x - s.x, dy = ta.y - s.y, dz = ta.z - s.z;
+                            ra = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         }
                         {
-                            const float dx = (yh.x - a.x) + (yl.x - b.x);
-                            const float dy = (yh.y - a.y) + (yl.y - b.y);
-                            const float dz = (yh.z - a.z) + (yl.z - b.z);
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            float rinv = rsqrt_hw(r2);
-                            rinv = r2 > eps2 ? rinv : 0.f;
-                            float sn, cs;
-                            if (REDUCE) turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
-                            else sincos_hw(6.28318530717958647692f * (r2 * rinv * kap2pi), &sn, &cs);
-                            if (DAMP) rinv *= ex2_hw(-lam2 * (r2 * rinv));
-                            gb = make_float2(cs * rinv, sn * rinv);
+                            const float dx = tb3.x - s.x, dy = tb3.y - s.y, dz = tb3.z - s.z;
+                            rb = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         }
-                        if (RB == 1) {
-                            acc[0].x = fmaf(ga.x, a.w, fmaf(-ga.y, b.w, acc[0].x));
-                            acc[0].y = fmaf(ga.x, b.w, fmaf(ga.y, a.w, acc[0].y));
-                            bcc[0].x = fmaf(gb.x, a.w, fmaf(-gb.y, b.w, bcc[0].x));
-                            bcc[0].y = fmaf(gb.x, b.w, fmaf(gb.y, a.w, bcc[0].y));
-                        } else {
+                        // near-coincident (or coincident) pairs, rare: the difference again from hi + lo
+                        const bool ca = fmaf(ra, 64.f, -s.w) <= na2, cb = fmaf(rb, 64.f, -s.w) <= nb2;
+                        if (__builtin_expect(ca || cb, 0)) {
+                            const float4 h = sh[k], l = sl[k];
+                            if (ca) ra = exact_r2(c.Xh[t0 + ia], c.Xl[t0 + ia], h, l, eps2);
+                            if (cb) rb = exact_r2(c.Xh[t0 + (has_b ? ib : ia)], c.Xl[t0 + (has_b ? ib : ia)], h, l, eps2);
+                        }
+                        const float2 ga = near_kernel<DAMP, REDUCE>(ra, kph, lam2);
+                        const float2 gb = near_kernel<DAMP, REDUCE>(rb, kph, lam2);
 #pragma unroll
-                            for (int r = 0; r < RB; ++r) {
-                                const float2 q = sq[r][k];
-                                acc[r].x = fmaf(ga.x, q.x, fmaf(-ga.y, q.y, acc[r].x));
-                                acc[r].y = fmaf(ga.x, q.y, fmaf(ga.y, q.x, acc[r].y));
-                                bcc[r].x = fmaf(gb.x, q.x, fmaf(-gb.y, q.y, bcc[r].x));
-                                bcc[r].y = fmaf(gb.x, q.y, fmaf(gb.y, q.x, bcc[r].y));
-                            }
+                        for (int r = 0; r < RB; ++r) {
+                            const float2 q = sq[r][k];
+                            acc[r].x = fmaf(ga.x, q.x, fmaf(-ga.y, q.y, acc[r].x));
+                            acc[r].y = fmaf(ga.x, q.y, fmaf(ga.y, q.x, acc[r].y));
+                            bcc[r].x = fmaf(gb.x, q.x, fmaf(-gb.y, q.y, bcc[r].x));
+                            bcc[r].y = fmaf(gb.x, q.y, fmaf(gb.y, q.x, bcc[r].y));
                         }
                     }
                 }
@@ -475,6 +500,15 @@ __global__ void __launch_bounds__(128) k_p2p_f32(DevCommon c, const float2* __re
             }
         __syncthreads();
     }
+}
+
+template <bool DAMP, bool REDUCE>
+void launch_p2p_f32(int rb, unsigned nu, const DevCommon& c, const float2* qs, float2* part, int R, int rb0,
+                    cudaStream_t stream) {
+    if (rb == 1) k_p2p_f32<1, DAMP, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
+    else if (rb == 16) k_p2p_f32<16, DAMP, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
+    else if (rb == 8) k_p2p_f32<8, DAMP, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
+    else k_p2p_f32<4, DAMP, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
 }
 
 // Sums each target's partial near-field sums over its leaf's work units, in
@@ -1743,8 +1777,8 @@ cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, 
 //   D[(r, im), t] = sum_s Qi[s,r] Gr[t,s] + Qr[s,r] Gi[t,s],
 // A = [[Qr, -Qi], [Qi, Qr]] interleaved per source (K index 2s + part),
 // B[(s, part), t] = (Gr, Gi)[t, s].  The kernel values G are formed on the
-// CUDA cores exactly as in k_p2p_f32 (hi + lo coordinates, reduced phase)
-// once per interaction for all 32 columns.  Each operand is split into a tf32
+// CUDA cores from the hi + lo coordinates of every pair with the reduced
+// phase, once per interaction for all 32 columns.  Each operand is split into a tf32
 // head and a tail (x = hi + lo, hi = tf32 rounding of x) and the three
 // products lo*hi + hi*lo + hi*hi of a tile of 16 sources are summed in f32 in
 // tensor memory (tf32 alone would leave ~1e-4 relative error).  The tensor
@@ -2209,18 +2243,13 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         if (c.n_p2p_units == 0) break;
         if constexpr (std::is_same<T, float>::value) {
             const unsigned nu = (unsigned)c.n_p2p_units;
+            const bool direct = c.p2p_direct_phase && !c.p2p_reduce_phase;
             if (c.damping > 0.0) {
-                if (R == 1 && c.p2p_short_phase) k_p2p_f32<1, true, false><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-                else if (R == 1) k_p2p_f32<1, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-                else if (p2p_rb == 16) k_p2p_f32<16, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-                else if (p2p_rb == 8) k_p2p_f32<8, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-                else k_p2p_f32<4, true><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                if (direct) launch_p2p_f32<true, false>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
+                else launch_p2p_f32<true, true>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
             } else {
-                if (R == 1 && c.p2p_short_phase) k_p2p_f32<1, false, false><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-                else if (R == 1) k_p2p_f32<1><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-                else if (p2p_rb == 16) k_p2p_f32<16><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-                else if (p2p_rb == 8) k_p2p_f32<8><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
-                else k_p2p_f32<4><<<nu, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);
+                if (direct) launch_p2p_f32<false, false>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
+                else launch_p2p_f32<false, true>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
             }
         } else {
             if (R == 1) k_p2p<T, 1><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);

@@ -54,9 +54,10 @@ struct DevCommon {
     int m2l_rb;               // right-hand sides per M2L pass (0: chosen from nrhs and N)
     int m2l_members;          // members per M2L block: 4, 8, 12 (4 or 8 by group size), 14 (4, 7
                               // or 8 by group size), 0 (default)
-    int p2p_short_phase;      // 1: every near-field phase kappa r / (2 pi) is below 0.45 turns
-                              // (bounded on the host from the P2P cell pairs), so the phase
-                              // reduction is the identity and the kernel skips it
+    int p2p_direct_phase;     // 1: every near-field phase kappa r is at most 90 pi (bounded on the
+                              // host from the P2P cell pairs), within the range where the hardware
+                              // sine and cosine are documented accurate without a reduction
+    int p2p_reduce_phase;     // tuning: 1 reduces the phase exactly whatever the bound
     int p2p_tc_min_rhs;       // complex64 applies with at least this many columns use the
                               // tensor-core near field (0: never)
     const int32_t* p2m_cells;  int64_t n_p2m;

@@ -256,7 +256,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
         defmm_plan pl = nullptr;
         defmm_status s = defmm_plan_create(X, nx, Y, ny, kappa, order, hit.leaf, &oc, stream, &pl);
         if (s != DEFMM_OK) return s;
-        defmm_tuning tn{hit.rb, hit.tc ? 1 : 0, hit.mem};
+        defmm_tuning tn{hit.rb, hit.tc ? 1 : 0, hit.mem, 0};
         s = defmm_plan_set_tuning(pl, &tn);
         if (s != DEFMM_OK) { defmm_destroy(pl); return s; }
         res.leaf_size = hit.leaf; res.fft_n = hit.fft_n; res.m2l_rhs_block = hit.rb; res.p2p_tensor_cores = hit.tc;
@@ -302,7 +302,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
             if (s != DEFMM_OK) { if (best) defmm_destroy(best); return s; }
             bool kept = false;
             for (const Launch& lc : launches) {
-                defmm_tuning tn{lc.rb, lc.tc ? 1 : 0, lc.mem};
+                defmm_tuning tn{lc.rb, lc.tc ? 1 : 0, lc.mem, 0};
                 s = defmm_plan_set_tuning(pl, &tn);
                 double ms = 0;
                 if (s == DEFMM_OK) s = time_applies(pl, b, t.nrhs, t.dtype, t.reps, st, &ms);
@@ -326,7 +326,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
         }
     }
     if (!best) return defmm::set_error(DEFMM_ERR_OOM, "autotune: no candidate fits the device or hbm_budget");
-    defmm_tuning tn{bc.rb, bc.tc ? 1 : 0, bc.mem};
+    defmm_tuning tn{bc.rb, bc.tc ? 1 : 0, bc.mem, 0};
     defmm_status s = defmm_plan_set_tuning(best, &tn);
     if (s != DEFMM_OK) { defmm_destroy(best); return s; }
     if (!cache_store(t.cache_path, key.h, bc)) {

@@ -52,7 +52,7 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("m2l_rhs_block", ctypes.c_int), ("p2p_tc_min_rhs", ctypes.c_int),
-                ("m2l_members_per_block", ctypes.c_int)]
+                ("m2l_members_per_block", ctypes.c_int), ("p2p_reduce_phase", ctypes.c_int)]
 
 
 class TuneOptions(ctypes.Structure):
@@ -242,16 +242,17 @@ class Plan:
         _check(lib().defmm_profile_read(self._h, buf, len(PHASES), ctypes.byref(n)))
         return {PHASES[i]: buf[i] for i in range(n.value)}
 
-    def set_tuning(self, m2l_rhs_block: int = 0, p2p_tc_min_rhs: int = 0, m2l_members_per_block: int = 0):
+    def set_tuning(self, m2l_rhs_block: int = 0, p2p_tc_min_rhs: int = 0, m2l_members_per_block: int = 0,
+                   p2p_reduce_phase: int = 0):
         """defmm_plan_set_tuning: launch choices of later applies."""
-        t = Tuning(int(m2l_rhs_block), int(p2p_tc_min_rhs), int(m2l_members_per_block))
+        t = Tuning(int(m2l_rhs_block), int(p2p_tc_min_rhs), int(m2l_members_per_block), int(p2p_reduce_phase))
         _check(lib().defmm_plan_set_tuning(self._h, ctypes.byref(t)))
 
     def tuning(self) -> dict:
         t = Tuning()
         _check(lib().defmm_plan_get_tuning(self._h, ctypes.byref(t)))
         return {"m2l_rhs_block": t.m2l_rhs_block, "p2p_tc_min_rhs": t.p2p_tc_min_rhs,
-                "m2l_members_per_block": t.m2l_members_per_block}
+                "m2l_members_per_block": t.m2l_members_per_block, "p2p_reduce_phase": t.p2p_reduce_phase}
 
     def gmres(self, b, x0=None, shift=1.0, tol=1e-6, restart=30, max_iter=200, stream=None):
         """defmm_gmres: solves (shift I + A) x = b on the GPU.  b: complex64/complex128

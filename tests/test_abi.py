@@ -93,11 +93,16 @@ def test_argument_errors():
 def test_tuning_values():
     """Apply-time tuning takes 0, 1, 2, 4 right-hand sides per M2L pass and rejects others."""
     pl = _host_plan(W.points("sphere", 300, 2), kappa=2.0, order=4, leaf_size=16)
-    assert pl.tuning() == {"m2l_rhs_block": 0, "p2p_tc_min_rhs": 0, "m2l_members_per_block": 0}
+    assert pl.tuning() == {"m2l_rhs_block": 0, "p2p_tc_min_rhs": 0, "m2l_members_per_block": 0,
+                           "p2p_reduce_phase": 0}
     for v in (1, 2, 4, 0):
-        pl.set_tuning(m2l_rhs_block=v, p2p_tc_min_rhs=v, m2l_members_per_block=v if v in (0, 4) else 8)
+        pl.set_tuning(m2l_rhs_block=v, p2p_tc_min_rhs=v, m2l_members_per_block=v if v in (0, 4) else 8,
+                      p2p_reduce_phase=v % 2)
         assert pl.tuning() == {"m2l_rhs_block": v, "p2p_tc_min_rhs": v,
-                               "m2l_members_per_block": v if v in (0, 4) else 8}
+                               "m2l_members_per_block": v if v in (0, 4) else 8, "p2p_reduce_phase": v % 2}
+    with pytest.raises(defmm.DefmmError) as e:
+        pl.set_tuning(p2p_reduce_phase=2)
+    assert e.value.status == 1
     for v in (12, 14):
         pl.set_tuning(m2l_members_per_block=v)
         assert pl.tuning()["m2l_members_per_block"] == v

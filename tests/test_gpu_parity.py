@@ -300,3 +300,22 @@ def test_oracle_parity_at_scale(case):
     _check_close(p2[:, 1], (1 + 2j) * ref, TOL64, 1e-4, "%s %d c64 column 1 of 2" % (kind, n))
     assert plan.info()["device_error"] == 0
     plan.close()
+
+
+@pytest.mark.parametrize("kd", [120.0, 200.0])
+def test_near_field_phase_forms(kd):
+    """The complex64 near field with the phase given to the hardware sine and cosine
+    directly (every near-field phase below 90 pi: kappa*D = 120 here, up to ~208 rad)
+    and with the exact reduction to [-1/2, 1/2] turns (kappa*D = 200: phases up to
+    ~346 rad, where the library must reduce), both against the oracle FMM."""
+    X = W.points("sphere", 6000, 31)
+    D = float(np.max(X.max(0) - X.min(0)))
+    kappa = kd / D
+    q = W.charges(len(X), 32, nrhs=1)[:, 0]
+    plan = defmm.Plan(X, kappa=kappa, order=4, leaf_size=32)
+    ref = oracle_fmm.fmm(X, q, kappa, order=4, leaf=32)
+    for reduce_phase in (0, 1):
+        plan.set_tuning(p2p_reduce_phase=reduce_phase)
+        p64 = _gpu(plan, q, torch.complex64)
+        _check_close(p64, ref, TOL64, 1e-4, "kD %g reduce %d c64" % (kd, reduce_phase))
+    plan.close()
