@@ -487,6 +487,8 @@ def main():
                 "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                 "rel_l2_c64_vs_c128": rel, "rel_l2_vs_oracle": vs_oracle and vs_oracle["rel_l2"],
                 "vs_oracle": vs_oracle, "phase_ms": phase_avg, "plan_s": plan_s,
+                "plan_ms": {"front_device": info["plan_front_device_ms"], "front_wall": info["plan_front_ms"],
+                            "host_rest": info["plan_host_ms"], "upload_and_spectra": info["plan_upload_ms"]},
                 "fp64_gpu_apply": {"ms": fp64_ms, "value": units / (fp64_ms * 1e-3) / 1e6, "unit": UNIT,
                                    "speedup_of_c64": fp64_ms / ms_per_step},
                 "plan": {k: info[k] for k in ("n_m2l_pairs", "n_p2p_pairs", "n_multipole", "n_local", "n_fourier",

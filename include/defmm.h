@@ -381,6 +381,13 @@ typedef struct {
                                          synchronises with the device to read it */
     double d_aabb;                    /* side of the smallest box holding X, Y */
     double cube_side;                 /* side of the octree root */
+    /* plan creation time (ms): the trees, the dual tree traversal, the best
+       directions and the Alg. 2 marks, built on the device (device time from
+       CUDA events, and the wall time of that step with its copies); the rest
+       of the construction on the host; the upload of the tables with the
+       spectra formed on the device.  Host-only plans build everything on the
+       host (front times 0).                                                  */
+    double plan_front_device_ms, plan_front_ms, plan_host_ms, plan_upload_ms;
 } defmm_info;
 
 defmm_status defmm_plan_info(defmm_plan plan, defmm_info* out);

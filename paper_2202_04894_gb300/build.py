@@ -24,6 +24,7 @@ SOURCES = [
     ("plan.cpp", "g++"),
     ("persist.cpp", "g++"),
     ("kernels.cu", "nvcc"),
+    ("plan_gpu.cu", "nvcc"),
     ("capi.cu", "nvcc"),
     ("noalloc.cu", "nvcc"),
     ("serve.cu", "nvcc"),

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@
 #include "defmm.h"
 #include "kernels.cuh"
 #include "plan.h"
+#include "plan_gpu.h"
 #include "plan_state.h"
 
 namespace defmm {
@@ -604,8 +606,22 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
     if (s == DEFMM_OK && !same) s = read_points(Y, ny, hy, host_only);
     if (s != DEFMM_OK) { delete pl; return s; }
     try {
-        build_host_plan(hx.data(), nx, same ? nullptr : hy.data(), same ? nx : ny, kappa, order, leaf_size, o.eta,
-                        o.hf_kw, o.fft_n, o.self_eps, o.m2l_chunk_blocks, pl->hp);
+        // trees, traversal, directions and Alg. 2 marks on the device unless the plan is host-only
+        const double* yp = same ? nullptr : hy.data();
+        const int64_t nyy = same ? nx : ny;
+        const auto t0 = std::chrono::steady_clock::now();
+        double dev_ms = 0, front_ms = 0;
+        FrontEnd front = [&](HostPlan& hp) {
+            const auto f0 = std::chrono::steady_clock::now();
+            device_front(hx.data(), nx, yp, nyy, leaf_size, hp, (cudaStream_t)stream, &dev_ms);
+            front_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - f0).count();
+        };
+        build_host_plan(hx.data(), nx, yp, nyy, kappa, order, leaf_size, o.eta, o.hf_kw, o.fft_n, o.self_eps,
+                        o.m2l_chunk_blocks, pl->hp, host_only ? nullptr : &front);
+        const double all_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        pl->front_device_ms = dev_ms;
+        pl->front_ms = front_ms;
+        pl->host_ms = all_ms - front_ms;
     } catch (const std::bad_alloc&) {
         delete pl;
         return fail(DEFMM_ERR_OOM, "host allocation while building the plan");
@@ -615,7 +631,11 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
     }
     pl->hp.damping = o.damping;
     pl->host_only = host_only;
-    s = host_only ? DEFMM_OK : upload(pl, hx, hy, (cudaStream_t)stream);
+    {
+        const auto u0 = std::chrono::steady_clock::now();
+        s = host_only ? DEFMM_OK : upload(pl, hx, hy, (cudaStream_t)stream);
+        pl->upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - u0).count();
+    }
     if (s != DEFMM_OK) {
         cudaFree(pl->arena);
         delete pl;
@@ -660,8 +680,15 @@ defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int
             std::vector<double> hx;
             defmm_status s = read_points(X[g], nx[g], hx, host_only);
             if (s != DEFMM_OK) { delete pl; return s; }
+            const double* xp = hx.data();
+            const int64_t ng = nx[g];
+            FrontEnd front = [&](HostPlan& hp) {
+                double ms = 0;
+                device_front(xp, ng, nullptr, ng, leaf_size, hp, (cudaStream_t)stream, &ms);
+                pl->front_device_ms += ms;
+            };
             build_host_plan(hx.data(), nx[g], nullptr, nx[g], kappa[g], order, leaf_size, o.eta, o.hf_kw, o.fft_n,
-                            o.self_eps, o.m2l_chunk_blocks, parts[g]);
+                            o.self_eps, o.m2l_chunk_blocks, parts[g], host_only ? nullptr : &front);
             parts[g].damping = o.damping;
             all.insert(all.end(), hx.begin(), hx.end());
         }
@@ -841,6 +868,10 @@ defmm_status defmm_plan_info(defmm_plan plan, defmm_info* out) {
     }
     out->d_aabb = hp.d_aabb;
     out->cube_side = hp.side;
+    out->plan_front_device_ms = plan->front_device_ms;
+    out->plan_front_ms = plan->front_ms;
+    out->plan_host_ms = plan->host_ms;
+    out->plan_upload_ms = plan->upload_ms;
     return DEFMM_OK;
 }
 

@@ -22,15 +22,23 @@ double Levels::radius(int l) const { return std::sqrt(3.0) / 2 * side(l); }
 
 // Strict MAC (footnote of Sec. 3.2) at low frequency, directional MAC
 // max(kappa w^2, 2w) <= eta dist (Eq. macdirref, Sec. 4.2.2) at high frequency.
+// The directional MAC reads A^2 <= F * S with S the integer squared gap.
+void Levels::mac_terms(int l, double* A2, double* F) const {
+    const double w = radius(l);
+    const double A = std::max(kappa * w * w, 2 * w);
+    const double s = side(l);
+    *A2 = A * A;
+    *F = eta * eta * s * s;
+}
+
 bool Levels::mac(int l, int64_t kx, int64_t ky, int64_t kz) const {
     int64_t ax = kx < 0 ? -kx : kx, ay = ky < 0 ? -ky : ky, az = kz < 0 ? -kz : kz;
     if (hf[l]) {
         int64_t gx = ax > 1 ? ax - 1 : 0, gy = ay > 1 ? ay - 1 : 0, gz = az > 1 ? az - 1 : 0;
         int64_t S = gx * gx + gy * gy + gz * gz;
-        double w = radius(l);
-        double A = std::max(kappa * w * w, 2 * w);
-        double s = side(l);
-        return A * A <= eta * eta * s * s * (double)S;
+        double A2, F;
+        mac_terms(l, &A2, &F);
+        return A2 <= F * (double)S;
     }
     return std::max(ax, std::max(ay, az)) >= 2;
 }
@@ -207,6 +215,53 @@ static void sort_unique(std::vector<int32_t>& v) {
     v.erase(std::unique(v.begin(), v.end()), v.end());
 }
 
+// Alg. 1 from (root, root), breadth first: the pairs of one level in order,
+// each giving an M2L pair (with its best direction), a P2P pair or its son
+// pairs in (a, b) order for the next level; then the marks of Alg. 2 (the
+// directions of each cell's M2L pairs).
+static void dual_tree_traversal(HostPlan& hp) {
+    const Tree& tt = hp.tt;
+    const Tree& ts = hp.ts();
+    const Levels& lv = hp.lv;
+    std::unordered_map<int64_t, int32_t> dir_memo;
+    auto pair_dir = [&](int l, int64_t kx, int64_t ky, int64_t kz) -> int32_t {
+        if (!lv.hf[l]) return -1;
+        int64_t key = ((((int64_t)l * 4096 + (kx + 2048)) * 4096) + (ky + 2048)) * 4096 + (kz + 2048);
+        auto it = dir_memo.find(key);
+        if (it != dir_memo.end()) return it->second;
+        int32_t u = (int32_t)best_direction(lv.E(l), kx, ky, kz);
+        dir_memo[key] = u;
+        return u;
+    };
+    std::vector<std::array<int32_t, 2>> cur = {{0, 0}}, next;
+    while (!cur.empty()) {
+        next.clear();
+        for (const auto& pr : cur) {
+            const int32_t t = pr[0], s = pr[1];
+            const int l = tt.level[t];
+            const int64_t kx = (int64_t)tt.ix[t] - ts.ix[s], ky = (int64_t)tt.iy[t] - ts.iy[s],
+                          kz = (int64_t)tt.iz[t] - ts.iz[s];
+            if (lv.mac(l, kx, ky, kz)) {
+                hp.m2l.push_back({t, s, pair_dir(l, kx, ky, kz)});
+            } else if (tt.leaf(t) || ts.leaf(s)) {
+                hp.p2p.push_back({t, s});
+            } else {
+                for (int32_t a = 0; a < tt.nchild[t]; ++a)
+                    for (int32_t b = 0; b < ts.nchild[s]; ++b)
+                        next.push_back({tt.first_child[t] + a, ts.first_child[s] + b});
+            }
+        }
+        cur.swap(next);
+    }
+    hp.marks_t.assign(tt.ncell(), {});
+    hp.marks_s.assign(ts.ncell(), {});
+    for (auto& pr : hp.m2l)
+        if (pr[2] >= 0) {
+            hp.marks_t[pr[0]].push_back(pr[2]);
+            hp.marks_s[pr[1]].push_back(pr[2]);
+        }
+}
+
 // ---------------------------------------------------------------- plan
 template <typename U> static bool units_for_leaf_empty(const std::vector<U>& units, int32_t li) {
     return units.empty() || units.back().leaf != li;
@@ -214,7 +269,7 @@ template <typename U> static bool units_for_leaf_empty(const std::vector<U>& uni
 
 void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa,
                      int order, int leaf, double eta, double hf_kw, int fft_n, double self_eps,
-                     int chunk_blocks, HostPlan& hp) {
+                     int chunk_blocks, HostPlan& hp, const FrontEnd* front) {
     if (nx < 1 || ny < 1) throw std::runtime_error("nx and ny must be >= 1");
     if (order < 2 || order > kMaxOrder) throw std::runtime_error("order must be in [2, 8]");
     if (leaf < 1) throw std::runtime_error("leaf_size must be >= 1");
@@ -254,10 +309,6 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
     for (int a = 0; a < 3; ++a) hp.corner[a] = (lo[a] + hi[a]) / 2.0 - hp.side / 2.0;
     hp.eps_self = self_eps * d;
 
-    build_tree(X, nx, hp.corner, hp.side, leaf, hp.tt);
-    if (Y) build_tree(Y, ny, hp.corner, hp.side, leaf, hp.ts_own);
-    const Tree& tt = hp.tt;
-    const Tree& ts = hp.ts();
 
     Levels& lv = hp.lv;
     lv.side0 = hp.side; lv.kappa = kappa; lv.eta = eta; lv.hf_kw = hf_kw;
@@ -270,47 +321,17 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
     if (lv.l_hf >= 0 && lv.l_hf > 12)
         throw std::runtime_error("kappa*D too large: more than 12 high-frequency levels");
 
-    // ---- Alg. 1: dual tree traversal from (root, root)
-    std::unordered_map<int64_t, int32_t> dir_memo;
-    auto pair_dir = [&](int l, int64_t kx, int64_t ky, int64_t kz) -> int32_t {
-        if (!lv.hf[l]) return -1;
-        int64_t key = ((((int64_t)l * 4096 + (kx + 2048)) * 4096) + (ky + 2048)) * 4096 + (kz + 2048);
-        auto it = dir_memo.find(key);
-        if (it != dir_memo.end()) return it->second;
-        int32_t u = (int32_t)best_direction(lv.E(l), kx, ky, kz);
-        dir_memo[key] = u;
-        return u;
-    };
-    // depth first from (root, root) with an explicit stack; son pairs are
-    // pushed in reverse so that they are visited in (a, b) order
-    std::vector<std::array<int32_t, 2>> stack = {{0, 0}};
-    while (!stack.empty()) {
-        const int32_t t = stack.back()[0], s = stack.back()[1];
-        stack.pop_back();
-        int l = tt.level[t];
-        int64_t kx = (int64_t)tt.ix[t] - ts.ix[s], ky = (int64_t)tt.iy[t] - ts.iy[s],
-                kz = (int64_t)tt.iz[t] - ts.iz[s];
-        if (lv.mac(l, kx, ky, kz)) {
-            hp.m2l.push_back({t, s, pair_dir(l, kx, ky, kz)});
-            continue;
-        }
-        if (tt.leaf(t) || ts.leaf(s)) {
-            hp.p2p.push_back({t, s});
-            continue;
-        }
-        for (int32_t a = tt.nchild[t] - 1; a >= 0; --a)
-            for (int32_t b = ts.nchild[s] - 1; b >= 0; --b)
-                stack.push_back({tt.first_child[t] + a, ts.first_child[s] + b});
+    if (front) {
+        (*front)(hp);   // trees, traversal, directions and Alg. 2 marks built elsewhere (the device)
+    } else {
+        build_tree(X, nx, hp.corner, hp.side, leaf, hp.tt);
+        if (Y) build_tree(Y, ny, hp.corner, hp.side, leaf, hp.ts_own);
+        dual_tree_traversal(hp);
     }
+    const Tree& tt = hp.tt;
+    const Tree& ts = hp.ts();
 
-    // ---- Alg. 2 marks + Alg. 3 blank downward pass on both trees
-    hp.marks_t.assign(tt.ncell(), {});
-    hp.marks_s.assign(ts.ncell(), {});
-    for (auto& pr : hp.m2l)
-        if (pr[2] >= 0) {
-            hp.marks_t[pr[0]].push_back(pr[2]);
-            hp.marks_s[pr[1]].push_back(pr[2]);
-        }
+    // ---- Alg. 3 blank downward pass on both trees (the marks of Alg. 2 are in place)
     auto downward = [&](const Tree& tr, std::vector<std::vector<int32_t>>& marks) {
         for (int32_t c = 0; c < tr.ncell(); ++c) {
             int l = tr.level[c];

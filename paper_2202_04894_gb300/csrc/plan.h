@@ -9,6 +9,7 @@
 
 #include <array>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -37,6 +38,7 @@ struct Levels {
     double side(int l) const;
     double radius(int l) const;
     bool mac(int l, int64_t kx, int64_t ky, int64_t kz) const;
+    void mac_terms(int l, double* A2, double* F) const;   // directional MAC: A2 <= F * S
     int E(int l) const { return l_hf - l; }
 };
 
@@ -166,10 +168,18 @@ void save_plan_file(const std::string& path, const HostPlan& hp, const std::vect
                     const std::vector<double>& Y);
 void load_plan_file(const std::string& path, HostPlan& hp, std::vector<double>& X, std::vector<double>& Y);
 
+// A replacement for the trees, the dual tree traversal and the marks of
+// Alg. 2: given hp with its cube and levels set, fills hp.tt (hp.ts_own),
+// hp.m2l, hp.p2p, hp.marks_t and hp.marks_s as the host construction would
+// (the marks may already be deduplicated).
+using FrontEnd = std::function<void(HostPlan&)>;
+
 // Builds everything above from host coordinates (Y == nullptr: same tree).
+// The traversal is breadth first: pairs of a level in order, son pairs in
+// (a, b) order.  With `front`, the trees, traversal and marks come from it.
 // Throws std::runtime_error with a message on invalid input.
 void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa,
                      int order, int leaf, double eta, double hf_kw, int fft_n, double self_eps,
-                     int chunk_blocks, HostPlan& hp);
+                     int chunk_blocks, HostPlan& hp, const FrontEnd* front = nullptr);
 
 }  // namespace defmm

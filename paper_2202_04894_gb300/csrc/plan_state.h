@@ -50,6 +50,9 @@ struct defmm_plan_s {
     cudaEvent_t events[defmm::kNumPhases + 1] = {};
     std::mutex busy;
     std::vector<double> X, Y;   // the coordinates the plan was built from (caller order; for plan files)
+    // plan creation timing (ms): the device front end (CUDA events; wall time
+    // of the call), the rest of the host construction, the upload and spectra
+    double front_device_ms = 0, front_ms = 0, host_ms = 0, upload_ms = 0;
     // the shard this plan's defmm_apply computes (nshards == 1: the whole operator)
     struct Shard {
         int nshards = 1, shard = 0;

@@ -47,7 +47,9 @@ class Info(ctypes.Structure):
                 ("p2p_interactions", ctypes.c_int64), ("plan_bytes", ctypes.c_size_t),
                 ("workspace_bytes", ctypes.c_size_t), ("launches_per_apply", ctypes.c_int64),
                 ("device_error", ctypes.c_int64),
-                ("d_aabb", ctypes.c_double), ("cube_side", ctypes.c_double)]
+                ("d_aabb", ctypes.c_double), ("cube_side", ctypes.c_double),
+                ("plan_front_device_ms", ctypes.c_double), ("plan_front_ms", ctypes.c_double),
+                ("plan_host_ms", ctypes.c_double), ("plan_upload_ms", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):

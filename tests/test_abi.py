@@ -326,7 +326,7 @@ def test_plan_file_round_trip(tmp_path):
         back = defmm.Plan.load(path, flags=defmm.PLAN_HOST_ONLY)
         a, b = pl.info(), back.info()
         for key in a:
-            if key not in ("plan_bytes", "workspace_bytes"):
+            if key not in ("plan_bytes", "workspace_bytes") and not key.startswith("plan_"):
                 assert a[key] == b[key], key
         for name in ("perm_t", "perm_s", "cells_t", "cells_s", "m2l", "p2p", "mult", "local"):
             assert np.array_equal(pl.table(name), back.table(name)), name
