@@ -69,7 +69,12 @@ typedef enum { DEFMM_C64 = 0, DEFMM_C128 = 1 } defmm_dtype;
  *  m2l_chunk_blocks - most spectra + Fourier multipoles staged together by the
  *               M2L kernel (0: the library's default, 8 for N = 7 or 9; a
  *               positive value >= 2 may only lower it).  Smaller chunks use
- *               less shared memory per block; no result depends on it.       */
+ *               less shared memory per block; no result depends on it.
+ *  radial_power - P in G(r) = exp((i kappa - lambda) r) / (4 pi r^P): 1 (the
+ *               default, the Helmholtz family above) or 2, an oscillatory
+ *               kernel outside that family; the method needs only an
+ *               asymptotically smooth kernel (Sec. 1), and the kernel enters
+ *               the transfer spectra and the near field only.               */
 typedef struct {
     double eta;
     double hf_kw;
@@ -79,6 +84,7 @@ typedef struct {
     size_t hbm_budget;
     double damping;
     int m2l_chunk_blocks;
+    int radial_power;
 } defmm_options;
 
 #define DEFMM_PLAN_HOST_ONLY 1
@@ -101,7 +107,8 @@ void defmm_default_options(defmm_options* opt);
  *  stream    - cudaStream_t for the plan's device work (NULL: legacy stream);
  *              the call returns after that work is complete.
  *  out       - receives the plan.  X and Y are only read during the call.
- * Errors: DEFMM_ERR_ARG (also for damping < 0 or not finite), DEFMM_ERR_OOM,
+ * Errors: DEFMM_ERR_ARG (also for damping < 0 or not finite, radial_power
+ * not 1 or 2), DEFMM_ERR_OOM,
  * DEFMM_ERR_CUDA.                                                             */
 defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int64_t ny,
                                double kappa, int order, int leaf_size,

@@ -7,7 +7,8 @@ the Helmholtz kernel of the complex wavenumber kappa + i lambda: lambda = 0 is t
 paper's kernel, kappa = lambda = 0 the Laplace kernel, kappa = 0 < lambda the
 Yukawa (modified Helmholtz) kernel.  The method applies to asymptotically smooth
 kernels in general (Sec. 1); kappa alone sets the oscillation the directional
-machinery follows.
+machinery follows.  A radial power P = 2 gives exp((i kappa - lambda) r) / (4 pi r^2),
+an oscillatory asymptotically smooth kernel outside the Helmholtz family.
 
 Pairs closer than ``eps_self`` are skipped: the paper resolves coincident
 particles by zeroing the interaction when the distance is "too small"
@@ -26,9 +27,9 @@ import numpy as np
 EPS_SELF_REL = 1e-10
 
 
-def helmholtz(r: np.ndarray, kappa: float, damping: float = 0.0) -> np.ndarray:
-    """G as a function of r = |x - y| (Sec. 1), with the damping lambda above."""
-    return np.exp((1j * kappa - damping) * r) / (4.0 * np.pi * r)
+def helmholtz(r: np.ndarray, kappa: float, damping: float = 0.0, power: int = 1) -> np.ndarray:
+    """G as a function of r = |x - y| (Sec. 1), with the damping lambda and the radial power P above."""
+    return np.exp((1j * kappa - damping) * r) / (4.0 * np.pi * r ** power)
 
 
 def eps_self(X: np.ndarray, Y: np.ndarray | None = None) -> float:
@@ -36,7 +37,7 @@ def eps_self(X: np.ndarray, Y: np.ndarray | None = None) -> float:
     return EPS_SELF_REL * float(np.max(P.max(axis=0) - P.min(axis=0)))
 
 
-def direct_sum(X, Y, q, kappa, eps, targets=None, chunk=256, damping=0.0):
+def direct_sum(X, Y, q, kappa, eps, targets=None, chunk=256, damping=0.0, power=1):
     """p at X[targets] (all of X by default) for charges q (ny,) or (ny, R)."""
     X = np.asarray(X, dtype=np.float64)
     Y = np.asarray(Y, dtype=np.float64)
@@ -52,7 +53,7 @@ def direct_sum(X, Y, q, kappa, eps, targets=None, chunk=256, damping=0.0):
         r = np.sqrt(np.sum(d * d, axis=2))
         far = r > eps
         G = np.zeros(r.shape, dtype=np.complex128)
-        G[far] = helmholtz(r[far], kappa, damping)
+        G[far] = helmholtz(r[far], kappa, damping, power)
         out[c0:c0 + chunk] = G @ q
     return out[:, 0] if squeeze else out
 
@@ -76,12 +77,12 @@ def _lib():
         lib.oracle_direct_sum.argtypes = [
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
-            ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+            ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
         _LIB = lib
     return _LIB
 
 
-def direct_sum_c(X, Y, q, kappa, eps, targets=None, damping=0.0):
+def direct_sum_c(X, Y, q, kappa, eps, targets=None, damping=0.0, power=1):
     """Same as ``direct_sum`` but in C with OpenMP over targets."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     Y = np.ascontiguousarray(Y, dtype=np.float64)
@@ -95,6 +96,6 @@ def direct_sum_c(X, Y, q, kappa, eps, targets=None, damping=0.0):
     out = np.zeros((q.shape[1], len(idx)), dtype=np.complex128)
     _lib().oracle_direct_sum(X.ctypes.data, len(X), Y.ctypes.data, len(Y),
                              qf.ctypes.data, q.shape[1], float(kappa), float(damping), float(eps),
-                             idx.ctypes.data, out.ctypes.data, len(idx))
+                             int(power), idx.ctypes.data, out.ctypes.data, len(idx))
     out = out.T
     return out[:, 0] if squeeze else out

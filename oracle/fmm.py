@@ -52,11 +52,12 @@ class Plan:
     spectra: dict          # (level, kbar) -> canonical spectrum
     dense_m2l: bool = False
     explicit_spectra: bool = False
-    damping: float = 0.0   # kernel exp((i kappa - damping) r) / (4 pi r)
+    damping: float = 0.0   # kernel exp((i kappa - damping) r) / (4 pi r^power)
+    power: int = 1
 
 
 def make_plan(X, Y=None, kappa=1.0, order=4, leaf=64, eta=1.0, hf_kw=1.0, fft_n=None,
-              force_p2p=False, dense_m2l=False, explicit_spectra=False, damping=0.0) -> Plan:
+              force_p2p=False, dense_m2l=False, explicit_spectra=False, damping=0.0, power=1) -> Plan:
     X = np.asarray(X, dtype=np.float64)
     same = Y is None
     Ys = X if same else np.asarray(Y, dtype=np.float64)
@@ -74,12 +75,12 @@ def make_plan(X, Y=None, kappa=1.0, order=4, leaf=64, eta=1.0, hf_kw=1.0, fft_n=
         l = int(tt.level[t])
         kbar, _, _ = m2l.canonical(tt.coords[t] - ts.coords[s])
         if (l, kbar) not in spectra:
-            spectra[(l, kbar)] = m2l.spectrum(kappa, lv.side(l), order, N, kbar, damping)
+            spectra[(l, kbar)] = m2l.spectrum(kappa, lv.side(l), order, N, kbar, damping, power)
     return Plan(kappa=kappa, order=order, fft_n=N, tt=tt, ts=ts, same=same, levels=lv,
                 m2l_pairs=m2l_pairs, p2p_pairs=p2p_pairs, pair_dir=pair_dir,
                 marks_t=marks_t, marks_s=marks_s, eps_self=EPS_SELF_REL * d_aabb,
                 d_aabb=d_aabb, spectra=spectra, dense_m2l=dense_m2l,
-                explicit_spectra=explicit_spectra, damping=damping)
+                explicit_spectra=explicit_spectra, damping=damping, power=power)
 
 
 def _dir_vec(lv, l, u):
@@ -127,7 +128,7 @@ def transfer(plan: Plan, M: dict) -> dict:
         for (t, s), u in zip(plan.m2l_pairs, plan.pair_dir):
             l = int(tt.level[t])
             k = tt.coords[t] - ts.coords[s]
-            contrib = m2l.dense_m2l(plan.kappa, lv.side(l), p, k, M[(s, u)], plan.damping)
+            contrib = m2l.dense_m2l(plan.kappa, lv.side(l), p, k, M[(s, u)], plan.damping, plan.power)
             L[(t, u)] = L.get((t, u), 0) + contrib
         return L
     Mhat = {}
@@ -139,7 +140,7 @@ def transfer(plan: Plan, M: dict) -> dict:
         l = int(tt.level[t])
         k = tt.coords[t] - ts.coords[s]
         if plan.explicit_spectra:
-            g = m2l.spectrum(plan.kappa, lv.side(l), p, N, k, plan.damping)
+            g = m2l.spectrum(plan.kappa, lv.side(l), p, N, k, plan.damping, plan.power)
         else:
             kbar, sigma, sg = m2l.canonical(k)
             g = m2l.permute_spectrum(plan.spectra[(l, kbar)], sigma, sg, N)
@@ -187,7 +188,7 @@ def near_field(plan: Plan, qs: np.ndarray) -> np.ndarray:
         r = np.sqrt(np.sum(d * d, axis=2))
         G = np.zeros(r.shape, dtype=np.complex128)
         far = r > plan.eps_self
-        G[far] = helmholtz(r[far], plan.kappa, plan.damping)
+        G[far] = helmholtz(r[far], plan.kappa, plan.damping, plan.power)
         pot[bt:et] += G @ qs[bs:es]
     return pot
 

@@ -35,7 +35,7 @@ import numpy as np
 from .direct import helmholtz
 
 
-def kernel_samples(kappa: float, side: float, p: int, k, damping: float = 0.0) -> np.ndarray:
+def kernel_samples(kappa: float, side: float, p: int, k, damping: float = 0.0, power: int = 1) -> np.ndarray:
     """g_k(delta) on the difference grid, array [dz, dy, dx] of shape (2p-1)^3."""
     h = side / (p - 1)
     d = np.arange(-(p - 1), p, dtype=np.float64)
@@ -43,7 +43,7 @@ def kernel_samples(kappa: float, side: float, p: int, k, damping: float = 0.0) -
     vx = side * k[0] + h * dx
     vy = side * k[1] + h * dy
     vz = side * k[2] + h * dz
-    return helmholtz(np.sqrt(vx * vx + vy * vy + vz * vz), kappa, damping)
+    return helmholtz(np.sqrt(vx * vx + vy * vy + vz * vz), kappa, damping, power)
 
 
 def embed_kernel(g: np.ndarray, p: int, N: int) -> np.ndarray:
@@ -54,9 +54,9 @@ def embed_kernel(g: np.ndarray, p: int, N: int) -> np.ndarray:
     return out
 
 
-def spectrum(kappa: float, side: float, p: int, N: int, k, damping: float = 0.0) -> np.ndarray:
+def spectrum(kappa: float, side: float, p: int, N: int, k, damping: float = 0.0, power: int = 1) -> np.ndarray:
     """F(g_k): diagonal of the Fourier-domain M2L operator (Eq. FourierDiagonal)."""
-    return np.fft.fftn(embed_kernel(kernel_samples(kappa, side, p, k, damping), p, N))
+    return np.fft.fftn(embed_kernel(kernel_samples(kappa, side, p, k, damping, power), p, N))
 
 
 def canonical(k):
@@ -98,11 +98,12 @@ def f2l(Lhat: np.ndarray, p: int) -> np.ndarray:
     return np.stack([full[r, :p, :p, :p].reshape(p ** 3) for r in range(R)], axis=1)
 
 
-def dense_m2l(kappa: float, side: float, p: int, k, M: np.ndarray, damping: float = 0.0) -> np.ndarray:
+def dense_m2l(kappa: float, side: float, p: int, k, M: np.ndarray, damping: float = 0.0,
+              power: int = 1) -> np.ndarray:
     """The definition: L[a] = sum_b G(x_a - y_b) M[b] (no FFT)."""
     from .interp import multi_index
     h = side / (p - 1)
     mi = multi_index(p).astype(np.float64)
     diff = side * np.asarray(k, dtype=np.float64)[None, None, :] + h * (mi[:, None, :] - mi[None, :, :])
-    G = helmholtz(np.sqrt(np.sum(diff * diff, axis=2)), kappa, damping)
+    G = helmholtz(np.sqrt(np.sum(diff * diff, axis=2)), kappa, damping, power)
     return G @ M

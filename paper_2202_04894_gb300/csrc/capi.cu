@@ -252,6 +252,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     DevCommon& c = pl->common;
     c.p = hp.p; c.N = hp.N; c.NF = hp.NF; c.NFpad = hp.NFpad; c.P3 = hp.P3;
     c.nx = hp.nx; c.ny = hp.ny; c.kappa = hp.kappa; c.eps_self = hp.eps_self; c.damping = hp.damping;
+    c.radial_power = hp.radial_power;
     if (hp.ngeo > 1) {
         c.cell_geo = (const int32_t*)P(o_cgeo);
         c.geo_kappa = (const double*)P(o_gk);
@@ -336,7 +337,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
 
     cudaError_t e = launch_spectra((const int32_t*)P(o_sl), (const int32_t*)P(o_sk), (int)nspec,
                                    (const double*)P(o_lside), hp.p, hp.N, hp.NFpad, hp.kappa,
-                                   hp.ngeo > 1 ? (const double*)P(o_spk) : nullptr, hp.damping,
+                                   hp.ngeo > 1 ? (const double*)P(o_spk) : nullptr, hp.damping, hp.radial_power,
                                    (double2*)P(o_specd), (float2*)P(o_specf), stream);
     if (e != cudaSuccess) return cuda_fail(e, "spectra kernel");
     CK(cudaStreamSynchronize(stream), "plan creation");
@@ -545,6 +546,7 @@ void defmm_default_options(defmm_options* opt) {
     opt->self_eps = 1e-10;
     opt->hbm_budget = 0;
     opt->damping = 0.0;
+    opt->radial_power = 1;
     opt->m2l_chunk_blocks = 0;
 }
 
@@ -597,6 +599,7 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
         if (g_config_err != cudaSuccess) return cuda_fail(g_config_err, "kernel configuration");
     }
     if (!(o.damping >= 0.0) || !std::isfinite(o.damping)) return fail(DEFMM_ERR_ARG, "damping must be finite and >= 0");
+    if (o.radial_power != 1 && o.radial_power != 2) return fail(DEFMM_ERR_ARG, "radial_power must be 1 or 2");
     if (o.m2l_chunk_blocks < 0 || o.m2l_chunk_blocks == 1) return fail(DEFMM_ERR_ARG, "m2l_chunk_blocks must be 0 or >= 2");
     defmm_plan_s* pl = new (std::nothrow) defmm_plan_s;
     if (!pl) return fail(DEFMM_ERR_OOM, "host allocation");
@@ -630,6 +633,7 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
         return fail(DEFMM_ERR_ARG, ex.what());
     }
     pl->hp.damping = o.damping;
+    pl->hp.radial_power = o.radial_power;
     pl->host_only = host_only;
     {
         const auto u0 = std::chrono::steady_clock::now();
@@ -669,6 +673,7 @@ defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int
         if (g_config_err != cudaSuccess) return cuda_fail(g_config_err, "kernel configuration");
     }
     if (!(o.damping >= 0.0) || !std::isfinite(o.damping)) return fail(DEFMM_ERR_ARG, "damping must be finite and >= 0");
+    if (o.radial_power != 1 && o.radial_power != 2) return fail(DEFMM_ERR_ARG, "radial_power must be 1 or 2");
     if (o.m2l_chunk_blocks < 0 || o.m2l_chunk_blocks == 1) return fail(DEFMM_ERR_ARG, "m2l_chunk_blocks must be 0 or >= 2");
     defmm_plan_s* pl = new (std::nothrow) defmm_plan_s;
     if (!pl) return fail(DEFMM_ERR_OOM, "host allocation");
@@ -690,6 +695,7 @@ defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int
             build_host_plan(hx.data(), nx[g], nullptr, nx[g], kappa[g], order, leaf_size, o.eta, o.hf_kw, o.fft_n,
                             o.self_eps, o.m2l_chunk_blocks, parts[g], host_only ? nullptr : &front);
             parts[g].damping = o.damping;
+            parts[g].radial_power = o.radial_power;
             all.insert(all.end(), hx.begin(), hx.end());
         }
         union_host_plans(parts, pl->hp);

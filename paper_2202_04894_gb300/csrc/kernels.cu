@@ -154,30 +154,20 @@ __device__ __forceinline__ void sincos_hw(float a, float* s, float* c) {
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(a));
 }
 
-// Kernel value G(x, y) for a difference d, zero when |d|^2 <= eps2 (Sec. 5.3).
-// Single precision: 1/r from the hardware reciprocal square root, the phase
-// kappa r / (2 pi) reduced exactly to [-1/2, 1/2] turns (round-to-nearest by
-// adding and subtracting 1.5 * 2^23), then the hardware sine and cosine on
-// [-pi, pi].
-__device__ __forceinline__ float2 helmholtz(float dx, float dy, float dz, float kap2pi, float eps2) {
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float rinv = rsqrt_hw(r2);
-    rinv = r2 > eps2 ? rinv : 0.f;      // coincident points contribute nothing
-    const float r = r2 * rinv;
-    float t = r * kap2pi;
-    t -= __fadd_rn(__fadd_rn(t, 12582912.f), -12582912.f);
-    float s, c;
-    sincos_hw(6.28318530717958647692f * t, &s, &c);
-    const float g = rinv * (float)kInv4Pi;
-    return make_float2(c * g, s * g);
-}
+// The kernel family: G(r) = e^{(i kappa - lambda) r} / (4 pi r^P) with P = 1
+// (Helmholtz; Laplace and Yukawa at kappa = 0) or P = 2 (an oscillatory kernel
+// outside that family).  The method needs the kernel only to be
+// asymptotically smooth (Sec. 1); it enters the transfer spectra (k_spectra)
+// and the near field (the P2P kernels) and nothing else.
+// Value for a difference d, zero when |d|^2 <= eps2 (Sec. 5.3), in float64.
 __device__ __forceinline__ double2 helmholtz(double dx, double dy, double dz, double kappa, double eps2,
-                                             double damping) {
+                                             double damping, int power) {
     double r2 = dx * dx + dy * dy + dz * dz;
     double r = sqrt(r2);
     double s, c;
     sincos(kappa * r, &s, &c);
     double g = kInv4Pi / r;
+    if (power == 2) g /= r;
     if (damping > 0.0) g *= exp(-damping * r);
     double2 out = make_double2(c * g, s * g);
     if (!(r2 > eps2)) out = make_double2(0.0, 0.0);
@@ -273,8 +263,8 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
                         dxa += xa.lo - ex; dya += ya.lo - ey; dza += za.lo - ez;
                         dxb += xb.lo - ex; dyb += yb.lo - ey; dzb += zb.lo - ez;
                     }
-                    const C ga = helmholtz(dxa, dya, dza, kpar, eps2, (T)c.damping);
-                    const C gb = helmholtz(dxb, dyb, dzb, kpar, eps2, (T)c.damping);
+                    const C ga = helmholtz(dxa, dya, dza, kpar, eps2, (T)c.damping, c.radial_power);
+                    const C gb = helmholtz(dxb, dyb, dzb, kpar, eps2, (T)c.damping, c.radial_power);
 #pragma unroll
                     for (int r = 0; r < RB; ++r) {
                         const C qv = sq[r][k];
@@ -339,17 +329,20 @@ __device__ __forceinline__ float3 local_coords(float4 h, float4 l, float4 oh, fl
     return make_float3((h.x - oh.x) + (l.x - ol.x), (h.y - oh.y) + (l.y - ol.y), (h.z - oh.z) + (l.z - ol.z));
 }
 
-// e^{i kappa r} / r (times a staged 1/(4 pi) in the charges) for r^2; kph is
-// kappa / (2 pi) with REDUCE (phase in turns), else kappa (phase in radians)
-template <bool DAMP, bool REDUCE>
+// e^{(i kappa - lambda) r} / r^P (times a staged 1/(4 pi) in the charges) for
+// r^2: KIND 0 is P = 1 without damping, 1 is P = 1 with it, 2 is P = 2 (with
+// the damping term, exact at lambda = 0).  kph is kappa / (2 pi) with REDUCE
+// (phase in turns), else kappa (phase in radians).
+template <int KIND, bool REDUCE>
 __device__ __forceinline__ float2 near_kernel(float r2, float kph, float lam2) {
-    float rinv = rsqrt_hw(r2);
+    const float rinv = rsqrt_hw(r2);
     const float r = r2 * rinv;
     float sn, cs;
     if (REDUCE) turns_sincos(r * kph, &sn, &cs);
     else sincos_hw(r * kph, &sn, &cs);
-    if (DAMP) rinv *= ex2_hw(-lam2 * r);
-    return make_float2(cs * rinv, sn * rinv);
+    float amp = KIND == 2 ? rinv * rinv : rinv;
+    if (KIND >= 1) amp *= ex2_hw(-lam2 * r);
+    return make_float2(cs * amp, sn * amp);
 }
 
 // r^2 of a near-coincident pair from the hi + lo pairs; 2^100 for coincident points
@@ -361,7 +354,7 @@ __device__ __forceinline__ float exact_r2(float4 th, float4 tl, float4 sh, float
     return r2 > eps2 ? r2 : 0x1p100f;
 }
 
-template <int RB, bool DAMP = false, bool REDUCE = true>
+template <int RB, int KIND = 0, bool REDUCE = true>
 __global__ void __launch_bounds__(128, RB == 1 ? 8 : 1) k_p2p_f32(DevCommon c, const float2* __restrict__ qs,
                                                  float2* __restrict__ part, int R, int rb0) {
     __shared__ float4 sa[128];   // source relative to the local origin; w: |s'|^2 + 64 eps_self^2
@@ -464,8 +457,8 @@ __global__ void __launch_bounds__(128, RB == 1 ? 8 : 1) k_p2p_f32(DevCommon c, c
                             if (ca) ra = exact_r2(c.Xh[t0 + ia], c.Xl[t0 + ia], h, l, eps2);
                             if (cb) rb = exact_r2(c.Xh[t0 + (has_b ? ib : ia)], c.Xl[t0 + (has_b ? ib : ia)], h, l, eps2);
                         }
-                        const float2 ga = near_kernel<DAMP, REDUCE>(ra, kph, lam2);
-                        const float2 gb = near_kernel<DAMP, REDUCE>(rb, kph, lam2);
+                        const float2 ga = near_kernel<KIND, REDUCE>(ra, kph, lam2);
+                        const float2 gb = near_kernel<KIND, REDUCE>(rb, kph, lam2);
 #pragma unroll
                         for (int r = 0; r < RB; ++r) {
                             const float2 q = sq[r][k];
@@ -502,13 +495,13 @@ __global__ void __launch_bounds__(128, RB == 1 ? 8 : 1) k_p2p_f32(DevCommon c, c
     }
 }
 
-template <bool DAMP, bool REDUCE>
+template <int KIND, bool REDUCE>
 void launch_p2p_f32(int rb, unsigned nu, const DevCommon& c, const float2* qs, float2* part, int R, int rb0,
                     cudaStream_t stream) {
-    if (rb == 1) k_p2p_f32<1, DAMP, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
-    else if (rb == 16) k_p2p_f32<16, DAMP, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
-    else if (rb == 8) k_p2p_f32<8, DAMP, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
-    else k_p2p_f32<4, DAMP, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
+    if (rb == 1) k_p2p_f32<1, KIND, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
+    else if (rb == 16) k_p2p_f32<16, KIND, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
+    else if (rb == 8) k_p2p_f32<8, KIND, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
+    else k_p2p_f32<4, KIND, REDUCE><<<nu, 128, 0, stream>>>(c, qs, part, R, rb0);
 }
 
 // Sums each target's partial near-field sums over its leaf's work units, in
@@ -1698,7 +1691,7 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_l2p_warp(DevCommon c, DevTy
 __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spec_level, const int32_t* __restrict__ kbar,
                                                  const double* __restrict__ level_side, int p, int N, int NFpad,
                                                  double kappa0, const double* __restrict__ spec_kappa, double damping,
-                                                 double2* __restrict__ out_d, float2* __restrict__ out_f) {
+                                                 int power, double2* __restrict__ out_d, float2* __restrict__ out_f) {
     extern __shared__ unsigned char smem_raw[];
     const int NF = N * N * N;
     double2* A = reinterpret_cast<double2*>(smem_raw);
@@ -1723,7 +1716,9 @@ __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spe
         const double r = sqrt(vx * vx + vy * vy + vz * vz);
         double s, c;
         sincos(kappa * r, &s, &c);
-        const double g = kInv4Pi / r * (damping > 0.0 ? exp(-damping * r) : 1.0);
+        double g = kInv4Pi / r;
+        if (power == 2) g /= r;
+        if (damping > 0.0) g *= exp(-damping * r);
         const int ix = (dx + N) % N, iy = (dy + N) % N, iz = (dz + N) % N;
         A[(iz * N + iy) * N + ix] = make_double2(c * g, s * g);
     }
@@ -1755,14 +1750,14 @@ __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spe
 
 cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
                            const double* level_side, int p, int N, int NFpad, double kappa,
-                           const double* spec_kappa, double damping, double2* out_d, float2* out_f,
+                           const double* spec_kappa, double damping, int power, double2* out_d, float2* out_f,
                            cudaStream_t stream) {
     if (nspec == 0) return cudaSuccess;
     size_t smem = 2 * (size_t)N * N * N * sizeof(double2);
     cudaError_t err = cudaFuncSetAttribute(k_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k_spectra<<<nspec, 256, smem, stream>>>(spec_level, spec_kbar, level_side, p, N, NFpad, kappa, spec_kappa, damping,
-                                            out_d, out_f);
+                                            power, out_d, out_f);
     return cudaGetLastError();
 }
 
@@ -1958,7 +1953,8 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
                                 rinv = r2 > eps2 ? rinv : 0.f;
                                 float sn, cs;
                                 turns_sincos(r2 * rinv * kap2pi, &sn, &cs);
-                                if (lam2 != 0.f) rinv *= ex2_hw(-lam2 * (r2 * rinv));
+                                const float amp = c.radial_power == 2 ? rinv * rinv : rinv;
+                                rinv = lam2 != 0.f ? amp * ex2_hw(-lam2 * (r2 * rinv)) : amp;
                                 gr = cs * rinv;
                                 gi = sn * rinv;
                             }
@@ -2244,12 +2240,15 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         if constexpr (std::is_same<T, float>::value) {
             const unsigned nu = (unsigned)c.n_p2p_units;
             const bool direct = c.p2p_direct_phase && !c.p2p_reduce_phase;
-            if (c.damping > 0.0) {
-                if (direct) launch_p2p_f32<true, false>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
-                else launch_p2p_f32<true, true>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
+            if (c.radial_power == 2) {
+                if (direct) launch_p2p_f32<2, false>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
+                else launch_p2p_f32<2, true>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
+            } else if (c.damping > 0.0) {
+                if (direct) launch_p2p_f32<1, false>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
+                else launch_p2p_f32<1, true>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
             } else {
-                if (direct) launch_p2p_f32<false, false>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
-                else launch_p2p_f32<false, true>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
+                if (direct) launch_p2p_f32<0, false>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
+                else launch_p2p_f32<0, true>(p2p_rb, nu, c, w.qs, w.part, R, rb0, stream);
             }
         } else {
             if (R == 1) k_p2p<T, 1><<<(unsigned)c.n_p2p_units, 128, 0, stream>>>(c, w.qs, w.part, R, rb0);

@@ -17,7 +17,8 @@ struct DevCommon {
     int p, N, NF, NFpad, P3;
     int64_t nx, ny;
     double kappa, eps_self;
-    double damping;          // lambda >= 0: G = exp((i kappa - lambda) r) / (4 pi r)
+    double damping;          // lambda >= 0: G = exp((i kappa - lambda) r) / (4 pi r^P)
+    int radial_power;        // P: 1 (Helmholtz family) or 2
     const double* Xs;        // nx*3 targets, Morton order
     const double* Ys;        // ny*3 sources, Morton order
     const float4* Xh;        // targets minus the cube centre, float hi part (w unused)
@@ -130,7 +131,7 @@ int sm_count();
 // Forms the canonical transfer spectra in float64 (Sec. 2.3 Eq. FourierDiagonal).
 cudaError_t launch_spectra(const int32_t* spec_level, const int32_t* spec_kbar, int nspec,
                            const double* level_side, int p, int N, int NFpad, double kappa,
-                           const double* spec_kappa, double damping, double2* out_d, float2* out_f,
+                           const double* spec_kappa, double damping, int power, double2* out_d, float2* out_f,
                            cudaStream_t stream);
 
 }  // namespace defmm

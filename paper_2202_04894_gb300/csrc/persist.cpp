@@ -23,7 +23,7 @@ namespace defmm {
 namespace {
 
 constexpr char kMagic[8] = {'D', 'E', 'F', 'M', 'M', 'P', 'L', 'N'};
-constexpr uint32_t kVersion = 2;   // 2: Levels field by field (no padding bytes)
+constexpr uint32_t kVersion = 3;   // 2: Levels field by field (no padding bytes); 3: radial power
 
 // 64-bit FNV-1a over every byte after the header, stored at the end of the
 // file: a damaged plan file is refused instead of handing the kernels
@@ -111,7 +111,7 @@ template <typename A, typename T> void tree_fields(A& a, T& t) {
 
 // Every HostPlan field, in one order for writing and reading.
 template <typename A, typename H> void plan_fields(A& a, H& h) {
-    a.raw(h.nx); a.raw(h.ny); a.raw(h.same); a.raw(h.kappa); a.raw(h.damping);
+    a.raw(h.nx); a.raw(h.ny); a.raw(h.same); a.raw(h.kappa); a.raw(h.damping); a.raw(h.radial_power);
     a.raw(h.p); a.raw(h.N); a.raw(h.NF); a.raw(h.NFpad); a.raw(h.P3);
     a.raw(h.eta); a.raw(h.hf_kw); a.raw(h.self_eps_rel); a.raw(h.eps_self); a.raw(h.d_aabb); a.raw(h.side);
     a.raw(h.corner);

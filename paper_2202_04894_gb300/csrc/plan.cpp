@@ -844,6 +844,7 @@ void union_host_plans(std::vector<HostPlan>& parts, HostPlan& u) {
     u.same = true;
     u.p = f.p; u.N = f.N; u.NF = f.NF; u.NFpad = f.NFpad; u.P3 = f.P3;
     u.eta = f.eta; u.hf_kw = f.hf_kw; u.self_eps_rel = f.self_eps_rel; u.damping = f.damping;
+    u.radial_power = f.radial_power;
     u.kappa = f.kappa; u.eps_self = f.eps_self; u.d_aabb = f.d_aabb; u.side = f.side;
     for (int a = 0; a < 3; ++a) u.corner[a] = f.corner[a];
     u.lv = f.lv;

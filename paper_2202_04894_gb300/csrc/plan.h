@@ -65,7 +65,8 @@ struct HostPlan {
     int64_t nx = 0, ny = 0;
     bool same = true;
     double kappa = 0;
-    double damping = 0;   // lambda of the kernel exp((i kappa - lambda) r) / (4 pi r)
+    double damping = 0;   // lambda of the kernel exp((i kappa - lambda) r) / (4 pi r^P)
+    int radial_power = 1; // P, 1 or 2
     int p = 4, N = 7, NF = 343, NFpad = 344, P3 = 64;
     double eta = 1, hf_kw = 1, self_eps_rel = 1e-10;
     double eps_self = 0, d_aabb = 0, side = 0;

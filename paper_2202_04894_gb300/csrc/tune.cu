@@ -245,7 +245,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
         }
         key.val(nx); key.val(nys); key.val(same); key.val(kappa); key.val(order);
         key.val(t.nrhs); key.val((int)t.dtype); key.val(t.leaf_min); key.val(t.leaf_max); key.val(t.tune_fft_n);
-        key.val(o.eta); key.val(o.hf_kw); key.val(o.fft_n); key.val(o.self_eps); key.val(o.damping); key.val(o.m2l_chunk_blocks);
+        key.val(o.eta); key.val(o.hf_kw); key.val(o.fft_n); key.val(o.self_eps); key.val(o.damping); key.val(o.radial_power); key.val(o.m2l_chunk_blocks);
     }
 
     defmm_tune_result res{};

@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("hf_kw", ctypes.c_double), ("fft_n", ctypes.c_int),
                 ("flags", ctypes.c_int), ("self_eps", ctypes.c_double),
                 ("hbm_budget", ctypes.c_size_t), ("damping", ctypes.c_double),
-                ("m2l_chunk_blocks", ctypes.c_int)]
+                ("m2l_chunk_blocks", ctypes.c_int), ("radial_power", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -128,6 +128,10 @@ WORKLOADS = {
     # 5*10^5 points on a 1 x 1 x 0.25 box surface, kappa*D = 64, order 5, 32 RHS
     "box500k_kD64_p5_r32": dict(kind="box", n=500_000, seed=3, kappa_d=64.0,
                                 order=5, leaf=64, nrhs=32, dtype="c64"),
+    # 5*10^5 points uniform in a cube, kappa*D = 64, order 4, leaf <= 64, complex64:
+    # the volumetric distribution, whose M2L lists are the densest
+    "cube500k_kD64_p4": dict(kind="cube", n=500_000, seed=4, kappa_d=64.0,
+                             order=4, leaf=64, nrhs=1, dtype="c64"),
 }
 
 

@@ -451,3 +451,14 @@ def test_m2l_schedule_of_a_large_plan():
     got = np.lexsort((td, sc, tc))
     want = np.lexsort((m2l[:, 2], m2l[:, 1], m2l[:, 0]))
     assert np.array_equal(np.stack([tc, sc, td], 1)[got], m2l[want])
+
+
+def test_radial_power_option():
+    """radial_power selects the kernel exp((i kappa - lambda) r)/(4 pi r^P), P = 1 or 2."""
+    X = W.points("sphere", 300, 2)
+    assert defmm.default_options().radial_power == 1
+    _host_plan(X, kappa=2.0, order=4, leaf_size=16, radial_power=2)
+    for bad in (0, 3, -1):
+        with pytest.raises(defmm.DefmmError) as e:
+            _host_plan(X, kappa=2.0, order=4, leaf_size=16, radial_power=bad)
+        assert e.value.status == 1

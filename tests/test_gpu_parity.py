@@ -172,6 +172,29 @@ def test_damped_kernel_against_oracle(kind, kd, damping_d, order):
     assert _rel(undamped, ref) > 0.05
 
 
+@pytest.mark.parametrize("kind,kd,damping_d,order", [("sphere", 24.0, 0.0, 4), ("cube", 0.0, 0.0, 5),
+                                                    ("box", 16.0, 4.0, 4)])
+def test_power_two_kernel_against_oracle(kind, kd, damping_d, order):
+    """exp((i kappa - lambda) r)/(4 pi r^2), outside the Helmholtz family (the plan
+    option radial_power = 2 reaches the transfer spectra and every near-field kernel):
+    complex128 and complex64 (one column, several columns, tensor-core near field,
+    both phase forms) against the oracle, element by element."""
+    X = W.points(kind, 2500, 73)
+    D = float(np.max(X.max(0) - X.min(0)))
+    kappa, lam = kd / D, damping_d / D
+    q = W.charges(2500, 74, nrhs=2)
+    plan = defmm.Plan(X, kappa=kappa, order=order, leaf_size=20, damping=lam, radial_power=2)
+    ref = oracle_fmm.fmm(X, q, kappa, order=order, leaf=20, damping=lam, power=2)
+    _check_close(_gpu(plan, q, torch.complex128), ref, TOL128, 1e-11, "r^-2 %s c128" % kind)
+    _check_close(_gpu(plan, q, torch.complex64), ref, TOL64, 1e-4, "r^-2 %s c64" % kind)
+    _check_close(_gpu(plan, q[:, 0], torch.complex64), ref[:, 0], TOL64, 1e-4, "r^-2 %s c64 one column" % kind)
+    plan.set_tuning(p2p_reduce_phase=1)
+    _check_close(_gpu(plan, q[:, 0], torch.complex64), ref[:, 0], TOL64, 1e-4, "r^-2 %s c64 reduced" % kind)
+    plan.set_tuning(p2p_tc_min_rhs=1)
+    _check_close(_gpu(plan, q, torch.complex64), ref, TOL64, 1e-4, "r^-2 %s c64 tensor cores" % kind)
+    assert _rel(oracle_fmm.fmm(X, q, kappa, order=order, leaf=20, damping=lam), ref) > 0.05
+
+
 def test_multi_rhs_columns_and_determinism():
     X = W.points("sphere", 4000, 31)
     kappa = 20.0

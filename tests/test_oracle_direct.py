@@ -99,3 +99,34 @@ def test_c_direct_matches_numpy_damped():
     a = direct.direct_sum(X, X, q, 4.0, 1e-10, targets=tg, damping=2.5)
     b = direct.direct_sum_c(X, X, q, 4.0, 1e-10, targets=tg, damping=2.5)
     assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a))
+
+
+@pytest.mark.parametrize("kappa", [0.0, 2.5, 7.0])
+def test_shell_mean_value_power_two(kappa):
+    """Radial power 2: with r^2 = R^2 + a^2 - 2aR cos(theta) the spherical mean of
+    exp(i kappa r)/(4 pi r^2) over a sphere of radius a seen from R > a is
+    (1/(8 pi a R)) * integral_{R-a}^{R+a} exp(i kappa r)/r dr
+    = [Ci(kappa r) + i Si(kappa r)]_{R-a}^{R+a} / (8 pi a R), and ln((R+a)/(R-a))/(8 pi a R)
+    at kappa = 0."""
+    sici = pytest.importorskip("scipy.special").sici
+    a, R = 0.5, 1.7
+    Y, w = _sphere_quadrature(64, 128, a)
+    x = np.array([[0.3 * R, -0.4 * R, np.sqrt(1 - 0.25) * R]])
+    got = direct.direct_sum(x, Y, w, kappa, 1e-12, power=2)[0]
+    if kappa == 0:
+        want = np.log((R + a) / (R - a)) / (8 * np.pi * a * R)
+    else:
+        (s1, c1), (s0, c0) = sici(kappa * (R + a)), sici(kappa * (R - a))
+        want = ((c1 - c0) + 1j * (s1 - s0)) / (8 * np.pi * a * R)
+    assert abs(got - want) <= 1e-12 * abs(want)
+    # a different kernel: the power-1 mean differs
+    assert abs(direct.direct_sum(x, Y, w, kappa, 1e-12)[0] - want) > 1e-3 * abs(want)
+
+
+def test_c_direct_matches_numpy_power_two():
+    X = W.points("box", 300, 9)
+    q = W.charges(300, 9, nrhs=2)
+    tg = np.array([3, 77, 299])
+    a = direct.direct_sum(X, X, q, 4.0, 1e-10, targets=tg, damping=1.5, power=2)
+    b = direct.direct_sum_c(X, X, q, 4.0, 1e-10, targets=tg, damping=1.5, power=2)
+    assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a))

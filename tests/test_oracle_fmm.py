@@ -88,3 +88,19 @@ def test_damped_kernel_against_direct_sum(kd, damping_d):
     # the damping changes the result (the kernel is really used everywhere)
     undamped = direct.direct_sum(X, X, q, kappa, direct.eps_self(X))
     assert _rel(undamped, want) > 0.1
+
+
+@pytest.mark.parametrize("kd", [0.0, 16.0])
+def test_power_two_kernel_against_direct_sum(kd):
+    """exp(i kappa r)/(4 pi r^2), a kernel outside the Helmholtz family: the FMM
+    with it converges to the direct sum with it, and it is really used (the
+    power-1 sum differs)."""
+    X = W.points("sphere", 1500, 12)
+    D = float(np.max(X.max(0) - X.min(0)))
+    kappa = kd / D
+    q = W.charges(1500, 13)[:, 0]
+    want = direct.direct_sum(X, X, q, kappa, direct.eps_self(X), power=2)
+    e3 = _rel(fmm.fmm(X, q, kappa, order=3, leaf=20, power=2), want)
+    e5 = _rel(fmm.fmm(X, q, kappa, order=5, leaf=20, power=2), want)
+    assert e5 < 1e-4 and e5 < e3 / 5
+    assert _rel(direct.direct_sum(X, X, q, kappa, direct.eps_self(X)), want) > 0.1

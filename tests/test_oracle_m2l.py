@@ -26,15 +26,16 @@ def test_fft_m2l_equals_dense(p):
         assert np.max(np.abs(fft - dense)) <= 1e-13 * np.max(np.abs(dense))
 
 
-@pytest.mark.parametrize("kappa,damping", [(0.0, 6.0), (9.0, 3.0)])
-def test_fft_m2l_equals_dense_damped(kappa, damping):
-    """The same identity for the damped kernel (Yukawa; damped Helmholtz)."""
+@pytest.mark.parametrize("kappa,damping,power", [(0.0, 6.0, 1), (9.0, 3.0, 1), (0.0, 0.0, 2), (9.0, 3.0, 2)])
+def test_fft_m2l_equals_dense_damped(kappa, damping, power):
+    """The same identity for the damped kernel (Yukawa; damped Helmholtz) and the
+    radial power 2 kernel exp((i kappa - lambda) r) / (4 pi r^2)."""
     side, p = 0.25, 4
     N = 2 * p - 1
     for k in [(2, 0, 0), (3, -1, 2), (-4, 4, 1)]:
         M = _rand((p ** 3, 2))
-        dense = m2l.dense_m2l(kappa, side, p, k, M, damping)
-        g = m2l.spectrum(kappa, side, p, N, k, damping)
+        dense = m2l.dense_m2l(kappa, side, p, k, M, damping, power)
+        g = m2l.spectrum(kappa, side, p, N, k, damping, power)
         fft = m2l.f2l(g[None] * m2l.m2f(M, p, N), p)
         assert np.max(np.abs(fft - dense)) <= 1e-13 * np.max(np.abs(dense))
 
