@@ -293,6 +293,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=10000, help="serve16: number of requests")
     ap.add_argument("--gap-ms", type=float, default=2.0, help="serve16: mean inter-arrival time")
+    ap.add_argument("--load-fracs", default="0.5,0.8,0.95",
+                    help="serve16: offered loads (fractions of the measured capacity) for the latency curve; '' skips")
+    ap.add_argument("--curve-requests", type=int, default=400, help="serve16: requests per load-curve point")
     ap.add_argument("--streams", type=int, default=4, help="serve16: batches in flight")
     ap.add_argument("--branches", type=int, default=8, help="batch48: graph branches")
     args = ap.parse_args()
@@ -627,33 +630,56 @@ def bench_serve(args):
     for g in range(len(plans)):                                   # warm-up: every geometry once
         srv.wait_ticket(srv.submit_ptr(g, qh[g].data_ptr(), ph[g].data_ptr(), maxr))
     st0 = srv.stats()
-    tickets = [None] * len(reqs)
     clocks = ClockSampler(_bus(torch))
     clocks.start()
     time.sleep(0.3)
 
-    def producer():
-        t0 = time.perf_counter()
-        for i, (t_ms, g, r) in enumerate(reqs):
-            delay = t0 + t_ms * 1e-3 - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            tickets[i] = srv.submit_ptr(g, qh[g].data_ptr(), ph[g].data_ptr(), r)
+    def run(stream):
+        """Submits the (t_ms, geometry, nrhs) stream on its schedule; returns latencies and wall time."""
+        tickets = [None] * len(stream)
 
-    t_start = time.perf_counter()
-    th = threading.Thread(target=producer)
-    th.start()
-    lat = []
-    for i in range(len(reqs)):
-        while tickets[i] is None:
-            time.sleep(1e-4)
-        lat.append(srv.wait_ticket(tickets[i]))
-    th.join()
-    wall = time.perf_counter() - t_start
-    clk = clocks.stop()
-    st = srv.stats()
-    srv.close()
-    work = sum(plans[g].nx * r for _, g, r in reqs)
+        def producer():
+            t0 = time.perf_counter()
+            for i, (t_ms, g, r) in enumerate(stream):
+                delay = t0 + t_ms * 1e-3 - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[i] = srv.submit_ptr(g, qh[g].data_ptr(), ph[g].data_ptr(), r)
+
+        t_start = time.perf_counter()
+        th = threading.Thread(target=producer)
+        th.start()
+        lat = []
+        for i in range(len(stream)):
+            while tickets[i] is None:
+                time.sleep(1e-4)
+            lat.append(srv.wait_ticket(tickets[i]))
+        th.join()
+        return lat, time.perf_counter() - t_start
+
+    def work_of(stream):
+        return sum(plans[g].nx * r for _, g, r in stream)
+
+    def pct(v, f):
+        srt = sorted(v)
+        return srt[min(len(srt) - 1, int(f * len(srt)))]
+
+    # latency at sustainable loads: the capacity from a burst (every request at once),
+    # then Poisson streams offering a fraction of it
+    curve, capacity = [], None
+    if args.load_fracs:
+        burst = [(0.0, g, r) for _, g, r in W.request_stream(args.curve_requests, 301, 1.0, len(plans), maxr)]
+        _, wall_b = run(burst)
+        capacity = work_of(burst) / wall_b / 1e6
+        mean_work = work_of(burst) / len(burst)
+        for frac in [float(f) for f in args.load_fracs.split(",")]:
+            gap = mean_work / (frac * capacity * 1e6) * 1e3
+            stream = W.request_stream(args.curve_requests, 302, gap, len(plans), maxr)
+            lat_f, wall_f = run(stream)
+            curve.append({"load": frac, "mean_gap_ms": gap, "p50_ms": pct(lat_f, 0.5), "p99_ms": pct(lat_f, 0.99),
+                          "served": work_of(stream) / wall_f / 1e6, "requests": len(stream)})
+    lat, wall = run(reqs)
+    work = work_of(reqs)
     srt = sorted(lat)
     offered = sum(plans[g].nx * r for _, g, r in reqs) / (reqs[-1][0] * 1e-3) / 1e6
     line = {"metric": METRIC, "value": work / wall / 1e6, "unit": UNIT, "n_gpus": 1, "steps": len(reqs),
@@ -667,6 +693,9 @@ def bench_serve(args):
             "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
             "mean_ms": statistics.mean(lat), "max_ms": srt[-1],
             "offered_load": {"value": offered, "unit": UNIT},
+            "capacity": {"value": capacity, "unit": UNIT, "from": "%d requests submitted at once" % args.curve_requests}
+            if capacity else None,
+            "load_curve": curve,
             "e2e": {"value": work / wall / 1e6, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * sum(plans[g].ny * r for _, g, r in reqs) // len(reqs),
                     "d2h_bytes_per_step": 8 * sum(plans[g].nx * r for _, g, r in reqs) // len(reqs)},

@@ -301,6 +301,16 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
                                  int order, const defmm_options* opt, const defmm_tune_options* topt,
                                  void* stream, defmm_plan* out, defmm_tune_result* result);
 
+/* The same search for a union plan (defmm_plan_create_union: ngeo
+ * geometries, sources = targets): every candidate is a union plan of all the
+ * geometries with one leaf size and DFT length, timed as one apply over all
+ * of them (nrhs columns of the total point count).  The cache key hashes every
+ * geometry's coordinates, point count and wavenumber.  Arguments and errors
+ * as defmm_plan_create_union and defmm_plan_autotune.                         */
+defmm_status defmm_plan_autotune_union(int ngeo, const double* const* X, const int64_t* nx, const double* kappa,
+                                       int order, const defmm_options* opt, const defmm_tune_options* topt,
+                                       void* stream, defmm_plan* out, defmm_tune_result* result);
+
 /* Iterative solve with the FMM operator: restarted GMRES (Saad and Schultz,
  * 1986) for (sigma I + A) x = b, A the plan's operator (p = A q).  The paper
  * applies the operator repeatedly inside iterative boundary-integral solvers

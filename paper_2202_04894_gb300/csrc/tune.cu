@@ -28,6 +28,7 @@
 #include <cinttypes>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -149,43 +150,15 @@ defmm_status time_applies(defmm_plan plan, DeviceBuffers& b, int nrhs, defmm_dty
     return DEFMM_OK;
 }
 
-}  // namespace
+// Candidates, timing and the cache, for any plan factory (one geometry or a
+// union): make(leaf, options, &plan) builds a candidate; nx / nys are the
+// total target / source counts of an apply.
+using Factory = std::function<defmm_status(int leaf, const defmm_options& o, defmm_plan* out)>;
 
-extern "C" {
-
-void defmm_default_tune_options(defmm_tune_options* t) {
-    if (!t) return;
-    t->leaf_min = 16;
-    t->leaf_max = 64;
-    t->nrhs = 1;
-    t->dtype = DEFMM_C64;
-    t->reps = 5;
-    t->tune_fft_n = 1;
-    t->cache_path = nullptr;
-}
-
-defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa, int order,
-                                 const defmm_options* opt, const defmm_tune_options* topt, void* stream,
-                                 defmm_plan* out, defmm_tune_result* result) {
-    if (!out) return defmm::set_error(DEFMM_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (!X || nx < 1) return defmm::set_error(DEFMM_ERR_ARG, "X is NULL or nx < 1");
-    defmm_tune_options t;
-    defmm_default_tune_options(&t);
-    if (topt) t = *topt;
-    defmm_options o;
-    defmm_default_options(&o);
-    if (opt) o = *opt;
-    if (t.leaf_min < 1 || t.leaf_max < t.leaf_min) return defmm::set_error(DEFMM_ERR_ARG, "leaf range must satisfy 1 <= leaf_min <= leaf_max");
-    if (t.nrhs < 1) return defmm::set_error(DEFMM_ERR_ARG, "nrhs must be >= 1");
-    if (t.reps < 1) return defmm::set_error(DEFMM_ERR_ARG, "reps must be >= 1");
-    if (t.dtype != DEFMM_C64 && t.dtype != DEFMM_C128) return defmm::set_error(DEFMM_ERR_UNSUPPORTED, "dtype");
-    if (o.flags & DEFMM_PLAN_HOST_ONLY) return defmm::set_error(DEFMM_ERR_UNSUPPORTED, "autotuning needs a device plan");
-    if (order < 2 || order > 8) return defmm::set_error(DEFMM_ERR_ARG, "order must be in [2, 8]");
-    const bool same = (Y == nullptr) || (Y == X && ny == nx);
-    const int64_t nys = same ? nx : ny;
+defmm_status tune_with(const Factory& make, uint64_t key, int64_t nx, int64_t nys, int order,
+                       const defmm_tune_options& t, const defmm_options& o, void* stream, defmm_plan* out,
+                       defmm_tune_result* result) {
     cudaStream_t st = (cudaStream_t)stream;
-
     // candidates
     std::vector<int> leaves;
     for (int c : {16, 24, 32, 48, 64})
@@ -216,45 +189,13 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
         return v;
     };
 
-    // cache key: coordinates (host or device), sizes, parameters
-    Fnv key;
-    {
-        std::vector<double> hx((size_t)nx * 3), hy;
-        cudaPointerAttributes a{};
-        const bool dev = cudaPointerGetAttributes(&a, X) == cudaSuccess && a.type == cudaMemoryTypeDevice;
-        cudaGetLastError();
-        if (dev) {
-            cudaError_t e = cudaMemcpy(hx.data(), X, hx.size() * 8, cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) return defmm::set_error(DEFMM_ERR_CUDA, std::string("autotune: read X: ") + cudaGetErrorString(e));
-        } else {
-            std::memcpy(hx.data(), X, hx.size() * 8);
-        }
-        key.add(hx.data(), hx.size() * 8);
-        if (!same) {
-            hy.resize((size_t)ny * 3);
-            cudaPointerAttributes ay{};
-            const bool devy = cudaPointerGetAttributes(&ay, Y) == cudaSuccess && ay.type == cudaMemoryTypeDevice;
-            cudaGetLastError();
-            if (devy) {
-                cudaError_t e = cudaMemcpy(hy.data(), Y, hy.size() * 8, cudaMemcpyDeviceToHost);
-                if (e != cudaSuccess) return defmm::set_error(DEFMM_ERR_CUDA, std::string("autotune: read Y: ") + cudaGetErrorString(e));
-            } else {
-                std::memcpy(hy.data(), Y, hy.size() * 8);
-            }
-            key.add(hy.data(), hy.size() * 8);
-        }
-        key.val(nx); key.val(nys); key.val(same); key.val(kappa); key.val(order);
-        key.val(t.nrhs); key.val((int)t.dtype); key.val(t.leaf_min); key.val(t.leaf_max); key.val(t.tune_fft_n);
-        key.val(o.eta); key.val(o.hf_kw); key.val(o.fft_n); key.val(o.self_eps); key.val(o.damping); key.val(o.radial_power); key.val(o.m2l_chunk_blocks);
-    }
-
     defmm_tune_result res{};
     Choice hit;
-    if (cache_lookup(t.cache_path, key.h, &hit)) {
+    if (cache_lookup(t.cache_path, key, &hit)) {
         defmm_options oc = o;
         oc.fft_n = hit.fft_n;
         defmm_plan pl = nullptr;
-        defmm_status s = defmm_plan_create(X, nx, Y, ny, kappa, order, hit.leaf, &oc, stream, &pl);
+        defmm_status s = make(hit.leaf, oc, &pl);
         if (s != DEFMM_OK) return s;
         defmm_tuning tn{hit.rb, hit.tc ? 1 : 0, hit.mem, 0};
         s = defmm_plan_set_tuning(pl, &tn);
@@ -297,7 +238,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
             defmm_options oc = o;
             oc.fft_n = fft;
             defmm_plan pl = nullptr;
-            defmm_status s = defmm_plan_create(X, nx, Y, ny, kappa, order, leaf, &oc, stream, &pl);
+            defmm_status s = make(leaf, oc, &pl);
             if (s == DEFMM_ERR_OOM) continue;            // over the budget: not a candidate
             if (s != DEFMM_OK) { if (best) defmm_destroy(best); return s; }
             bool kept = false;
@@ -329,7 +270,7 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
     defmm_tuning tn{bc.rb, bc.tc ? 1 : 0, bc.mem, 0};
     defmm_status s = defmm_plan_set_tuning(best, &tn);
     if (s != DEFMM_OK) { defmm_destroy(best); return s; }
-    if (!cache_store(t.cache_path, key.h, bc)) {
+    if (!cache_store(t.cache_path, key, bc)) {
         defmm_destroy(best);
         return defmm::set_error(DEFMM_ERR_ARG, std::string("autotune: cannot append to ") + t.cache_path);
     }
@@ -340,6 +281,121 @@ defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, i
     if (result) *result = res;
     *out = best;
     return DEFMM_OK;
+}
+
+defmm_status check_tune_args(const defmm_tune_options& t, const defmm_options& o, int order) {
+    if (t.leaf_min < 1 || t.leaf_max < t.leaf_min) return defmm::set_error(DEFMM_ERR_ARG, "leaf range must satisfy 1 <= leaf_min <= leaf_max");
+    if (t.nrhs < 1) return defmm::set_error(DEFMM_ERR_ARG, "nrhs must be >= 1");
+    if (t.reps < 1) return defmm::set_error(DEFMM_ERR_ARG, "reps must be >= 1");
+    if (t.dtype != DEFMM_C64 && t.dtype != DEFMM_C128) return defmm::set_error(DEFMM_ERR_UNSUPPORTED, "dtype");
+    if (o.flags & DEFMM_PLAN_HOST_ONLY) return defmm::set_error(DEFMM_ERR_UNSUPPORTED, "autotuning needs a device plan");
+    if (order < 2 || order > 8) return defmm::set_error(DEFMM_ERR_ARG, "order must be in [2, 8]");
+    return DEFMM_OK;
+}
+
+// Host copy of n x 3 coordinates given in host or device memory.
+defmm_status host_points(const double* P, int64_t n, std::vector<double>& h) {
+    h.resize((size_t)n * 3);
+    cudaPointerAttributes a{};
+    const bool dev = cudaPointerGetAttributes(&a, P) == cudaSuccess && a.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    if (dev) {
+        cudaError_t e = cudaMemcpy(h.data(), P, h.size() * 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return defmm::set_error(DEFMM_ERR_CUDA, std::string("autotune: read points: ") + cudaGetErrorString(e));
+    } else {
+        std::memcpy(h.data(), P, h.size() * 8);
+    }
+    return DEFMM_OK;
+}
+
+void key_options(Fnv& key, const defmm_tune_options& t, const defmm_options& o, int order) {
+    key.val(order);
+    key.val(t.nrhs); key.val((int)t.dtype); key.val(t.leaf_min); key.val(t.leaf_max); key.val(t.tune_fft_n);
+    key.val(o.eta); key.val(o.hf_kw); key.val(o.fft_n); key.val(o.self_eps); key.val(o.damping); key.val(o.radial_power);
+    key.val(o.m2l_chunk_blocks);
+}
+
+}  // namespace
+
+extern "C" {
+
+void defmm_default_tune_options(defmm_tune_options* t) {
+    if (!t) return;
+    t->leaf_min = 16;
+    t->leaf_max = 64;
+    t->nrhs = 1;
+    t->dtype = DEFMM_C64;
+    t->reps = 5;
+    t->tune_fft_n = 1;
+    t->cache_path = nullptr;
+}
+
+defmm_status defmm_plan_autotune(const double* X, int64_t nx, const double* Y, int64_t ny, double kappa, int order,
+                                 const defmm_options* opt, const defmm_tune_options* topt, void* stream,
+                                 defmm_plan* out, defmm_tune_result* result) {
+    if (!out) return defmm::set_error(DEFMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!X || nx < 1) return defmm::set_error(DEFMM_ERR_ARG, "X is NULL or nx < 1");
+    defmm_tune_options t;
+    defmm_default_tune_options(&t);
+    if (topt) t = *topt;
+    defmm_options o;
+    defmm_default_options(&o);
+    if (opt) o = *opt;
+    defmm_status s = check_tune_args(t, o, order);
+    if (s != DEFMM_OK) return s;
+    const bool same = (Y == nullptr) || (Y == X && ny == nx);
+    const int64_t nys = same ? nx : ny;
+    // cache key: coordinates (host or device), sizes, parameters
+    Fnv key;
+    std::vector<double> h;
+    s = host_points(X, nx, h);
+    if (s != DEFMM_OK) return s;
+    key.add(h.data(), h.size() * 8);
+    if (!same) {
+        s = host_points(Y, ny, h);
+        if (s != DEFMM_OK) return s;
+        key.add(h.data(), h.size() * 8);
+    }
+    key.val(nx); key.val(nys); key.val(same); key.val(kappa);
+    key_options(key, t, o, order);
+    auto make = [&](int leaf, const defmm_options& oc, defmm_plan* pl) {
+        return defmm_plan_create(X, nx, Y, ny, kappa, order, leaf, &oc, stream, pl);
+    };
+    return tune_with(make, key.h, nx, nys, order, t, o, stream, out, result);
+}
+
+defmm_status defmm_plan_autotune_union(int ngeo, const double* const* X, const int64_t* nx, const double* kappa,
+                                       int order, const defmm_options* opt, const defmm_tune_options* topt,
+                                       void* stream, defmm_plan* out, defmm_tune_result* result) {
+    if (!out) return defmm::set_error(DEFMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (ngeo < 1 || !X || !nx || !kappa) return defmm::set_error(DEFMM_ERR_ARG, "need ngeo >= 1 and X, nx, kappa arrays");
+    defmm_tune_options t;
+    defmm_default_tune_options(&t);
+    if (topt) t = *topt;
+    defmm_options o;
+    defmm_default_options(&o);
+    if (opt) o = *opt;
+    defmm_status s = check_tune_args(t, o, order);
+    if (s != DEFMM_OK) return s;
+    Fnv key;
+    int64_t total = 0;
+    std::vector<double> h;
+    for (int g = 0; g < ngeo; ++g) {
+        if (!X[g] || nx[g] < 1) return defmm::set_error(DEFMM_ERR_ARG, "every geometry needs points (X[g] != NULL, nx[g] >= 1)");
+        s = host_points(X[g], nx[g], h);
+        if (s != DEFMM_OK) return s;
+        key.add(h.data(), h.size() * 8);
+        key.val(nx[g]); key.val(kappa[g]);
+        total += nx[g];
+    }
+    key.val(ngeo);
+    key_options(key, t, o, order);
+    auto make = [&](int leaf, const defmm_options& oc, defmm_plan* pl) {
+        return defmm_plan_create_union(ngeo, X, nx, kappa, order, leaf, &oc, stream, pl);
+    };
+    return tune_with(make, key.h, total, total, order, t, o, stream, out, result);
 }
 
 }  // extern "C"

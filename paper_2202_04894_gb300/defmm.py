@@ -24,6 +24,7 @@ EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_
             "defmm_destroy", "defmm_plan_info", "defmm_plan_table", "defmm_profile_enable",
             "defmm_profile_read", "defmm_apply_noalloc", "defmm_plan_set_tuning",
             "defmm_plan_get_tuning", "defmm_default_tune_options", "defmm_plan_autotune",
+            "defmm_plan_autotune_union",
             "defmm_default_gmres_options", "defmm_gmres", "defmm_plan_set_shard", "defmm_plan_shard_range",
             "defmm_plan_create_union", "defmm_selftest_bounded_wait", "defmm_plan_save", "defmm_plan_load",
             "defmm_last_error"]
@@ -128,6 +129,11 @@ def lib():
                                           ctypes.POINTER(TuneOptions), vp, ctypes.POINTER(vp),
                                           ctypes.POINTER(TuneResult)]
         L.defmm_plan_autotune.restype = ctypes.c_int
+        L.defmm_plan_autotune_union.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                                ctypes.POINTER(dbl), ctypes.c_int, ctypes.POINTER(Options),
+                                                ctypes.POINTER(TuneOptions), vp, ctypes.POINTER(vp),
+                                                ctypes.POINTER(TuneResult)]
+        L.defmm_plan_autotune_union.restype = ctypes.c_int
         L.defmm_default_gmres_options.argtypes = [ctypes.POINTER(GmresOptions)]
         L.defmm_default_gmres_options.restype = None
         L.defmm_gmres.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(GmresOptions), vp,
@@ -412,3 +418,33 @@ def union_plan(geometries, kappas, order=4, leaf_size=64, stream=None, **options
     plan._keep = None
     plan.nx = plan.ny = int(sum(P.shape[0] for P in pts))
     return plan
+
+
+def autotune_union(geometries, kappas, order=4, nrhs=1, dtype=C64, leaf_range=(16, 64), reps=5,
+                   tune_fft_n=True, cache_path=None, stream=None, **options):
+    """defmm_plan_autotune_union: the fastest candidate union plan of these geometries.
+
+    Returns (plan, choice) like ``autotune``; the plan is a union plan (nx = ny =
+    the total point count)."""
+    pts = [Plan._points(X) for X in geometries]
+    n = len(pts)
+    if len(kappas) != n:
+        raise ValueError("one kappa per geometry")
+    opt = default_options(**options)
+    t = TuneOptions()
+    lib().defmm_default_tune_options(ctypes.byref(t))
+    t.leaf_min, t.leaf_max = int(leaf_range[0]), int(leaf_range[1])
+    t.nrhs, t.dtype, t.reps, t.tune_fft_n = int(nrhs), int(dtype), int(reps), 1 if tune_fft_n else 0
+    t.cache_path = None if cache_path is None else os.fsencode(cache_path)
+    xs = (ctypes.c_void_p * n)(*[ctypes.c_void_p(P.data_ptr()) for P in pts])
+    ns = (ctypes.c_int64 * n)(*[P.shape[0] for P in pts])
+    ks = (ctypes.c_double * n)(*[float(k) for k in kappas])
+    h = ctypes.c_void_p()
+    r = TuneResult()
+    _check(lib().defmm_plan_autotune_union(n, xs, ns, ks, int(order), ctypes.byref(opt), ctypes.byref(t),
+                                           _stream_handle(stream), ctypes.byref(h), ctypes.byref(r)))
+    plan = Plan.__new__(Plan)
+    plan._h = h
+    plan._keep = None
+    plan.nx = plan.ny = int(sum(P.shape[0] for P in pts))
+    return plan, {name: getattr(r, name) for name, _ in TuneResult._fields_}

@@ -63,3 +63,25 @@ def test_autotune_choice_cache_and_results(tmp_path):
                             tune_fft_n=False, cache_path=str(cache))
     assert c4["candidates"] == 2 * (4 + 2 + 2) and c4["p2p_tensor_cores"] in (0, 1)
     assert p8.tuning()["p2p_tc_min_rhs"] == (1 if c4["p2p_tensor_cores"] else 0)
+
+
+def test_autotune_union_plan(tmp_path):
+    """A union of uneven geometries tuned as one plan: the choice is a candidate,
+    the tuned union equals an untuned union with that choice bit for bit, and the
+    cache rebuilds it without timing."""
+    geos = [W.points("sphere", 9000, 141), W.points("ellipsoid", 4000, 142), W.points("box", 6000, 143)]
+    kappas = [12.0, 30.0, 20.0]
+    total = sum(len(g) for g in geos)
+    q = torch.from_numpy(W.charges(total, 144)[:, 0]).to("cuda").to(torch.complex64)
+    cache = tmp_path / "tune_u.txt"
+    plan, choice = defmm.autotune_union(geos, kappas, order=4, leaf_range=(32, 64), reps=3, cache_path=str(cache))
+    assert choice["from_cache"] == 0 and choice["candidates"] > 0
+    assert choice["leaf_size"] in (32, 48, 64) and choice["fft_n"] in (0, 8)
+    assert plan.nx == total
+    tuned = plan.apply(q).cpu().numpy()
+    ref = defmm.union_plan(geos, kappas, order=4, leaf_size=choice["leaf_size"], fft_n=choice["fft_n"])
+    ref.set_tuning(m2l_members_per_block=choice["m2l_members_per_block"])
+    assert np.array_equal(ref.apply(q).cpu().numpy(), tuned)
+    again, c2 = defmm.autotune_union(geos, kappas, order=4, leaf_range=(32, 64), reps=3, cache_path=str(cache))
+    assert c2["from_cache"] == 1 and c2["leaf_size"] == choice["leaf_size"]
+    assert np.array_equal(again.apply(q).cpu().numpy(), tuned)
