@@ -678,7 +678,11 @@ def bench_serve(args):
             lat_f, wall_f = run(stream)
             curve.append({"load": frac, "mean_gap_ms": gap, "p50_ms": pct(lat_f, 0.5), "p99_ms": pct(lat_f, 0.99),
                           "served": work_of(stream) / wall_f / 1e6, "requests": len(stream)})
+    st0 = srv.stats()   # the stated stream alone in the server counters below
     lat, wall = run(reqs)
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
     work = work_of(reqs)
     srt = sorted(lat)
     offered = sum(plans[g].nx * r for _, g, r in reqs) / (reqs[-1][0] * 1e-3) / 1e6
