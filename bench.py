@@ -302,8 +302,8 @@ def main():
     if args.impl == "reference":
         reference_arm(args)
         return
-    if args.workload in ("batch48", "serve16"):
-        (bench_batch if args.workload == "batch48" else bench_serve)(args)
+    if args.workload in ("batch48", "batch48small", "serve16"):
+        (bench_serve if args.workload == "serve16" else bench_batch)(args)
         return
 
     import torch
@@ -526,7 +526,7 @@ def bench_batch(args):
     import __graft_entry__
     from paper_2202_04894_gb300 import defmm, serve, workloads as W
     __graft_entry__.build()
-    geos = W.geometry_set(**W.BATCH48)
+    geos = W.geometry_set(**(W.BATCH48_SMALL if args.workload == "batch48small" else W.BATCH48))
     plans, plan_s = _plans_of(geos, defmm, W)
     c64 = torch.complex64
     qs = [torch.from_numpy(np.ascontiguousarray(W.charges(p.ny, g["seed"]))).to("cuda").to(c64)
@@ -594,14 +594,21 @@ def bench_batch(args):
     u_avg, g_avg, s_avg = statistics.mean(u_ms), statistics.mean(g_ms), statistics.mean(s_ms)
     info = b.info()
     u_launches = int(uni.info()["launches_per_apply"])
+    uni.profile(True)   # phase times of one union apply (events on its stream), after the timed steps
+    union()
+    torch.cuda.synchronize()
+    u_phases = uni.phase_ms()
+    uni.profile(False)
+    bset = W.BATCH48_SMALL if args.workload == "batch48small" else W.BATCH48
     line = {"metric": METRIC, "value": points / (u_avg * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": u_avg, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": "batch48", "geometries": len(plans), "points": points,
-                       "n_range": list(W.BATCH48["n_range"]), "kappa_d_range": list(W.BATCH48["kd_range"]),
+            "config": {"workload": args.workload, "geometries": len(plans), "points": points,
+                       "n_range": list(bset["n_range"]), "kappa_d_range": list(bset["kd_range"]),
                        "order": 4, "leaf": 64, "nrhs": 1, "form": "union plan (one launch per phase)",
                        "l2": "flushed (512 MB write) before each step", "parallelism": "single"},
-            "union": {"kernel_launches": u_launches, "plan_s": union_s, "bitwise_equal_to_individual": union_bitwise},
+            "union": {"kernel_launches": u_launches, "plan_s": union_s, "bitwise_equal_to_individual": union_bitwise,
+                      "phase_ms": u_phases},
             "graph": {"ms_per_step": g_avg, "value": points / (g_avg * 1e-3) / 1e6, "branches": args.branches,
                       "kernel_launches": info["kernel_launches"], "graph_nodes": info["graph_nodes"]},
             "sequential": {"ms_per_step": s_avg, "value": points / (s_avg * 1e-3) / 1e6},

@@ -182,6 +182,8 @@ def make_geometry(g: dict):
 # 48 uneven geometries applied together: N log-uniform in [2*10^4, 8*10^5],
 # kappa*D log-uniform in [16, 256], order 4, one complex64 right-hand side each.
 BATCH48 = dict(count=48, seed0=100, n_range=(2e4, 8e5), kd_range=(16.0, 256.0), orders=(4,))
+# the same recipe with small geometries (2*10^4 to 5*10^4 points), where launch gaps weigh most
+BATCH48_SMALL = dict(count=48, seed0=100, n_range=(2e4, 5e4), kd_range=(16.0, 64.0), orders=(4,))
 # 16 resident geometries for the request server: N log-uniform in
 # [5*10^4, 2*10^6], kappa*D log-uniform in [32, 256], order 4, 5 or 6.
 SERVE16 = dict(count=16, seed0=200, n_range=(5e4, 2e6), kd_range=(32.0, 256.0), orders=(4, 5, 6))
