@@ -393,7 +393,9 @@ typedef struct {
     size_t plan_bytes;                /* device bytes held by the plan tables */
     size_t workspace_bytes;           /* device bytes of the current workspace */
     int64_t launches_per_apply;       /* kernels launched by the last apply (0 before any) */
-    int64_t device_error;             /* 1 if a bounded device-side wait of an apply gave up
+    int64_t device_error;             /* 1 if a bounded device-side wait of an apply gave up,
+                                         2 if a table index was out of range (only a
+                                         bounds-checked build, DEFMM_CHECKED, tests them)
                                          (that apply's results are invalid); this call
                                          synchronises with the device to read it */
     double d_aabb;                    /* side of the smallest box holding X, Y */

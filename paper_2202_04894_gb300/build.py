@@ -46,18 +46,26 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles every translation unit and links ``libdefmm.so``; returns its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compiles every translation unit and links ``libdefmm.so``; returns its path.
+
+    checked=True builds ``libdefmm_checked.so`` instead (objects in their own
+    folder): every CUDA unit compiled with DEFMM_CHECKED, so the kernels test
+    the table indices they follow and raise the plan's error flag (value 2) on
+    one out of range instead of reading outside a table."""
+    lib = LIB if not checked else os.path.join(HERE, "libdefmm_checked.so")
+    bdir = BUILD if not checked else BUILD + "_checked"
+    extra = [] if not checked else ["-DDEFMM_CHECKED"]
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     procs, objs = [], []
     for src, tool in SOURCES:
-        obj = os.path.join(BUILD, src.rsplit(".", 1)[0] + ".o")
+        obj = os.path.join(bdir, src.rsplit(".", 1)[0] + ".o")
         path = os.path.join(CSRC, src)
         if tool == "nvcc":
-            cmd = [nvcc] + NVCC_FLAGS + ["-c", path, "-o", obj]
+            cmd = [nvcc] + NVCC_FLAGS + extra + ["-c", path, "-o", obj]
         else:
             cmd = ["g++"] + CXX_FLAGS + ["-c", path, "-o", obj]
         if verbose:
@@ -68,13 +76,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         out, _ = pr.communicate()
         if pr.returncode != 0:
             raise RuntimeError("compile failed: %s\n%s" % (" ".join(cmd), out.decode(errors="replace")))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl"]
     out = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if out.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(cmd), out.stdout.decode(errors="replace")))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -268,6 +268,9 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.cs_level = (const int32_t*)P(o_csl); c.cs_corner = (const double*)P(o_csc);
     c.level_side = (const double*)P(o_lside);
     c.err_flag = (int*)P(o_err);
+    c.n_cell_t = hp.tt.ncell(); c.n_cell_s = hp.ts().ncell();
+    c.n_mult = hp.nM(); c.n_local = hp.nL();
+    c.n_slot = (int64_t)hp.slot_level.size(); c.n_spec = (int64_t)hp.spec_level.size();
     c.m_first = (const int32_t*)P(o_mf); c.m_count = (const int32_t*)P(o_mc); c.m_slot = (const int32_t*)P(o_ms);
     c.l_first = (const int32_t*)P(o_lf); c.l_count = (const int32_t*)P(o_lc); c.l_slot = (const int32_t*)P(o_ls);
     c.slot_u = (const double*)P(o_su);
@@ -807,6 +810,7 @@ defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host,
     CK(cudaStreamSynchronize(st), "apply");
     int flag = 0;
     CK(cudaMemcpy(&flag, plan->common.err_flag, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+    if (flag == 2) return fail(DEFMM_ERR_CUDA, "a table index out of range (checked build; results invalid)");
     if (flag) return fail(DEFMM_ERR_TIMEOUT, "a bounded device wait gave up (results invalid)");
     return DEFMM_OK;
 }

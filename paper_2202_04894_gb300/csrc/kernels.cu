@@ -115,22 +115,24 @@ __device__ __forceinline__ double eps_of(const DevCommon& c, int cell) {
 // ------------------------------------------------------------------ gather / scatter
 template <typename C>
 __global__ void k_gather(const C* __restrict__ q, C* __restrict__ qs, const int64_t* __restrict__ perm,
-                         int64_t n, int R) {
+                         int64_t n, int R, int* err_flag) {
+    const struct { int* err_flag; } c{err_flag};   // for the checked-build index test
     int64_t total = n * R;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t r = i / n, j = i - r * n;
-        qs[i] = q[r * n + perm[j]];
+        qs[i] = q[r * n + DEFMM_IX(c, perm[j], n)];
     }
 }
 
 template <typename C>
 __global__ void k_scatter(const C* __restrict__ ps, C* __restrict__ p, const int64_t* __restrict__ perm,
-                          int64_t n, int R, int64_t j0, int64_t j1) {
+                          int64_t n, int R, int64_t j0, int64_t j1, int* err_flag) {
+    const struct { int* err_flag; } c{err_flag};   // for the checked-build index test
     // sorted targets j0 <= j < j1 (all of them unless the plan computes one shard)
     const int64_t m = j1 - j0, total = m * R;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t r = i / m, j = j0 + (i - r * m);
-        p[r * n + perm[j]] = ps[r * n + j];
+        p[r * n + DEFMM_IX(c, perm[j], n)] = ps[r * n + j];
     }
 }
 
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
     __shared__ C sq[RB][128];
     __shared__ C red[4][64][RB];
     const int u = c.sh_unit ? c.sh_unit[blockIdx.x] : (int)blockIdx.x;   // work unit (of the shard)
-    const int cell = c.p2p_leaf[c.p2p_unit_leaf[u]];
+    const int cell = DEFMM_IX(c, c.p2p_leaf[DEFMM_IX(c, c.p2p_unit_leaf[u], c.n_p2p_leaf)], c.n_cell_t);
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
     const double side = c.level_side[c.ct_level[cell]];
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
 #pragma unroll
         for (int r = 0; r < RB; ++r) { acca[r] = czero<C>(); accb[r] = czero<C>(); }
         for (int rr = r0; rr < r1; ++rr) {
-            const int sb = c.p2p_sbeg[rr], se = c.p2p_send[rr];
+            const int sb = DEFMM_IX(c, c.p2p_sbeg[rr], c.ny + 1), se = DEFMM_IX(c, c.p2p_send[rr], c.ny + 1);
             for (int s0 = sb; s0 < se; s0 += 128) {
                 const int ns = min(128, se - s0);
                 __syncthreads();
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(128, RB == 1 ? 8 : 1) k_p2p_f32(DevCommon c, c
     __shared__ float2 red[RB][128];
     __shared__ int rbeg[kP2PRanges], roff[kP2PRanges + 1];
     const int u = c.sh_unit ? c.sh_unit[blockIdx.x] : (int)blockIdx.x;   // work unit (of the shard)
-    const int cell = c.p2p_leaf[c.p2p_unit_leaf[u]];
+    const int cell = DEFMM_IX(c, c.p2p_leaf[DEFMM_IX(c, c.p2p_unit_leaf[u], c.n_p2p_leaf)], c.n_cell_t);
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
     const int nr = min(RB, R - rb0);
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(128, RB == 1 ? 8 : 1) k_p2p_f32(DevCommon c, c
             float2 nq[RB];
             auto fetch = [&](int f0) {
                 if (f0 + (int)threadIdx.x < total) {
-                    const int64_t j = source_of(f0 + threadIdx.x);
+                    const int64_t j = DEFMM_IX(c, (int64_t)source_of(f0 + threadIdx.x), c.ny);
                     nh = c.Yh[j];
                     nl = c.Yl[j];
 #pragma unroll
@@ -509,7 +511,7 @@ void launch_p2p_f32(int rb, unsigned nu, const DevCommon& c, const float2* qs, f
 template <typename C>
 __global__ void __launch_bounds__(128) k_p2p_reduce(DevCommon c, const C* __restrict__ part, C* __restrict__ ps, int R) {
     const int li = c.sh_leaf ? c.sh_leaf[blockIdx.x] : (int)blockIdx.x;  // leaf (of the shard)
-    const int cell = c.p2p_leaf[li];
+    const int cell = DEFMM_IX(c, c.p2p_leaf[li], c.n_cell_t);
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int u0 = c.p2p_leaf_off[li], u1 = c.p2p_leaf_off[li + 1];
     for (int r = 0; r < R; ++r)
@@ -538,14 +540,14 @@ __global__ void __launch_bounds__(128) k_p2m(DevCommon c, DevTyped<T> t, const t
     T* lag = reinterpret_cast<T*>(smem_raw);
     const int p = PC ? PC : c.p, P3 = p * p * p;
     C* qm = reinterpret_cast<C*>(smem_raw + (((size_t)kP2MChunk * 3 * p * sizeof(T) + 15) / 16) * 16);
-    const int cell = c.p2m_cells[blockIdx.x];
+    const int cell = DEFMM_IX(c, c.p2m_cells[blockIdx.x], c.n_cell_s);
     const int b = c.cs_beg[cell], e = c.cs_end[cell];
     const double side = c.level_side[c.cs_level[cell]];
     const double h = side / (p - 1);
     const double cor[3] = {c.cs_corner[3 * cell], c.cs_corner[3 * cell + 1], c.cs_corner[3 * cell + 2]};
     const int nr = min(RB, R - rb0);
     const T k2pi = (T)(kappa_of(c, cell) * kInv2Pi);
-    const int ex0 = c.m_first[cell], nex = c.m_count[cell];
+    const int ex0 = DEFMM_IX(c, c.m_first[cell], c.n_mult + 1), nex = DEFMM_IX(c, c.m_count[cell], c.n_mult - ex0 + 1);
     for (int e0 = 0; e0 < nex; e0 += epass) {
         const int ne = min(epass, nex - e0);
         // outputs of this thread: (expansion, node) pairs o = threadIdx.x + 128 v (ne * P3 <= 16 * 128)
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(128) k_p2m(DevCommon c, DevTyped<T> t, const t
             }
             for (int idx = threadIdx.x; idx < ne * nj; idx += blockDim.x) {
                 const int ee = idx / nj, j = idx - ee * nj;
-                const int slot = c.m_slot[ex0 + e0 + ee];
+                const int slot = DEFMM_IX(c, c.m_slot[ex0 + e0 + ee] + 1, c.n_slot + 1) - 1;
                 C ph = mk((T)1, (T)0);
                 if (slot >= 0) {
                     T arg = 0;
@@ -608,7 +610,7 @@ __global__ void __launch_bounds__(128) k_p2m(DevCommon c, DevTyped<T> t, const t
             if (o < nout) {
                 const int ee = o / P3, a = o - ee * P3;
                 const int ex = ex0 + e0 + ee;
-                const int slot = c.m_slot[ex];
+                const int slot = DEFMM_IX(c, c.m_slot[ex] + 1, c.n_slot + 1) - 1;
                 C ph = mk((T)1, (T)0);
                 if (slot >= 0) {
                     const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
@@ -660,8 +662,8 @@ __global__ void __launch_bounds__(256) k_m2m(DevCommon c, DevTyped<T> t, const i
     C* Ps = B + P3;          // [3][p]
     C* Qs = Ps + 24;         // [3][2][p]
     const int32_t* ent = list + 9 * item;
-    const int ep = ent[0];
-    const int slot = c.m_slot[ep];
+    const int ep = DEFMM_IX(c, ent[0], c.n_mult);
+    const int slot = DEFMM_IX(c, c.m_slot[ep] + 1, c.n_slot + 1) - 1;
     for (int i = lane; i < 3 * p; i += 32) Ps[i] = slot >= 0 ? t.slot_P[(int64_t)slot * 3 * p + i] : mk((T)1, (T)0);
     for (int i = lane; i < 6 * p; i += 32) Qs[i] = slot >= 0 ? t.slot_Q[(int64_t)slot * 6 * p + i] : mk((T)1, (T)0);
     __syncwarp();
@@ -671,7 +673,7 @@ __global__ void __launch_bounds__(256) k_m2m(DevCommon c, DevTyped<T> t, const i
 #pragma unroll
         for (int v = 0; v < 16; ++v) acc[v] = czero<C>();
         for (int o = 0; o < 8; ++o) {
-            const int ce = ent[1 + o];
+            const int ce = ent[1 + o] < 0 ? -1 : DEFMM_IX(c, ent[1 + o], c.n_mult);
             if (ce < 0) continue;
             const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
             const T* mx = m1s + ox * p * p;
@@ -741,7 +743,7 @@ __global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const t
     C* A = reinterpret_cast<C*>(smem_raw) + (size_t)warp * (P3 + p * p * N + p * N * N);
     C* B = A + P3;              // [bz][by][xi_x]   p*p*N
     C* D = B + p * p * N;       // [bz][xi_y][xi_x] p*N*N
-    const int e = c.m2f_list[item];
+    const int e = DEFMM_IX(c, c.m2f_list[item], c.n_mult);
     {   // this warp's right-hand side
         const int r = rr;
         for (int a = lane; a < P3; a += 32) A[a] = M[((int64_t)e * R + r) * P3 + a];
@@ -887,7 +889,7 @@ __global__ void __launch_bounds__(MAXT) k_m2l(DevCommon c, DevTyped<T> t, const 
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bars[st], (uint32_t)nb * blk_bytes);
         for (int b = 0; b < nb; ++b) {
-            const int id = c.chk_blk[b0 + b];
+            const int id = DEFMM_IX(c, c.chk_blk[b0 + b], b < nsp ? c.n_spec : c.n_m2f);
             const C* src = b < nsp ? t.spec + (int64_t)id * NFpad : Mhat + ((int64_t)id * R + r) * NFpad;
             tma_bulk_load(base + (size_t)b * NFpad, src, blk_bytes, &bars[st]);
         }
@@ -961,7 +963,7 @@ __global__ void __launch_bounds__(MAXT) k_m2l(DevCommon c, DevTyped<T> t, const 
                 T2[q] = s;
             }
             __syncthreads();
-            const int te = c.grp_members[mem0 + m];
+            const int te = DEFMM_IX(c, c.grp_members[mem0 + m], c.n_local);
             for (int a = threadIdx.x; a < P3; a += blockDim.x) {  // x, crop, 1/N^3
                 const int ax = a % p, rest = a / p;  // rest = az*p + ay
                 C s = czero<C>();
@@ -1082,7 +1084,7 @@ __global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c,
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_expect_tx(&full[st], (uint32_t)(nsp + (nb - nsp) * nrb) * blk_bytes);
                     for (int b = 0; b < nb; ++b) {
-                        const int id = c.chk_blk[b0 + b];
+                        const int id = DEFMM_IX(c, c.chk_blk[b0 + b], b < nsp ? c.n_spec : c.n_m2f);
                         if (b < nsp)
                             tma_bulk_load(base + (size_t)b * NFpad, t.spec + (int64_t)id * NFpad, blk_bytes, &full[st]);
                         else   // right-hand sides r0 .. r0+nrb-1 of one source: one contiguous copy
@@ -1158,7 +1160,7 @@ __global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c,
         // m uses its own arrays (aliasing the drained ring) and its TPM threads
         C* Tx = ring + (size_t)(member ? m : 0) * (NN * p + N * p * p);   // [z][y][ax]
         C* Ty = Tx + NN * p;                                               // [z][ay][ax]
-        const int te = member ? c.grp_members[mem0 + m] : 0;
+        const int te = member ? DEFMM_IX(c, c.grp_members[mem0 + m], c.n_local) : 0;
 #pragma unroll
         for (int rr = 0; rr < RB; ++rr) {
             if (rr >= nrb) break;
@@ -1251,7 +1253,7 @@ __global__ void __launch_bounds__(256) k_l2l(DevCommon c, DevTyped<T> t, const i
     C* Ps = B + P3;          // [3][p]
     C* Qs = Ps + 24;         // [3][2][p]
     const int32_t* ent = list + 4 * item;
-    const int ec = ent[0], o = ent[1], first = ent[2], cnt = ent[3];
+    const int ec = DEFMM_IX(c, ent[0], c.n_local), o = ent[1], first = ent[2], cnt = ent[3];
     const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
     const T* mx = m1s + ox * p * p;
     const T* my = m1s + oy * p * p;
@@ -1262,8 +1264,8 @@ __global__ void __launch_bounds__(256) k_l2l(DevCommon c, DevTyped<T> t, const i
 #pragma unroll
         for (int v = 0; v < 16; ++v) acc[v] = czero<C>();
         for (int k = 0; k < cnt; ++k) {
-            const int pe = par[first + k];
-            const int slot = c.l_slot[pe];
+            const int pe = DEFMM_IX(c, par[first + k], c.n_local);
+            const int slot = DEFMM_IX(c, c.l_slot[pe] + 1, c.n_slot + 1) - 1;
             __syncwarp();
             for (int i = lane; i < 3 * p; i += 32) Ps[i] = slot >= 0 ? t.slot_P[(int64_t)slot * 3 * p + i] : mk((T)1, (T)0);
             for (int i = lane; i < 6 * p; i += 32) Qs[i] = slot >= 0 ? t.slot_Q[(int64_t)slot * 6 * p + i] : mk((T)1, (T)0);
@@ -1324,7 +1326,7 @@ __global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const t
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* Ls = reinterpret_cast<C*>(smem_raw);            // [RB][epass][P3]
     C* red = Ls + (size_t)RB * epass * c.P3;            // [RB][128]
-    const int cell = c.l2p_cells[blockIdx.x];
+    const int cell = DEFMM_IX(c, c.l2p_cells[blockIdx.x], c.n_cell_t);
     const int b = c.ct_beg[cell], e = c.ct_end[cell];
     const double side = c.level_side[c.ct_level[cell]];
     const int p = PC ? PC : c.p, P3 = p * p * p;
@@ -1332,7 +1334,7 @@ __global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const t
     const double cor[3] = {c.ct_corner[3 * cell], c.ct_corner[3 * cell + 1], c.ct_corner[3 * cell + 2]};
     const int nr = min(RB, R - rb0);
     const T k2pi = (T)(kappa_of(c, cell) * kInv2Pi);
-    const int ex0 = c.l_first[cell], nex = c.l_count[cell];
+    const int ex0 = DEFMM_IX(c, c.l_first[cell], c.n_local + 1), nex = DEFMM_IX(c, c.l_count[cell], c.n_local - ex0 + 1);
     for (int t0 = b; t0 < e; t0 += 128) {
         const int nt = min(128, e - t0);
         const int splits = 128 / nt;
@@ -1354,7 +1356,7 @@ __global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const t
             for (int i = threadIdx.x; i < nr * ne * P3; i += blockDim.x) {
                 const int r = i / (ne * P3), rem = i - r * ne * P3, ee = rem / P3, a = rem - ee * P3;
                 const int ex = ex0 + e0 + ee;
-                const int slot = c.l_slot[ex];
+                const int slot = DEFMM_IX(c, c.l_slot[ex] + 1, c.n_slot + 1) - 1;
                 C v = L[((int64_t)ex * R + rb0 + r) * P3 + a];
                 if (slot >= 0) {
                     const int a0 = a % p, a1 = (a / p) % p, a2 = a / (p * p);
@@ -1366,7 +1368,7 @@ __global__ void __launch_bounds__(128) k_l2p(DevCommon c, DevTyped<T> t, const t
             __syncthreads();
             if (active) {
                 for (int ee = sj; ee < ne; ee += splits) {
-                    const int slot = c.l_slot[ex0 + e0 + ee];
+                    const int slot = DEFMM_IX(c, c.l_slot[ex0 + e0 + ee] + 1, c.n_slot + 1) - 1;
                     C E = mk((T)1, (T)0);
                     if (slot >= 0) {
                         const T arg = dc[0] * (T)c.slot_u[3 * slot] + dc[1] * (T)c.slot_u[3 * slot + 1] +
@@ -1458,14 +1460,14 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_p2m_warp(DevCommon c, DevTy
     unsigned char* base = smem_raw + (size_t)warp * (lag_bytes + (size_t)RB * epass * 32 * sizeof(C));
     T* lag = reinterpret_cast<T*>(base);                 // [32][3][PC]
     C* qm = reinterpret_cast<C*>(base + lag_bytes);      // [RB][epass][32]
-    const int cell = c.p2m_cells[li];
+    const int cell = DEFMM_IX(c, c.p2m_cells[li], c.n_cell_s);
     const int b = c.cs_beg[cell], e = c.cs_end[cell];
     const double side = c.level_side[c.cs_level[cell]];
     const double h = side / (PC - 1);
     const double cx = c.cs_corner[3 * cell], cy = c.cs_corner[3 * cell + 1], cz = c.cs_corner[3 * cell + 2];
     const int nr = min(RB, R - rb0);
     const T k2pi = (T)(kappa_of(c, cell) * kInv2Pi);
-    const int ex0 = c.m_first[cell], nex = c.m_count[cell];
+    const int ex0 = DEFMM_IX(c, c.m_first[cell], c.n_mult + 1), nex = DEFMM_IX(c, c.m_count[cell], c.n_mult - ex0 + 1);
     for (int e0 = 0; e0 < nex; e0 += epass) {
         const int ne = min(epass, nex - e0);
         const int nitems = ne * P2;
@@ -1506,7 +1508,7 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_p2m_warp(DevCommon c, DevTy
 #pragma unroll
                 for (int r = 0; r < RB; ++r) q[r] = r < nr ? qs[(int64_t)(rb0 + r) * c.ny + j] : czero<C>();
                 for (int ee = 0; ee < ne; ++ee) {
-                    const int slot = c.m_slot[ex0 + e0 + ee];
+                    const int slot = DEFMM_IX(c, c.m_slot[ex0 + e0 + ee] + 1, c.n_slot + 1) - 1;
                     C ph = mk((T)1, (T)0);
                     if (slot >= 0) {
                         const T arg = x0 * (T)c.slot_u[3 * slot] + x1 * (T)c.slot_u[3 * slot + 1] +
@@ -1557,7 +1559,7 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_p2m_warp(DevCommon c, DevTy
             if (js == 0 && it < nitems) {
                 const int ee = it / P2, rem = it - ee * P2;
                 const int ex = ex0 + e0 + ee;
-                const int slot = c.m_slot[ex];
+                const int slot = DEFMM_IX(c, c.m_slot[ex] + 1, c.n_slot + 1) - 1;
                 const C* P = t.slot_P + (int64_t)(slot < 0 ? 0 : slot) * 3 * PC;
                 const C p12 = slot >= 0 ? cmul(P[PC + rem % PC], P[2 * PC + rem / PC]) : mk((T)1, (T)0);
 #pragma unroll
@@ -1595,14 +1597,14 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_l2p_warp(DevCommon c, DevTy
     const int li = blockIdx.x * kLeafWarps + warp;
     if (li >= c.n_l2p) return;
     C* Ls = reinterpret_cast<C*>(smem_raw) + (size_t)warp * RB * epass * P3;   // [epass][RB][P3]
-    const int cell = c.l2p_cells[li];
+    const int cell = DEFMM_IX(c, c.l2p_cells[li], c.n_cell_t);
     const int b = c.ct_beg[cell], e = c.ct_end[cell];
     const double side = c.level_side[c.ct_level[cell]];
     const double h = side / (PC - 1);
     const double cx = c.ct_corner[3 * cell], cy = c.ct_corner[3 * cell + 1], cz = c.ct_corner[3 * cell + 2];
     const int nr = min(RB, R - rb0);
     const T k2pi = (T)(kappa_of(c, cell) * kInv2Pi);
-    const int ex0 = c.l_first[cell], nex = c.l_count[cell];
+    const int ex0 = DEFMM_IX(c, c.l_first[cell], c.n_local + 1), nex = DEFMM_IX(c, c.l_count[cell], c.n_local - ex0 + 1);
     for (int t0 = b; t0 < e; t0 += 32) {
         const bool act = t0 + lane < e;
         const int64_t j = act ? t0 + lane : t0;
@@ -1627,7 +1629,7 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_l2p_warp(DevCommon c, DevTy
             for (int i = lane; i < ne * nr * P3; i += 32) {
                 const int ee = i / (nr * P3), rem = i - ee * nr * P3, r = rem / P3, a = rem - r * P3;
                 const int ex = ex0 + e0 + ee;
-                const int slot = c.l_slot[ex];
+                const int slot = DEFMM_IX(c, c.l_slot[ex] + 1, c.n_slot + 1) - 1;
                 C v = L[((int64_t)ex * R + rb0 + r) * P3 + a];
                 if (slot >= 0) {
                     const int a0 = a % PC, a1 = (a / PC) % PC, a2 = a / (PC * PC);
@@ -1638,7 +1640,7 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_l2p_warp(DevCommon c, DevTy
             }
             __syncwarp();
             for (int ee = 0; ee < ne; ++ee) {
-                const int slot = c.l_slot[ex0 + e0 + ee];
+                const int slot = DEFMM_IX(c, c.l_slot[ex0 + e0 + ee] + 1, c.n_slot + 1) - 1;
                 C E = mk((T)1, (T)0);
                 if (slot >= 0) {
                     const T arg = x0 * (T)c.slot_u[3 * slot] + x1 * (T)c.slot_u[3 * slot + 1] + x2 * (T)c.slot_u[3 * slot + 2];
@@ -1816,7 +1818,7 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
     __shared__ int fail_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int u = c.sh_unit ? c.sh_unit[blockIdx.x] : (int)blockIdx.x;   // work unit (of the shard)
-    const int cell = c.p2p_leaf[c.p2p_unit_leaf[u]];
+    const int cell = DEFMM_IX(c, c.p2p_leaf[DEFMM_IX(c, c.p2p_unit_leaf[u], c.n_p2p_leaf)], c.n_cell_t);
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
     const int nr = min(32, R - rb0);
@@ -1890,7 +1892,7 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
             auto fetch = [&](int f) {
                 const int s = tid & 15;
                 int64_t j = -1;
-                if (f + s < total) j = source_of(f + s);
+                if (f + s < total) j = DEFMM_IX(c, (int64_t)source_of(f + s), c.ny);
                 if (tid < kTcSrc) {
                     pf_h = j >= 0 ? c.Yh[j] : make_float4(0.f, 0.f, 0.f, 0.f);
                     pf_l = j >= 0 ? c.Yl[j] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -2217,7 +2219,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     const int sms = sm_count() * 8;
     DEFMM_MARK();
     // gather charges into Morton order
-    k_gather<C><<<sms, 256, 0, stream>>>(reinterpret_cast<const C*>(q), w.qs, c.perm_s, c.ny, R);
+    k_gather<C><<<sms, 256, 0, stream>>>(reinterpret_cast<const C*>(q), w.qs, c.perm_s, c.ny, R, c.err_flag);
     DEFMM_CHECK_LAUNCH();
     DEFMM_MARK();
     // near field: work units write partial sums, reduced per target in fixed order
@@ -2353,7 +2355,7 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
     }
     if (!c.sh_on || c.sh_t1 > c.sh_t0)
         k_scatter<C><<<sms, 256, 0, stream>>>(w.ps, reinterpret_cast<C*>(p), c.perm_t, c.nx, R,
-                                              c.sh_on ? c.sh_t0 : 0, c.sh_on ? c.sh_t1 : c.nx);
+                                              c.sh_on ? c.sh_t0 : 0, c.sh_on ? c.sh_t1 : c.nx, c.err_flag);
     DEFMM_CHECK_LAUNCH();
     DEFMM_MARK();
 #undef DEFMM_CHECK_LAUNCH

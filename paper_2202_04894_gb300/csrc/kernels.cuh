@@ -81,7 +81,28 @@ struct DevCommon {
     // eps_self above).  Cell levels are global level ids into level_side.
     const int32_t* cell_geo;
     const double *geo_kappa, *geo_eps;
+    // table sizes, for the bounds checks of a checked build (DEFMM_CHECKED)
+    int64_t n_cell_t, n_cell_s, n_mult, n_local, n_slot, n_spec;
 };
+
+// A table index a kernel follows.  In a checked build (compiled with
+// DEFMM_CHECKED) an index outside [0, n) raises the plan's error flag with the
+// value 2 and is replaced by 0, so the access stays inside the table and no
+// control flow changes (no thread leaves a barrier or a wait behind); the
+// apply's results are then invalid and the host reports the flag.  Otherwise
+// the index is used as it is.
+#ifdef DEFMM_CHECKED
+__device__ __forceinline__ int64_t checked_index(int* flag, int64_t i, int64_t n) {
+    if (i < 0 || i >= n) {
+        atomicCAS(flag, 0, 2);
+        return 0;
+    }
+    return i;
+}
+#define DEFMM_IX(c, i, n) ((decltype(i))::defmm::checked_index((c).err_flag, (int64_t)(i), (int64_t)(n)))
+#else
+#define DEFMM_IX(c, i, n) (i)
+#endif
 
 // Tables in the arithmetic precision T.
 template <typename T>

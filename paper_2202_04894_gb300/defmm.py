@@ -90,12 +90,17 @@ _LIB = None
 
 
 def lib():
-    """Loads libdefmm.so (raises if it has not been built)."""
+    """Loads libdefmm.so (raises if it has not been built).  With the environment
+    variable DEFMM_LIBRARY=checked it loads libdefmm_checked.so instead, the
+    bounds-checked build (build.build(checked=True))."""
     global _LIB
     if _LIB is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libdefmm.so is not built; run __graft_entry__.build()")
-        L = ctypes.CDLL(LIB_PATH)
+        path = LIB_PATH
+        if os.environ.get("DEFMM_LIBRARY") == "checked":
+            path = os.path.join(os.path.dirname(LIB_PATH), "libdefmm_checked.so")
+        if not os.path.exists(path):
+            raise RuntimeError("%s is not built; run __graft_entry__.build()" % os.path.basename(path))
+        L = ctypes.CDLL(path)
         vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
         L.defmm_default_options.argtypes = [ctypes.POINTER(Options)]
         L.defmm_default_options.restype = None
