@@ -271,6 +271,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.n_cell_t = hp.tt.ncell(); c.n_cell_s = hp.ts().ncell();
     c.n_mult = hp.nM(); c.n_local = hp.nL();
     c.n_slot = (int64_t)hp.slot_level.size(); c.n_spec = (int64_t)hp.spec_level.size();
+    c.n_leaf_all = (int64_t)hp.p2p_leaf.size();
     c.m_first = (const int32_t*)P(o_mf); c.m_count = (const int32_t*)P(o_mc); c.m_slot = (const int32_t*)P(o_ms);
     c.l_first = (const int32_t*)P(o_lf); c.l_count = (const int32_t*)P(o_lc); c.l_slot = (const int32_t*)P(o_ls);
     c.slot_u = (const double*)P(o_su);
@@ -808,10 +809,13 @@ defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host,
     if (s != DEFMM_OK) return s;
     CK(cudaMemcpyAsync(p_host, pd, pb, cudaMemcpyDeviceToHost, st), "copy p to host");
     CK(cudaStreamSynchronize(st), "apply");
-    int flag = 0;
-    CK(cudaMemcpy(&flag, plan->common.err_flag, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
-    if (flag == 2) return fail(DEFMM_ERR_CUDA, "a table index out of range (checked build; results invalid)");
-    if (flag) return fail(DEFMM_ERR_TIMEOUT, "a bounded device wait gave up (results invalid)");
+    int flag[4] = {0, 0, 0, 0};
+    CK(cudaMemcpy(flag, plan->common.err_flag, sizeof(flag), cudaMemcpyDeviceToHost), "read error flag");
+    if (flag[0] == 2)
+        return fail(DEFMM_ERR_CUDA, "a table index out of range (checked build; results invalid): kernels.cu line " +
+                                        std::to_string(flag[1]) + ", index " + std::to_string(flag[2]) + ", size " +
+                                        std::to_string(flag[3]));
+    if (flag[0]) return fail(DEFMM_ERR_TIMEOUT, "a bounded device wait gave up (results invalid)");
     return DEFMM_OK;
 }
 

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(128) k_p2p(DevCommon c, const typename Cplx<T>
     __shared__ C sq[RB][128];
     __shared__ C red[4][64][RB];
     const int u = c.sh_unit ? c.sh_unit[blockIdx.x] : (int)blockIdx.x;   // work unit (of the shard)
-    const int cell = DEFMM_IX(c, c.p2p_leaf[DEFMM_IX(c, c.p2p_unit_leaf[u], c.n_p2p_leaf)], c.n_cell_t);
+    const int cell = DEFMM_IX(c, c.p2p_leaf[DEFMM_IX(c, c.p2p_unit_leaf[u], c.n_leaf_all)], c.n_cell_t);
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
     const double side = c.level_side[c.ct_level[cell]];
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(128, RB == 1 ? 8 : 1) k_p2p_f32(DevCommon c, c
     __shared__ float2 red[RB][128];
     __shared__ int rbeg[kP2PRanges], roff[kP2PRanges + 1];
     const int u = c.sh_unit ? c.sh_unit[blockIdx.x] : (int)blockIdx.x;   // work unit (of the shard)
-    const int cell = DEFMM_IX(c, c.p2p_leaf[DEFMM_IX(c, c.p2p_unit_leaf[u], c.n_p2p_leaf)], c.n_cell_t);
+    const int cell = DEFMM_IX(c, c.p2p_leaf[DEFMM_IX(c, c.p2p_unit_leaf[u], c.n_leaf_all)], c.n_cell_t);
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
     const int nr = min(RB, R - rb0);
@@ -1818,7 +1818,7 @@ __global__ void __launch_bounds__(128) k_p2p_tc(DevCommon c, const float2* __res
     __shared__ int fail_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int u = c.sh_unit ? c.sh_unit[blockIdx.x] : (int)blockIdx.x;   // work unit (of the shard)
-    const int cell = DEFMM_IX(c, c.p2p_leaf[DEFMM_IX(c, c.p2p_unit_leaf[u], c.n_p2p_leaf)], c.n_cell_t);
+    const int cell = DEFMM_IX(c, c.p2p_leaf[DEFMM_IX(c, c.p2p_unit_leaf[u], c.n_leaf_all)], c.n_cell_t);
     const int tb = c.ct_beg[cell], te = c.ct_end[cell];
     const int64_t pbase = c.p2p_part[u];
     const int nr = min(32, R - rb0);

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 namespace defmm {
 
@@ -83,23 +84,30 @@ struct DevCommon {
     const double *geo_kappa, *geo_eps;
     // table sizes, for the bounds checks of a checked build (DEFMM_CHECKED)
     int64_t n_cell_t, n_cell_s, n_mult, n_local, n_slot, n_spec;
+    int64_t n_leaf_all;   // near-field leaves of the whole operator (n_p2p_leaf counts a shard's)
 };
 
 // A table index a kernel follows.  In a checked build (compiled with
 // DEFMM_CHECKED) an index outside [0, n) raises the plan's error flag with the
-// value 2 and is replaced by 0, so the access stays inside the table and no
-// control flow changes (no thread leaves a barrier or a wait behind); the
-// apply's results are then invalid and the host reports the flag.  Otherwise
-// the index is used as it is.
+// value 2 (the first such index also records its source line, value and
+// bound in the flag's next three words) and is replaced by 0, so the access
+// stays inside the table and no control flow changes (no thread leaves a
+// barrier or a wait behind); the apply's results are then invalid and the host
+// reports the flag.  Otherwise the index is used as it is.
 #ifdef DEFMM_CHECKED
-__device__ __forceinline__ int64_t checked_index(int* flag, int64_t i, int64_t n) {
+__device__ __forceinline__ int64_t checked_index(int* flag, int64_t i, int64_t n, int line) {
     if (i < 0 || i >= n) {
-        atomicCAS(flag, 0, 2);
+        if (atomicCAS(flag, 0, 2) == 0) {
+            flag[1] = line;
+            flag[2] = (int)i;
+            flag[3] = (int)n;
+        }
         return 0;
     }
     return i;
 }
-#define DEFMM_IX(c, i, n) ((decltype(i))::defmm::checked_index((c).err_flag, (int64_t)(i), (int64_t)(n)))
+#define DEFMM_IX(c, i, n) \
+    ((std::remove_cv_t<std::remove_reference_t<decltype(i)>>)::defmm::checked_index((c).err_flag, (int64_t)(i), (int64_t)(n), __LINE__))
 #else
 #define DEFMM_IX(c, i, n) (i)
 #endif

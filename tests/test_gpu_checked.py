@@ -42,6 +42,12 @@ for kind, n, other, kd, order, leaf in cases:
     q = W.charges(len(X) if Y is None else len(Y), 23, nrhs=2)
     plan = defmm.Plan(X, Y, kappa=kappa, order=order, leaf_size=leaf)
     ref = oracle_fmm.fmm(X, q, kappa, order=order, leaf=leaf, Y=Y)
+    for dt in (np.complex128, np.complex64):   # the host-buffer apply names a failed index
+        try:
+            plan.apply_host(np.ascontiguousarray(q.astype(dt)))
+        except defmm.DefmmError as ex:
+            print("checked %s %d: %s" % (kind, n, ex))
+            raise
     e128, e64 = rel(gpu(plan, q, torch.complex128), ref), rel(gpu(plan, q, torch.complex64), ref)
     plan.set_tuning(p2p_tc_min_rhs=1, m2l_members_per_block=4)
     etc = rel(gpu(plan, q, torch.complex64), ref)
