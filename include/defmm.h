@@ -388,7 +388,7 @@ typedef struct {
     int64_t n_m2l_pairs, n_p2p_pairs;
     int64_t n_multipole, n_local;     /* effective expansions (Sec. 4.2.3) */
     int64_t n_fourier;                /* multipoles transformed by M2F */
-    int64_t n_spectra;                /* canonical spectra (Sec. 4.3), each stored in 6 axis orders */
+    int64_t n_spectra;                /* canonical spectra stored (Sec. 4.3) */
     int64_t p2p_interactions;         /* sum over near pairs of n_t * n_s */
     size_t plan_bytes;                /* device bytes held by the plan tables */
     size_t workspace_bytes;           /* device bytes of the current workspace */
@@ -422,9 +422,8 @@ defmm_status defmm_plan_info(defmm_plan plan, defmm_info* out);
  *       the M2L schedule: "grp_member_off", "grp_members" (CSR: group ->
  *       local expansion ids), "grp_chunk_off" (CSR: group -> chunks),
  *       "chk_blk_off", "chk_nspec", "chk_blk" (CSR: chunk -> staged blocks,
- *       its first chk_nspec are spectrum blocks, canonical spectrum id * 6 +
- *       the axis order of the pairs' permutation (each spectrum is stored in
- *       the 6 axis orders), the rest Fourier-multipole slots), "chk_op_off" (9 per chunk: op ranges of members 0..7, end),
+ *       its first chk_nspec are spectrum ids, the rest Fourier-multipole
+ *       slots), "chk_op_off" (9 per chunk: op ranges of members 0..7, end),
  *       "chk_op" (spectrum block | multipole block << 8 | symmetry code << 16;
  *       code bit a negates axis a, code >> 3 names the axis permutation),
  *       the near-field work units: "p2p_leaf" (near-field target leaf cells),

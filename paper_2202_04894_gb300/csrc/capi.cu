@@ -236,9 +236,9 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     size_t o_sl = b.add(hp.spec_level), o_sk = b.add(kbar);
     size_t nspec = hp.spec_level.size();
     size_t o_specd = b.add((const double2*)nullptr, 0);
-    b.bytes.resize(o_specd + kSpecOrders * nspec * hp.NFpad * sizeof(double2));   // every axis order
+    b.bytes.resize(o_specd + nspec * hp.NFpad * sizeof(double2));
     size_t o_specf = b.add((const float2*)nullptr, 0);
-    b.bytes.resize(o_specf + kSpecOrders * nspec * hp.NFpad * sizeof(float2));
+    b.bytes.resize(o_specf + nspec * hp.NFpad * sizeof(float2));
 
     size_t total = b.bytes.size();
     if (pl->hbm_budget && total + workspace_bytes<float>(hp, 1) > pl->hbm_budget)
@@ -270,7 +270,7 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.err_flag = (int*)P(o_err);
     c.n_cell_t = hp.tt.ncell(); c.n_cell_s = hp.ts().ncell();
     c.n_mult = hp.nM(); c.n_local = hp.nL();
-    c.n_slot = (int64_t)hp.slot_level.size(); c.n_spec = kSpecOrders * (int64_t)hp.spec_level.size();
+    c.n_slot = (int64_t)hp.slot_level.size(); c.n_spec = (int64_t)hp.spec_level.size();
     c.n_leaf_all = (int64_t)hp.p2p_leaf.size();
     c.m_first = (const int32_t*)P(o_mf); c.m_count = (const int32_t*)P(o_mc); c.m_slot = (const int32_t*)P(o_ms);
     c.l_first = (const int32_t*)P(o_lf); c.l_count = (const int32_t*)P(o_lc); c.l_slot = (const int32_t*)P(o_ls);

@@ -856,10 +856,15 @@ __global__ void __launch_bounds__(MAXT) k_m2l(DevCommon c, DevTyped<T> t, const 
     C* T2 = T1 + p * N * N;                    // [az][ay][xi_x]    p*p*N
     __shared__ __align__(8) uint64_t bars[kM2LMaxStages];
     __shared__ C tws[16];
+    __shared__ int stride[6][3];               // N^sigma(a) for each axis permutation
     const int g = c.sh_grp ? c.sh_grp[blockIdx.x] : (int)blockIdx.x;   // group (of the shard)
     const int mem0 = c.grp_member_off[g], nm = c.grp_member_off[g + 1] - mem0;
     const int ch0 = c.grp_chunk_off[g], nchunks = c.grp_chunk_off[g + 1] - ch0;
     if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
+    if (threadIdx.x < 18) {
+        const int q = kPermDev[threadIdx.x / 3][threadIdx.x % 3];
+        stride[threadIdx.x / 3][threadIdx.x % 3] = q == 0 ? 1 : (q == 1 ? N : N * N);
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
         mbar_fence_init();
@@ -920,9 +925,8 @@ __global__ void __launch_bounds__(MAXT) k_m2l(DevCommon c, DevTyped<T> t, const 
                 const int o1 = opoff[m + 1];
                 for (int o = opoff[m]; o < o1; ++o) {
                     const int op = c.chk_op[o];
-                    // the spectrum block is stored in the pair's axis order: plain strides
-                    const int code = op >> 16;
-                    const int s0 = 1, s1 = N, s2 = N * N;
+                    const int code = op >> 16, pid = code >> 3;
+                    const int s0 = stride[pid][0], s1 = stride[pid][1], s2 = stride[pid][2];
                     const C* gs = base + (size_t)(op & 255) * NFpad;
                     const C* ms = base + (size_t)((op >> 8) & 255) * NFpad;
 #pragma unroll
@@ -981,12 +985,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // 4, one half of a larger group (its own pass over the group's chunks, using
 // the ops of its members only).  Consumer thread (member m, lane l) of
 // the first MAXM*TPM threads owns the x-rows l + j*TPM (j < ROWS) of member m; row (y, z) = (l mod N,
-// l div N) holds the N samples xi = x + N*row.  A pair's spectrum block is
-// the canonical spectrum stored in the axis order of the pair's permutation
-// sigma (Sec. 4.3; six orders per spectrum, chosen at plan time), so its row
-// is contiguous like the multipole's: the sample at xi is
-// base(s_1 y, s_2 z) + (s_0 x mod N), the signs s only reflect coordinates,
-// and the row reads fall in distinct banks whatever the permutation.  RB
+// l div N) holds the N samples xi = x + N*row.  Under a pair's symmetry
+// (sigma, s) a row's permuted indices are base(y, z) + x*step (with a wrap
+// for a negated x), so the permutation costs one row base per pair.  RB
 // right-hand sides share a pass: a stage holds the chunk's spectra once and
 // RB consecutive right-hand sides of each source multipole (contiguous in
 // Mhat), so every gathered spectrum sample serves RB products.  The last warp
@@ -1010,6 +1011,7 @@ __global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c,
     C* ring = reinterpret_cast<C*>(smem_raw);
     __shared__ __align__(8) uint64_t full[kM2LMaxStages], empty[kM2LMaxStages];
     __shared__ C tws[16];
+    __shared__ int stride[6][3];
     __shared__ int abort_store, issued_sh, abort_at;
     volatile int& abort_sh = abort_store;   // written and polled by different warps
     int g = blockIdx.x, mb = 0;                  // group (of the shard), first member of this block
@@ -1039,6 +1041,10 @@ __global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c,
     }
     const int consumer_warps = nm * (TPM / 32);
     if (threadIdx.x < N) tws[threadIdx.x] = t.tw[threadIdx.x];
+    if (threadIdx.x < 18) {
+        const int q = kPermDev[threadIdx.x / 3][threadIdx.x % 3];
+        stride[threadIdx.x / 3][threadIdx.x % 3] = q == 0 ? 1 : (q == 1 ? N : N * N);
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -1107,9 +1113,8 @@ __global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c,
                     for (int o = o0; o < o1; ++o) {
                         const int op = op_next;
                         if (o + 1 < o1) op_next = __ldg(&c.chk_op[o + 1]);   // in flight during this pair
-                        // the spectrum block is stored in the pair's axis order: plain strides
-                        const int code = op >> 16;
-                        const int s0 = 1, s1 = N, s2 = NN;
+                        const int code = op >> 16, pid = code >> 3;
+                        const int s0 = stride[pid][0], s1 = stride[pid][1], s2 = stride[pid][2];
                         const C* gs = base + (size_t)(op & 255) * NFpad;
                         // source block b sits at nsp + (b - nsp) * RB blocks
                         const C* msrc = base + (size_t)(((op >> 8) & 255) * RB - msh) * NFpad;
@@ -1734,26 +1739,14 @@ __global__ void __launch_bounds__(256) k_spectra(const int32_t* __restrict__ spe
         A[i] = s;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < NF; i += blockDim.x) {  // z
+    for (int i = threadIdx.x; i < NFpad; i += blockDim.x) {  // z
         double2 s = make_double2(0.0, 0.0);
-        const int xy = i % (N * N), zz = i / (N * N);
-        for (int k = 0; k < N; ++k) cfma(s, A[k * N * N + xy], tw[(zz * k) % N]);
-        B[i] = s;
-    }
-    __syncthreads();
-    // every axis order: block sid * 6 + q holds the sample at canonical xi' under
-    // index xi'_{s(0)} + N xi'_{s(1)} + N^2 xi'_{s(2)}, s = permutation q (padding zero)
-    for (int i = threadIdx.x; i < kSpecOrders * NFpad; i += blockDim.x) {
-        const int q = i / NFpad, j = i - q * NFpad;
-        double2 v = make_double2(0.0, 0.0);
-        if (j < NF) {
-            const int c[3] = {j % N, (j / N) % N, j / (N * N)};   // c[a] = xi'_{s(a)}
-            int xi[3];
-            for (int a = 0; a < 3; ++a) xi[kPermDev[q][a]] = c[a];
-            v = B[(xi[2] * N + xi[1]) * N + xi[0]];
+        if (i < NF) {
+            const int xy = i % (N * N), zz = i / (N * N);
+            for (int k = 0; k < N; ++k) cfma(s, A[k * N * N + xy], tw[(zz * k) % N]);
         }
-        out_d[((int64_t)sid * kSpecOrders + q) * NFpad + j] = v;
-        out_f[((int64_t)sid * kSpecOrders + q) * NFpad + j] = make_float2((float)v.x, (float)v.y);
+        out_d[(int64_t)sid * NFpad + i] = s;
+        out_f[(int64_t)sid * NFpad + i] = make_float2((float)s.x, (float)s.y);
     }
 }
 

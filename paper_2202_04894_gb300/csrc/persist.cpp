@@ -23,8 +23,7 @@ namespace defmm {
 namespace {
 
 constexpr char kMagic[8] = {'D', 'E', 'F', 'M', 'M', 'P', 'L', 'N'};
-constexpr uint32_t kVersion = 4;   // 2: Levels field by field (no padding bytes); 3: radial power;
-                                   // 4: spectrum blocks per axis order
+constexpr uint32_t kVersion = 3;   // 2: Levels field by field (no padding bytes); 3: radial power
 
 // 64-bit FNV-1a over every byte after the header, stored at the end of the
 // file: a damaged plan file is refused instead of handing the kernels

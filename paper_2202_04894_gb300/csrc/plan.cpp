@@ -534,10 +534,8 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
                 members[g].push_back(te);
             }
             const int32_t s_cell = hp.m_cell[recs[i].src];
-            // the spectrum block: the canonical spectrum in the axis order of the pair's
-            // permutation (stored once per canonical offset and axis order, 6 per spectrum)
-            gops[grp_of_te[te]].push_back({slot_of_te[te], ts.parent[s_cell], hp.mhat_of_m[recs[i].src],
-                                           recs[i].spec * kSpecOrders + (recs[i].code >> 3), recs[i].code});
+            gops[grp_of_te[te]].push_back({slot_of_te[te], ts.parent[s_cell], hp.mhat_of_m[recs[i].src], recs[i].spec,
+                                           recs[i].code});
         }
         // heaviest groups first
         std::vector<int32_t> gorder(members.size());
@@ -878,7 +876,7 @@ void union_host_plans(std::vector<HostPlan>& parts, HostPlan& u) {
         const int32_t mb = (int32_t)u.m_cell.size();           // multipole base
         const int32_t eb = (int32_t)u.l_cell.size();           // local expansion base
         const int32_t sb = (int32_t)u.slot_level.size();       // phase-slot base
-        const int32_t spb = (int32_t)u.spec_level.size() * kSpecOrders;   // spectrum block base
+        const int32_t spb = (int32_t)u.spec_level.size();      // spectrum base
         const int32_t hb = (int32_t)u.m2f_list.size();         // Fourier-multipole base
         const int32_t gb = (int32_t)u.grp_member_off.size() - 1;
         const int32_t gmb = (int32_t)u.grp_members.size();

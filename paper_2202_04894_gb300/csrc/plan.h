@@ -20,11 +20,6 @@ constexpr int kNumLevels = kMaxLevel + 1;
 constexpr int kMaxOrder = 8;
 constexpr int kP2PUnitSources = 4096;
 constexpr int kP2PUnitRanges = 256;
-// Each canonical spectrum is stored in the 6 axis orders of the signed
-// permutations (Sec. 4.3): block sid * kSpecOrders + p holds it with the axis
-// that permutation p maps the target's x axis to innermost, so every row read
-// of the M2L is contiguous.
-constexpr int kSpecOrders = 6;
 
 struct Tree {
     std::vector<int64_t> perm;  // sorted position -> input index
@@ -117,8 +112,7 @@ struct HostPlan {
     std::vector<int32_t> grp_chunk_off;                 // CSR: group -> chunks
     std::vector<int32_t> grp_half;                      // blocks of <= 4 members: group * 2 + half
     std::vector<int32_t> chk_blk_off, chk_nspec;        // CSR: chunk -> blocks; spectra first
-    std::vector<int32_t> chk_blk;                       // spectrum block (id * kSpecOrders + axis order)
-                                                        // or Fourier-multipole slot
+    std::vector<int32_t> chk_blk;                       // spectrum id or Fourier-multipole slot
     std::vector<int32_t> chk_op_off;                    // 9 per chunk: op ranges of members 0..7, end
     std::vector<int32_t> chk_op;                        // spec_blk | mhat_blk << 8 | code << 16
     int32_t chk_max_blocks = 0;

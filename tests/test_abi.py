@@ -399,10 +399,7 @@ def test_m2l_schedule_covers_every_pair_once(kind, n, kd, order):
                     bs, bm, code = op & 255, (op >> 8) & 255, op >> 16
                     assert bs < ns <= bm < nb
                     sc, sd = mult[t["m2f_list"][t["chk_blk"][boff[ch] + bm]]]
-                    # spectrum blocks: canonical spectrum * 6 + the axis order of the pair's permutation
-                    sblk = t["chk_blk"][boff[ch] + bs]
-                    assert sblk % 6 == code >> 3
-                    lev, kbar = spec[sblk // 6, 0], spec[sblk // 6, 1:]
+                    lev, kbar = spec[t["chk_blk"][boff[ch] + bs], 0], spec[t["chk_blk"][boff[ch] + bs], 1:]
                     k = cells[tc, 1:4] - cells[sc, 1:4]
                     sigma = perms[code >> 3]
                     for a in range(3):
@@ -441,9 +438,7 @@ def test_m2l_schedule_of_a_large_plan():
     te = t["grp_members"][goff[group] + member]
     bs, bm, code = ops & 255, (ops >> 8) & 255, ops >> 16
     assert np.all(bs < nspec[chunk]) and np.all(nspec[chunk] <= bm) and np.all(bm < (boff[chunk + 1] - boff[chunk]))
-    sblk, slot = t["chk_blk"][boff[chunk] + bs], t["chk_blk"][boff[chunk] + bm]
-    assert np.all(sblk % 6 == code >> 3)     # the spectrum stored in the pair's axis order
-    sid = sblk // 6
+    sid, slot = t["chk_blk"][boff[chunk] + bs], t["chk_blk"][boff[chunk] + bm]
     tc, td = loc[te, 0], loc[te, 1]
     sc, sd = mult[t["m2f_list"][slot], 0], mult[t["m2f_list"][slot], 1]
     assert np.all(td == sd) and np.all(spec[sid, 0] == cells[tc, 0])
