@@ -262,6 +262,42 @@ static void dual_tree_traversal(HostPlan& hp) {
         }
 }
 
+// Threads for the plan's parallel passes: up to 8 (hardware permitting), or
+// DEFMM_PLAN_THREADS (1..8).
+static int plan_threads() {
+    int n = (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency()));
+    if (const char* env = std::getenv("DEFMM_PLAN_THREADS")) {
+        const int v = std::atoi(env);
+        if (v >= 1) n = std::min(v, 8);
+    }
+    return n;
+}
+
+// fn(begin, end) over nthreads equal slices of [0, n); slices whose thread cannot
+// be created run on this thread; an exception in any slice is rethrown here.
+static void parallel_slices(size_t n, int nthreads, const std::function<void(size_t, size_t)>& fn) {
+    nthreads = std::max(1, std::min<int>(nthreads, (int)std::max<size_t>(1, n)));
+    std::vector<std::exception_ptr> failed(nthreads);
+    auto run = [&](int j) {
+        try {
+            fn(n * j / nthreads, n * (j + 1) / nthreads);
+        } catch (...) {
+            failed[j] = std::current_exception();
+        }
+    };
+    std::vector<std::thread> pool;
+    int started = 1;
+    try {
+        for (; started < nthreads; ++started) pool.emplace_back(run, started);
+    } catch (...) {
+    }
+    run(0);
+    for (int j = started; j < nthreads; ++j) run(j);
+    for (auto& th : pool) th.join();
+    for (auto& e : failed)
+        if (e) std::rethrow_exception(e);
+}
+
 // ---------------------------------------------------------------- plan
 template <typename U> static bool units_for_leaf_empty(const std::vector<U>& units, int32_t li) {
     return units.empty() || units.back().leaf != li;
@@ -457,9 +493,21 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         const int64_t w = 2 * kmax[l] + 1;
         if (kmax[l] >= 0 && w * w * w <= (int64_t(1) << 22)) by_offset[l].assign((size_t)(w * w * w), -1);
     }
+    // the target and source expansion of every pair (independent per pair: slices on
+    // several threads), then the spectra in the order the pairs first use them (one pass)
+    recs.resize(hp.m2l.size());
+    parallel_slices(hp.m2l.size(), hp.m2l.size() >= ((size_t)1 << 20) ? plan_threads() : 1,
+                    [&](size_t i0, size_t i1) {
+        for (size_t i = i0; i < i1; ++i) {
+            const auto& pr = hp.m2l[i];
+            const int32_t te = find_exp(hp.l_dir, hp.l_first[pr[0]], hp.l_count[pr[0]], pr[2]);
+            const int32_t se = find_exp(hp.m_dir, hp.m_first[pr[1]], hp.m_count[pr[1]], pr[2]);
+            recs[i] = {te, se, 0, 0, (int32_t)i};
+        }
+    });
     for (size_t i = 0; i < hp.m2l.size(); ++i) {
         auto& pr = hp.m2l[i];
-        int32_t t = pr[0], s = pr[1], u = pr[2];
+        int32_t t = pr[0], s = pr[1];
         int l = tt.level[t];
         int64_t kx = (int64_t)tt.ix[t] - ts.ix[s], ky = (int64_t)tt.iy[t] - ts.iy[s],
                 kz = (int64_t)tt.iz[t] - ts.iz[s];
@@ -476,11 +524,11 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         } else {
             sid = spectrum_of(l, kx, ky, kz, &code);
         }
-        int32_t te = find_exp(hp.l_dir, hp.l_first[t], hp.l_count[t], u);
-        int32_t se = find_exp(hp.m_dir, hp.m_first[s], hp.m_count[s], u);
-        if (te < 0 || se < 0) throw std::runtime_error("internal: M2L expansion missing");
-        is_src[se] = 1;
-        recs.push_back({te, se, sid, code, (int32_t)i});
+        PairRec& r = recs[i];
+        if (r.tgt < 0 || r.src < 0) throw std::runtime_error("internal: M2L expansion missing");
+        r.spec = sid;
+        r.code = code;
+        is_src[r.src] = 1;
     }
     hp.mhat_of_m.assign(hp.m_cell.size(), -1);
     for (size_t e = 0; e < hp.m_cell.size(); ++e)
@@ -488,15 +536,6 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
             hp.mhat_of_m[e] = (int32_t)hp.m2f_list.size();
             hp.m2f_list.push_back((int32_t)e);
         }
-    {   // stable counting sort of the pair records by target expansion
-        std::vector<int64_t> at(hp.l_cell.size() + 1, 0);
-        for (const PairRec& r : recs) ++at[(size_t)r.tgt + 1];
-        for (size_t e = 1; e < at.size(); ++e) at[e] += at[e - 1];
-        std::vector<PairRec> by_tgt(recs.size());
-        for (const PairRec& r : recs) by_tgt[(size_t)at[r.tgt]++] = r;
-        recs.swap(by_tgt);
-    }
-
     // ---- M2L groups and chunks (sibling targets sharing a father and a direction)
     {
         // blocks per chunk: about 22 KB of complex64 for N <= 8; for longer DFTs
@@ -508,39 +547,49 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         struct Op { int32_t member, src_parent, src, spec, code; };
         std::unordered_map<int64_t, int32_t> group_of;   // (father cell, direction) -> group
         std::vector<std::vector<int32_t>> members;        // local expansion ids
-        std::vector<std::vector<Op>> gops;
-        // group and member slot of each target expansion, fixed at its first pair
-        // (records come sorted by target, so groups and members are numbered in
-        // the order their first pair appears)
+        // group and member slot of each target expansion, in increasing target
+        // expansion order (groups and members numbered in that order)
         std::vector<int32_t> grp_of_te(hp.l_cell.size(), -1), slot_of_te(hp.l_cell.size(), -1);
-        for (size_t i = 0; i < recs.size(); ++i) {
-            const int32_t te = recs[i].tgt;
-            if (grp_of_te[te] < 0) {
-                const int32_t t = hp.l_cell[te], u = hp.l_dir[te];
-                const int64_t key = (int64_t)tt.parent[t] * (1LL << 32) + (int64_t)(u + 1);
-                auto it = group_of.find(key);
-                int32_t g;
-                if (it == group_of.end()) {
-                    g = (int32_t)members.size();
-                    group_of[key] = g;
-                    members.push_back({});
-                    gops.push_back({});
-                } else {
-                    g = it->second;
-                }
-                if (members[g].size() >= 8) throw std::runtime_error("internal: more than 8 siblings in an M2L group");
-                grp_of_te[te] = g;
-                slot_of_te[te] = (int32_t)members[g].size();
-                members[g].push_back(te);
+        std::vector<int64_t> tcount(hp.l_cell.size(), 0), gcount;
+        for (const PairRec& r : recs) ++tcount[r.tgt];
+        for (size_t te = 0; te < hp.l_cell.size(); ++te) {
+            if (tcount[te] == 0) continue;
+            const int32_t t = hp.l_cell[te], u = hp.l_dir[te];
+            const int64_t key = (int64_t)tt.parent[t] * (1LL << 32) + (int64_t)(u + 1);
+            auto it = group_of.find(key);
+            int32_t g;
+            if (it == group_of.end()) {
+                g = (int32_t)members.size();
+                group_of[key] = g;
+                members.push_back({});
+                gcount.push_back(0);
+            } else {
+                g = it->second;
             }
-            const int32_t s_cell = hp.m_cell[recs[i].src];
-            gops[grp_of_te[te]].push_back({slot_of_te[te], ts.parent[s_cell], hp.mhat_of_m[recs[i].src], recs[i].spec,
-                                           recs[i].code});
+            if (members[g].size() >= 8) throw std::runtime_error("internal: more than 8 siblings in an M2L group");
+            grp_of_te[te] = g;
+            slot_of_te[te] = (int32_t)members[g].size();
+            members[g].push_back((int32_t)te);
+            gcount[g] += tcount[te];
         }
+        // every group's ops in one array (CSR; their order within a group does not
+        // matter: each group's ops are sorted by a unique key below)
+        std::vector<int64_t> gop_off(members.size() + 1, 0);
+        for (size_t g = 0; g < members.size(); ++g) gop_off[g + 1] = gop_off[g] + gcount[g];
+        std::vector<Op> gop_all(recs.size());
+        {
+            std::vector<int64_t> at(gop_off.begin(), gop_off.end() - 1);
+            for (size_t i = 0; i < recs.size(); ++i) {
+                const int32_t te = recs[i].tgt, s_cell = hp.m_cell[recs[i].src];
+                gop_all[(size_t)at[grp_of_te[te]]++] = {slot_of_te[te], ts.parent[s_cell], hp.mhat_of_m[recs[i].src],
+                                                        recs[i].spec, recs[i].code};
+            }
+        }
+        auto gops_size = [&](int32_t g) { return gop_off[g + 1] - gop_off[g]; };
         // heaviest groups first
         std::vector<int32_t> gorder(members.size());
         std::iota(gorder.begin(), gorder.end(), 0);
-        std::stable_sort(gorder.begin(), gorder.end(), [&](int32_t a, int32_t b) { return gops[a].size() > gops[b].size(); });
+        std::stable_sort(gorder.begin(), gorder.end(), [&](int32_t a, int32_t b) { return gops_size(a) > gops_size(b); });
         // Chunks of each group, built by several threads over contiguous slices of
         // the group order into their own arrays (block and op offsets relative to
         // the slice), then concatenated in order: the same tables as one pass.
@@ -557,21 +606,23 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
                 const int32_t g = gorder[q];
                 out.members.insert(out.members.end(), members[g].begin(), members[g].end());
                 out.member_n.push_back((int32_t)members[g].size());
-                auto& ops = gops[g];
+                Op* const ops_b = gop_all.data() + gop_off[g];
+                Op* const ops_e = gop_all.data() + gop_off[g + 1];
                 // sources grouped by their father: a chunk then covers about one father's sons
-                std::stable_sort(ops.begin(), ops.end(), [](const Op& a, const Op& b) {
+                std::stable_sort(ops_b, ops_e, [](const Op& a, const Op& b) {
                     if (a.src_parent != b.src_parent) return a.src_parent < b.src_parent;
                     if (a.src != b.src) return a.src < b.src;
                     return a.member < b.member;
                 });
                 int32_t nchunk = 0;
                 size_t i = 0;
-                while (i < ops.size()) {
+                const size_t nops = (size_t)(ops_e - ops_b);
+                while (i < nops) {
                     specs.clear();
                     srcs.clear();
                     chunk.clear();
-                    while (i < ops.size()) {
-                        const Op& o = ops[i];
+                    while (i < nops) {
+                        const Op& o = ops_b[i];
                         const auto sp = std::find(specs.begin(), specs.end(), o.spec);
                         const bool new_sp = sp == specs.end();
                         // ops are sorted by (source father, source) and a source has one
@@ -616,17 +667,14 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         };
         // slices of about equal op counts; one thread for small plans
         const size_t ng = gorder.size();
-        int nthreads = (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency()));
-        if (recs.size() < (size_t)1 << 20) nthreads = 1;
-        if (const char* env = std::getenv("DEFMM_PLAN_THREADS")) {   // explicit count (1..8), any plan size
-            const int v = std::atoi(env);
-            if (v >= 1) nthreads = std::min(v, 8);
-        }
+        // an explicit DEFMM_PLAN_THREADS applies to any plan size (tests compare counts)
+        int nthreads = plan_threads();
+        if (recs.size() < (size_t)1 << 20 && !std::getenv("DEFMM_PLAN_THREADS")) nthreads = 1;
         std::vector<size_t> cut(1, 0);
         {
             size_t acc = 0, k = 1;
             for (size_t q = 0; q < ng && (int)k < nthreads; ++q) {
-                acc += gops[gorder[q]].size();
+                acc += (size_t)gops_size(gorder[q]);
                 if (acc * nthreads >= recs.size() * k) { cut.push_back(q + 1); ++k; }
             }
             cut.push_back(ng);
@@ -654,22 +702,44 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
             for (auto& e : failed)
                 if (e) std::rethrow_exception(e);
         }
-        hp.grp_member_off.push_back(0);
-        hp.grp_chunk_off.push_back(0);
-        hp.chk_blk_off.push_back(0);
-        hp.chk_op.reserve(recs.size());
-        for (const Slice& sl : slices) {
-            hp.grp_members.insert(hp.grp_members.end(), sl.members.begin(), sl.members.end());
-            for (int32_t n : sl.member_n) hp.grp_member_off.push_back(hp.grp_member_off.back() + n);
-            for (int32_t n : sl.chunk_n) hp.grp_chunk_off.push_back(hp.grp_chunk_off.back() + n);
-            const int32_t blk0 = (int32_t)hp.chk_blk.size(), op0 = (int32_t)hp.chk_op.size();
-            hp.chk_nspec.insert(hp.chk_nspec.end(), sl.nspec.begin(), sl.nspec.end());
-            hp.chk_blk.insert(hp.chk_blk.end(), sl.blk.begin(), sl.blk.end());
-            for (int32_t e : sl.blk_end) hp.chk_blk_off.push_back(blk0 + e);
-            hp.chk_op.insert(hp.chk_op.end(), sl.op.begin(), sl.op.end());
-            for (int32_t o : sl.op_off) hp.chk_op_off.push_back(op0 + o);
+        // concatenation: every slice's part of each table at its prefix offsets, copied in parallel
+        struct Base { size_t grp, mem, chk, blk, op; };
+        std::vector<Base> base(slices.size() + 1, Base{0, 0, 0, 0, 0});
+        for (size_t j = 0; j < slices.size(); ++j) {
+            const Slice& sl = slices[j];
+            base[j + 1] = {base[j].grp + sl.member_n.size(), base[j].mem + sl.members.size(),
+                           base[j].chk + sl.nspec.size(), base[j].blk + sl.blk.size(), base[j].op + sl.op.size()};
             for (int v = 0; v < 3; ++v) hp.chk_stage_blocks[v] = std::max(hp.chk_stage_blocks[v], sl.stage[v]);
         }
+        const Base& all = base.back();
+        if (all.op > (size_t)INT32_MAX || all.blk > (size_t)INT32_MAX) throw std::runtime_error("M2L schedule too large");
+        hp.grp_members.resize(all.mem);
+        hp.grp_member_off.assign(all.grp + 1, 0);
+        hp.grp_chunk_off.assign(all.grp + 1, 0);
+        hp.chk_nspec.resize(all.chk);
+        hp.chk_blk.resize(all.blk);
+        hp.chk_blk_off.assign(all.chk + 1, 0);
+        hp.chk_op.resize(all.op);
+        hp.chk_op_off.resize(9 * all.chk);
+        parallel_slices(slices.size(), (int)slices.size(), [&](size_t j0, size_t j1) {
+            for (size_t j = j0; j < j1; ++j) {
+                const Slice& sl = slices[j];
+                const Base& b = base[j];
+                std::copy(sl.members.begin(), sl.members.end(), hp.grp_members.begin() + b.mem);
+                int32_t m = (int32_t)b.mem, ck = (int32_t)b.chk;
+                for (size_t i = 0; i < sl.member_n.size(); ++i) {
+                    m += sl.member_n[i];
+                    ck += sl.chunk_n[i];
+                    hp.grp_member_off[b.grp + i + 1] = m;
+                    hp.grp_chunk_off[b.grp + i + 1] = ck;
+                }
+                std::copy(sl.nspec.begin(), sl.nspec.end(), hp.chk_nspec.begin() + b.chk);
+                std::copy(sl.blk.begin(), sl.blk.end(), hp.chk_blk.begin() + b.blk);
+                for (size_t i = 0; i < sl.blk_end.size(); ++i) hp.chk_blk_off[b.chk + i + 1] = (int32_t)b.blk + sl.blk_end[i];
+                std::copy(sl.op.begin(), sl.op.end(), hp.chk_op.begin() + b.op);
+                for (size_t i = 0; i < sl.op_off.size(); ++i) hp.chk_op_off[9 * b.chk + i] = (int32_t)b.op + sl.op_off[i];
+            }
+        });
         // the same groups cut into blocks of at most 4 members (heaviest first)
         for (size_t gi = 0; gi + 1 < hp.grp_member_off.size(); ++gi) {
             const int nm = hp.grp_member_off[gi + 1] - hp.grp_member_off[gi];
@@ -739,46 +809,64 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
     };
     for (auto& pr : hp.p2p) push_down(pr[0], pr[1]);
     struct Unit { int32_t leaf; int64_t work; std::vector<int32_t> b, e; };
-    std::vector<Unit> units;
-    for (int32_t c = 0; c < tt.ncell(); ++c) {
-        if (!tt.leaf(c)) continue;
-        const int32_t li = (int32_t)hp.p2p_leaf.size();
-        hp.p2p_leaf.push_back(c);
-        auto& v = near[c];
-        std::sort(v.begin(), v.end(), [&](int32_t a, int32_t b) { return ts.begin[a] < ts.begin[b]; });
-        const int64_t nt = tt.end[c] - tt.begin[c];
-        // merged ranges of the leaf, then cut into units of bounded size
-        std::vector<int32_t> rb, re;
-        for (size_t i = 0; i < v.size(); ++i) {
-            const int32_t b = (int32_t)ts.begin[v[i]], e = (int32_t)ts.end[v[i]];
-            hp.p2p_interactions += nt * (int64_t)(e - b);
-            if (!re.empty() && re.back() == b) re.back() = e;
-            else { rb.push_back(b); re.push_back(e); }
-        }
-        Unit u{li, 0, {}, {}};
-        int32_t have = 0;
-        auto flush = [&]() {
-            if (!u.b.empty()) { u.work = nt * (int64_t)have; units.push_back(u); }
-            u = Unit{li, 0, {}, {}};
-            have = 0;
-        };
-        for (size_t k = 0; k < rb.size(); ++k) {
-            int32_t b = rb[k];
-            while (b < re[k]) {
-                if (have == kP2PUnitSources || (int)u.b.size() == kP2PUnitRanges) flush();
-                const int32_t take = std::min(re[k] - b, kP2PUnitSources - have);
-                u.b.push_back(b);
-                u.e.push_back(b + take);
-                have += take;
-                b += take;
+    for (int32_t c = 0; c < tt.ncell(); ++c)
+        if (tt.leaf(c)) hp.p2p_leaf.push_back(c);
+    // each leaf's units, independent per leaf: slices of the leaves on several threads,
+    // concatenated in leaf order
+    const size_t nleaf = hp.p2p_leaf.size();
+    const int nth = hp.p2p.size() >= ((size_t)1 << 18) ? plan_threads() : 1;
+    std::vector<std::vector<Unit>> units_of(nth);
+    std::vector<int64_t> inter_of(nth, 0);
+    parallel_slices((size_t)nth, nth, [&](size_t j0, size_t j1) {
+        for (size_t j = j0; j < j1; ++j) {   // slice j of the leaves
+            const size_t l0 = nleaf * j / nth, l1 = nleaf * (j + 1) / nth;
+            std::vector<Unit>& units = units_of[j];
+            int64_t inter = 0;
+            for (size_t lix = l0; lix < l1; ++lix) {
+                const int32_t li = (int32_t)lix, c = hp.p2p_leaf[lix];
+                auto& v = near[c];
+                std::sort(v.begin(), v.end(), [&](int32_t a, int32_t b) { return ts.begin[a] < ts.begin[b]; });
+                const int64_t nt = tt.end[c] - tt.begin[c];
+                // merged ranges of the leaf, then cut into units of bounded size
+                std::vector<int32_t> rb, re;
+                for (size_t i = 0; i < v.size(); ++i) {
+                    const int32_t b = (int32_t)ts.begin[v[i]], e = (int32_t)ts.end[v[i]];
+                    inter += nt * (int64_t)(e - b);
+                    if (!re.empty() && re.back() == b) re.back() = e;
+                    else { rb.push_back(b); re.push_back(e); }
+                }
+                Unit u{li, 0, {}, {}};
+                int32_t have = 0;
+                auto flush = [&]() {
+                    if (!u.b.empty()) { u.work = nt * (int64_t)have; units.push_back(u); }
+                    u = Unit{li, 0, {}, {}};
+                    have = 0;
+                };
+                for (size_t k = 0; k < rb.size(); ++k) {
+                    int32_t b = rb[k];
+                    while (b < re[k]) {
+                        if (have == kP2PUnitSources || (int)u.b.size() == kP2PUnitRanges) flush();
+                        const int32_t take = std::min(re[k] - b, kP2PUnitSources - have);
+                        u.b.push_back(b);
+                        u.e.push_back(b + take);
+                        have += take;
+                        b += take;
+                    }
+                }
+                if (u.b.empty() && units_for_leaf_empty(units, li)) {
+                    // a leaf without near sources still owns one (empty) unit: its sums are zero
+                    units.push_back(Unit{li, 0, {}, {}});
+                } else {
+                    flush();
+                }
             }
+            inter_of[j] = inter;
         }
-        if (u.b.empty() && units_for_leaf_empty(units, li)) {
-            // a leaf without near sources still owns one (empty) unit: its sums are zero
-            units.push_back(Unit{li, 0, {}, {}});
-        } else {
-            flush();
-        }
+    });
+    std::vector<Unit> units;
+    for (int j = 0; j < nth; ++j) {
+        hp.p2p_interactions += inter_of[j];
+        for (Unit& u : units_of[j]) units.push_back(std::move(u));
     }
     // heaviest units first, so that the last blocks to start are short ones
     std::stable_sort(units.begin(), units.end(), [](const Unit& a, const Unit& b) { return a.work > b.work; });
