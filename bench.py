@@ -57,18 +57,20 @@ SAMPLE_N = 16000          # cpu_baseline: ~10-20 s of single-core oracle work
 ORACLE_S_PER_POINT = 6e-4  # measured oracle cost on this recipe, used to size samples
 
 
-# the row M2L kernel and its launch (which blocks serve which groups)
-M2L_REGIONS = [("// The same group schedule with rows of samples",
+# the row M2L kernel and its launch (which blocks serve which groups) in kernels.cu, and the
+# plan's M2L schedule (chunks) in plan.cpp
+M2L_REGIONS = [("kernels.cu", "// The same group schedule with rows of samples",
                 "// Ring depth S and the dynamic shared memory of the per-sample M2L kernel"),
-               ("// The Hadamard M2L + F2L of one apply", "cudaError_t launch_wait_probe")]
+               ("kernels.cu", "// The Hadamard M2L + F2L of one apply", "cudaError_t launch_wait_probe"),
+               ("plan.cpp", "    // ---- M2L groups and chunks", "    // ---- M2M per parent level")]
 
 
 def m2l_rows_source_sha():
-    """sha256 (first 16 hex) of the row M2L kernel's and its launch's source text in kernels.cu."""
+    """sha256 (first 16 hex) of the row M2L kernel's, its launch's and the M2L schedule's source text."""
     import hashlib
-    src = open(os.path.join(ROOT, "paper_2202_04894_gb300", "csrc", "kernels.cu")).read()
     h = hashlib.sha256()
-    for begin, end in M2L_REGIONS:
+    for name, begin, end in M2L_REGIONS:
+        src = open(os.path.join(ROOT, "paper_2202_04894_gb300", "csrc", name)).read()
         a = src.index(begin)
         h.update(src[a:src.index(end, a)].encode())
     return h.hexdigest()[:16]

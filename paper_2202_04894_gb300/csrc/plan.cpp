@@ -538,9 +538,12 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         }
     // ---- M2L groups and chunks (sibling targets sharing a father and a direction)
     {
-        // blocks per chunk: about 22 KB of complex64 for N <= 8; for longer DFTs
-        // up to 8, as long as two stages of complex128 fit in shared memory
-        int max_blocks = hp.N <= 8 ? std::max(2, std::min(31, 22528 / (hp.NFpad * 8)))
+        // blocks per chunk: about 35 KB of complex64 for N <= 8 (13 blocks for N = 7:
+        // two stages of the row kernel still fit three blocks of 7 members per SM, and
+        // each staged block serves more pairs; measured against 8 to 24 blocks on the
+        // 10^6-point sphere, cube and ellipsoid); for longer DFTs up to 8, as long as
+        // two stages of complex128 fit in shared memory
+        int max_blocks = hp.N <= 8 ? std::max(2, std::min(31, 35840 / (hp.NFpad * 8)))
                                    : std::max(2, std::min(8, 115200 / (hp.NFpad * 16)));
         if (chunk_blocks > 0) max_blocks = std::max(2, std::min(max_blocks, chunk_blocks));   // may only shrink
         hp.chk_max_blocks = max_blocks;
