@@ -288,6 +288,14 @@ defmm_status upload(defmm_plan_s* pl, const std::vector<double>& X, const std::v
     c.chk_op_off = (const int32_t*)P(o_coo); c.chk_op = (const int32_t*)P(o_co);
     c.chk_max_blocks = hp.chk_max_blocks;
     for (int v = 0; v < 3; ++v) c.chk_stage_blocks[v] = hp.chk_stage_blocks[v];
+    for (int v = 0; v < 3; ++v) c.chk_stage_small[v] = 0;
+    for (size_t g = 0; g + 1 < hp.grp_member_off.size(); ++g) {
+        if (hp.grp_member_off[g + 1] - hp.grp_member_off[g] > 4) continue;
+        for (int32_t ch = hp.grp_chunk_off[g]; ch < hp.grp_chunk_off[g + 1]; ++ch) {
+            const int32_t nb = hp.chk_blk_off[ch + 1] - hp.chk_blk_off[ch], nsp = hp.chk_nspec[ch];
+            for (int v = 0; v < 3; ++v) c.chk_stage_small[v] = std::max(c.chk_stage_small[v], nsp + (1 << v) * (nb - nsp));
+        }
+    }
     c.m2l_rb = 0;
     c.m2l_members = 0;
     c.p2p_tc_min_rhs = 0;

@@ -2101,6 +2101,7 @@ cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T
                     if (fb && c.n_grp_small > 0) {
                         DevCommon cs = c;
                         cs.grp_half = c.grp_small; cs.n_grp_half = c.n_grp_small;
+                        for (int v = 0; v < 3; ++v) cs.chk_stage_blocks[v] = c.chk_stage_small[v];   // smaller chunks
                         rows_launch<T, 8, 64, 1, 1, 5, 4, 7, 4>(cs, t, w, stream, &fs);
                         ++*nlaunch;
                     }
@@ -2111,10 +2112,16 @@ cudaError_t launch_m2l(const DevCommon& c, const DevTyped<T>& t, const DevWork<T
                 else if (rb == 1) rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(c, t, w, stream, &fits);
                 else if (rb == 2) rows_launch<T, 8, 64, 1, 2, 2, 4, 7>(c, t, w, stream, &fits);
                 else rows_launch<T, 8, 64, 1, 4, 1, 4, 7>(c, t, w, stream, &fits);
+                // a stage of 4 (or 2) columns of the plan's largest chunk may not fit in
+                // shared memory: fewer columns per pass (the same sums, so the same bits)
+                if (!fits && rb == 4) rows_launch<T, 8, 64, 1, 2, 2, 4, 7>(c, t, w, stream, &fits);
+                if (!fits && rb >= 2) rows_launch<T, 8, 64, 1, 1, 3, 4, 7>(c, t, w, stream, &fits);
             } else {
                 if (rb == 1) rows_launch<T, 8, 64, 1, 1, 3, 0, 0>(c, t, w, stream, &fits);
                 else if (rb == 2) rows_launch<T, 8, 64, 1, 2, 2, 0, 0>(c, t, w, stream, &fits);
                 else rows_launch<T, 8, 64, 1, 4, 1, 0, 0>(c, t, w, stream, &fits);
+                if (!fits && rb == 4) rows_launch<T, 8, 64, 1, 2, 2, 0, 0>(c, t, w, stream, &fits);
+                if (!fits && rb >= 2) rows_launch<T, 8, 64, 1, 1, 3, 0, 0>(c, t, w, stream, &fits);
             }
         } else {
             if (p == 4 && N == 7) rows_launch<T, 8, 64, 1, 1, 1, 4, 7>(c, t, w, stream, &fits);

@@ -53,6 +53,7 @@ struct DevCommon {
     const int32_t *chk_blk_off, *chk_nspec, *chk_blk, *chk_op_off, *chk_op;
     int chk_max_blocks;
     int chk_stage_blocks[3];  // largest stage (blocks) for 1, 2, 4 right-hand sides per pass
+    int chk_stage_small[3];   // the same over the chunks of groups of at most 4 siblings
     int m2l_rb;               // right-hand sides per M2L pass (0: chosen from nrhs and N)
     int m2l_members;          // members per M2L block: 4, 8, 12 (4 or 8 by group size), 14 (4, 7
                               // or 8 by group size), 0 (default)

@@ -547,6 +547,10 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
                                    : std::max(2, std::min(8, 115200 / (hp.NFpad * 16)));
         if (chunk_blocks > 0) max_blocks = std::max(2, std::min(max_blocks, chunk_blocks));   // may only shrink
         hp.chk_max_blocks = max_blocks;
+        // groups of at most 4 siblings run in blocks of 4 members, five per SM: their
+        // chunks keep about 22 KB (8 blocks for N = 7) so that two stages still fit
+        const int max_blocks_small = hp.N <= 8 ? std::min(max_blocks, std::max(2, std::min(31, 22528 / (hp.NFpad * 8))))
+                                               : max_blocks;
         struct Op { int32_t member, src_parent, src, spec, code; };
         std::unordered_map<int64_t, int32_t> group_of;   // (father cell, direction) -> group
         std::vector<std::vector<int32_t>> members;        // local expansion ids
@@ -607,6 +611,7 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
             std::vector<ChunkOp> chunk, by_member;
             for (size_t q = q0; q < q1; ++q) {
                 const int32_t g = gorder[q];
+                const int budget = members[g].size() <= 4 ? max_blocks_small : max_blocks;
                 out.members.insert(out.members.end(), members[g].begin(), members[g].end());
                 out.member_n.push_back((int32_t)members[g].size());
                 Op* const ops_b = gop_all.data() + gop_off[g];
@@ -632,7 +637,7 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
                         // father, so each source's ops form one run
                         const bool new_src = srcs.empty() || srcs.back() != o.src;
                         const int need = (int)specs.size() + (int)srcs.size() + (new_sp ? 1 : 0) + (new_src ? 1 : 0);
-                        if (!chunk.empty() && need > max_blocks) break;
+                        if (!chunk.empty() && need > budget) break;
                         const int32_t sb = (int32_t)(sp - specs.begin());
                         if (new_sp) specs.push_back(o.spec);
                         if (new_src) srcs.push_back(o.src);
