@@ -733,8 +733,12 @@ __global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const t
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int p = PC ? PC : c.p, N = NC ? NC : c.N, P3 = p * p * p, NF = N * N * N, NFpad = c.NFpad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ C tws[16];
-    if (threadIdx.x < N) tws[threadIdx.x] = mk(t.tw[threadIdx.x].x, -t.tw[threadIdx.x].y);   // e^{-2 pi i m / N}
+    // twm[m * p + b] = e^{-2 pi i m b / N}: the twiddle of output m and input b of a pruned line
+    __shared__ C twm[16 * 8];
+    for (int i = threadIdx.x; i < N * p; i += blockDim.x) {
+        const int m = i / p, b = i - m * p, q = (m * b) % N;
+        twm[i] = mk(t.tw[q].x, -t.tw[q].y);
+    }
     __syncthreads();
     const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;   // (item, right-hand side)
     const int64_t item = wid / R;
@@ -751,14 +755,14 @@ __global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const t
         for (int i = lane; i < p * p * N; i += 32) {
             const int xx = i % N, rest = i / N;  // rest = bz*p + by
             C s = czero<C>();
-            for (int b = 0; b < p; ++b) cfma(s, A[rest * p + b], tws[(xx * b) % N]);
+            for (int b = 0; b < p; ++b) cfma(s, A[rest * p + b], twm[xx * p + b]);
             B[i] = s;
         }
         __syncwarp();
         for (int i = lane; i < p * N * N; i += 32) {
             const int xx = i % N, yy = (i / N) % N, bz = i / (N * N);
             C s = czero<C>();
-            for (int b = 0; b < p; ++b) cfma(s, B[(bz * p + b) * N + xx], tws[(yy * b) % N]);
+            for (int b = 0; b < p; ++b) cfma(s, B[(bz * p + b) * N + xx], twm[yy * p + b]);
             D[i] = s;
         }
         __syncwarp();
@@ -767,7 +771,7 @@ __global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const t
             C s = czero<C>();
             if (i < NF) {
                 const int xy = i % (N * N), zz = i / (N * N);
-                for (int b = 0; b < p; ++b) cfma(s, D[b * N * N + xy], tws[(zz * b) % N]);
+                for (int b = 0; b < p; ++b) cfma(s, D[b * N * N + xy], twm[zz * p + b]);
             }
             out[i] = s;
         }
