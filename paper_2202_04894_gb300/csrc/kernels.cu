@@ -733,12 +733,8 @@ __global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const t
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int p = PC ? PC : c.p, N = NC ? NC : c.N, P3 = p * p * p, NF = N * N * N, NFpad = c.NFpad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // twm[m * p + b] = e^{-2 pi i m b / N}: the twiddle of output m and input b of a pruned line
-    __shared__ C twm[16 * 8];
-    for (int i = threadIdx.x; i < N * p; i += blockDim.x) {
-        const int m = i / p, b = i - m * p, q = (m * b) % N;
-        twm[i] = mk(t.tw[q].x, -t.tw[q].y);
-    }
+    __shared__ C tws[16];
+    if (threadIdx.x < N) tws[threadIdx.x] = mk(t.tw[threadIdx.x].x, -t.tw[threadIdx.x].y);   // e^{-2 pi i m / N}
     __syncthreads();
     const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;   // (item, right-hand side)
     const int64_t item = wid / R;
@@ -755,14 +751,22 @@ __global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const t
         for (int i = lane; i < p * p * N; i += 32) {
             const int xx = i % N, rest = i / N;  // rest = bz*p + by
             C s = czero<C>();
-            for (int b = 0; b < p; ++b) cfma(s, A[rest * p + b], twm[xx * p + b]);
+            for (int b = 0, w = 0; b < p; ++b) {   // w = xx * b mod N
+                cfma(s, A[rest * p + b], tws[w]);
+                w += xx;
+                w -= w >= N ? N : 0;
+            }
             B[i] = s;
         }
         __syncwarp();
         for (int i = lane; i < p * N * N; i += 32) {
             const int xx = i % N, yy = (i / N) % N, bz = i / (N * N);
             C s = czero<C>();
-            for (int b = 0; b < p; ++b) cfma(s, B[(bz * p + b) * N + xx], twm[yy * p + b]);
+            for (int b = 0, w = 0; b < p; ++b) {   // w = yy * b mod N
+                cfma(s, B[(bz * p + b) * N + xx], tws[w]);
+                w += yy;
+                w -= w >= N ? N : 0;
+            }
             D[i] = s;
         }
         __syncwarp();
@@ -771,7 +775,11 @@ __global__ void __launch_bounds__(256) k_m2f(DevCommon c, DevTyped<T> t, const t
             C s = czero<C>();
             if (i < NF) {
                 const int xy = i % (N * N), zz = i / (N * N);
-                for (int b = 0; b < p; ++b) cfma(s, D[b * N * N + xy], twm[zz * p + b]);
+                for (int b = 0, w = 0; b < p; ++b) {   // w = zz * b mod N
+                    cfma(s, D[b * N * N + xy], tws[w]);
+                    w += zz;
+                    w -= w >= N ? N : 0;
+                }
             }
             out[i] = s;
         }
@@ -1183,7 +1191,11 @@ __global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c,
                 for (int q = l; q < N * p * p; q += TPM) {  // y
                     const int ax = q % p, ay = (q / p) % p, zz = q / (p * p);
                     C s = czero<C>();
-                    for (int k = 0; k < N; ++k) cfma(s, Tx[(zz * N + k) * p + ax], tws[(k * ay) % N]);
+                    for (int k = 0, w = 0; k < N; ++k) {   // w = k * ay mod N
+                        cfma(s, Tx[(zz * N + k) * p + ax], tws[w]);
+                        w += ay;
+                        w -= w >= N ? N : 0;
+                    }
                     Ty[q] = s;
                 }
             __syncthreads();
@@ -1191,7 +1203,11 @@ __global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c,
                 for (int a = l; a < P3; a += TPM) {  // z, crop, 1/N^3
                     const int ax = a % p, ay = (a / p) % p, az = a / (p * p);
                     C s = czero<C>();
-                    for (int k = 0; k < N; ++k) cfma(s, Ty[(k * p + ay) * p + ax], tws[(k * az) % N]);
+                    for (int k = 0, w = 0; k < N; ++k) {   // w = k * az mod N
+                        cfma(s, Ty[(k * p + ay) * p + ax], tws[w]);
+                        w += az;
+                        w -= w >= N ? N : 0;
+                    }
                     L[((int64_t)te * R + r0 + rr) * P3 + a] = cscale(s, scale);
                 }
             __syncthreads();   // Tx, Ty reused by the next right-hand side / the next pass's ring
