@@ -448,6 +448,23 @@ def main():
                 "ms": phase_avg["m2l"], "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic_source": "profiles/m2l_rows_sphere300k_kD128_p4.md, DRAM bytes per pair x pairs"}
     roof = p2p_roof if dominant == "p2p" else m2l_roof
+    # the M2L phase under three more views: operand reads from shared memory (a gathered
+    # spectrum sample and a multipole sample, 16 B per sample-pair and column, against
+    # 128 B per clock per SM), the DRAM traffic it really moves, and its compulsory bytes
+    # (each Fourier multipole read once, each local expansion written once, the spectra once)
+    m2l_s = phase_avg["m2l"] * 1e-3
+    smem_bytes = info["n_m2l_pairs"] * NF * 16 * R
+    smem_peak = sms * 128 * sm_max * 1e6 / 1e9
+    compulsory = (info["n_fourier"] * info["fft_n"] ** 3 + info["n_local"] * P3) * csz * R + info["n_spectra"] * NF * csz
+    m2l_views = {
+        "smem_operands": {"achieved": smem_bytes / m2l_s / 1e9, "peak": smem_peak, "unit": "GB/s",
+                          "frac": smem_bytes / m2l_s / 1e9 / smem_peak,
+                          "peak_source": "%d SMs x 128 B/clk at %.0f MHz" % (sms, sm_max)},
+        "dram_measured": None if m2l_traffic is None else
+        {"achieved": m2l_traffic / m2l_s / 1e9, "peak": peak_gbs, "unit": "GB/s",
+         "frac": m2l_traffic / m2l_s / 1e9 / peak_gbs},
+        "compulsory": {"achieved": compulsory / m2l_s / 1e9, "peak": peak_gbs, "unit": "GB/s",
+                       "frac": compulsory / m2l_s / 1e9 / peak_gbs}}
 
     cpu, vs_oracle = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD and not args.n:
@@ -484,7 +501,7 @@ def main():
                            "p2p": "tensor cores (tcgen05)" if args.p2p_tensor_cores else "cuda cores",
                            "parallelism": ("sharded targets, all-reduce of p" if sharded else "replicas") if world > 1
                            else "single"},
-                "roofline": roof, "m2l_roofline": m2l_roof, "p2p_roofline": p2p_roof,
+                "roofline": roof, "m2l_roofline": m2l_roof, "m2l_views": m2l_views, "p2p_roofline": p2p_roof,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(X) * R * csz,
                         "d2h_bytes_per_step": len(X) * R * csz, "ms_per_step": statistics.mean(e2e_ms)},
