@@ -640,6 +640,9 @@ defmm_status defmm_plan_create(const double* X, int64_t nx, const double* Y, int
     } catch (const std::bad_alloc&) {
         delete pl;
         return fail(DEFMM_ERR_OOM, "host allocation while building the plan");
+    } catch (const DeviceFailure& ex) {
+        delete pl;
+        return fail(ex.out_of_memory ? DEFMM_ERR_OOM : DEFMM_ERR_CUDA, ex.what());
     } catch (const std::exception& ex) {
         delete pl;
         return fail(DEFMM_ERR_ARG, ex.what());
@@ -714,6 +717,9 @@ defmm_status defmm_plan_create_union(int ngeo, const double* const* X, const int
     } catch (const std::bad_alloc&) {
         delete pl;
         return fail(DEFMM_ERR_OOM, "host allocation while building the plan");
+    } catch (const DeviceFailure& ex) {
+        delete pl;
+        return fail(ex.out_of_memory ? DEFMM_ERR_OOM : DEFMM_ERR_CUDA, ex.what());
     } catch (const std::exception& ex) {
         delete pl;
         return fail(DEFMM_ERR_ARG, ex.what());

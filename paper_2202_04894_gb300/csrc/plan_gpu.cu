@@ -41,15 +41,18 @@ template <typename V> struct DBuf {
         if (p) cudaFree(p);
         p = nullptr;
         n = count;
-        if (count > 0 && cudaMalloc(&p, sizeof(V) * (size_t)count) != cudaSuccess)
-            throw std::runtime_error("device allocation failed while building the plan");
+        if (count > 0 && cudaMalloc(&p, sizeof(V) * (size_t)count) != cudaSuccess) {
+            cudaGetLastError();
+            throw DeviceFailure("device allocation failed while building the plan", true);
+        }
     }
     void swap(DBuf& o) { std::swap(p, o.p); std::swap(n, o.n); }
 };
 
 void ck(cudaError_t e, const char* what) {
-    if (e != cudaSuccess) throw std::runtime_error(std::string("plan construction on the device: ") + what + ": " +
-                                                   cudaGetErrorString(e));
+    if (e != cudaSuccess)
+        throw DeviceFailure(std::string("plan construction on the device: ") + what + ": " + cudaGetErrorString(e),
+                            e == cudaErrorMemoryAllocation);
 }
 
 unsigned grid_for(int64_t n, int threads) {
@@ -609,10 +612,16 @@ __global__ void k_mark_keys(const int32_t* __restrict__ pr, const int32_t* __res
 // ------------------------------------------------------------ the front end
 void device_front(const double* X, int64_t nx, const double* Y, int64_t ny, int ncrit, HostPlan& hp,
                   cudaStream_t st, double* device_ms) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    ck(cudaEventCreate(&e0), "event");
-    ck(cudaEventCreate(&e1), "event");
-    ck(cudaEventRecord(e0, st), "event");
+    struct Events {   // released on every exit
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    ck(cudaEventCreate(&ev.a), "event");
+    ck(cudaEventCreate(&ev.b), "event");
+    ck(cudaEventRecord(ev.a, st), "event");
     device_tree(X, nx, hp.corner, hp.side, ncrit, hp.tt, st);
     if (Y) device_tree(Y, ny, hp.corner, hp.side, ncrit, hp.ts_own, st);
     const Tree& tt = hp.tt;
@@ -701,13 +710,11 @@ void device_front(const double* X, int64_t nx, const double* Y, int64_t ny, int 
         for (uint64_t k : marks[0]) hp.marks_t[(size_t)(k >> 27)].push_back((int32_t)(k & ((1u << 27) - 1)));
         for (uint64_t k : marks[1]) hp.marks_s[(size_t)(k >> 27)].push_back((int32_t)(k & ((1u << 27) - 1)));
     }
-    ck(cudaEventRecord(e1, st), "event");
-    ck(cudaEventSynchronize(e1), "event");
+    ck(cudaEventRecord(ev.b, st), "event");
+    ck(cudaEventSynchronize(ev.b), "event");
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    ck(cudaEventElapsedTime(&ms, ev.a, ev.b), "event");
     if (device_ms) *device_ms = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
 }
 
 }  // namespace defmm
