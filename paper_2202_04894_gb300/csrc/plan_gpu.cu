@@ -36,6 +36,8 @@ template <typename V> struct DBuf {
     DBuf() = default;
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept { swap(o); }
+    DBuf& operator=(DBuf&& o) noexcept { swap(o); return *this; }
     ~DBuf() { if (p) cudaFree(p); }
     void alloc(int64_t count) {
         if (p) cudaFree(p);
@@ -431,17 +433,25 @@ __global__ void k_dtt_write(const int32_t* __restrict__ ft, const int32_t* __res
 
 // Breadth-first Alg. 1 from (root, root): the pairs of level l are handled in
 // frontier order, each producing an M2L pair, a P2P pair or its son pairs (the
-// next frontier).  M2L pairs are returned with direction -2 (set later).
+// next frontier).  The M2L pairs of every level stay on the device (levels in
+// order, pairs of a level in frontier order) for the direction and mark passes;
+// the P2P pairs go to hp.p2p.
+struct LevelPairs {
+    int level;
+    int64_t n;
+    DBuf<int32_t> pr;   // 2 per pair: target cell, source cell
+};
+
 void device_dtt(const DevTree& dt, const DevTree& ds, const std::vector<MacLevel>& macs, HostPlan& hp,
-                std::vector<int32_t>& m2l_level, cudaStream_t st) {
+                std::vector<LevelPairs>& m2l_levels, cudaStream_t st) {
     DBuf<int32_t> ft, fs;
     ft.alloc(1);
     fs.alloc(1);
     const int32_t zero = 0;
     ck(cudaMemcpyAsync(ft.p, &zero, 4, cudaMemcpyHostToDevice, st), "frontier");
     ck(cudaMemcpyAsync(fs.p, &zero, 4, cudaMemcpyHostToDevice, st), "frontier");
-    int64_t nf = 1;
-    std::vector<int32_t> buf;
+    int64_t nf = 1, total = 0;
+    std::vector<int32_t> pbuf;
     for (int l = 0; nf > 0; ++l) {
         if (l >= (int)macs.size()) throw std::runtime_error("internal: traversal deeper than the trees");
         DBuf<int64_t> nm, np, nk, om, op, ok;
@@ -453,21 +463,23 @@ void device_dtt(const DevTree& dt, const DevTree& ds, const std::vector<MacLevel
         const int64_t cm = scan_excl(nm.p, om.p, nf, st);
         const int64_t cp = scan_excl(np.p, op.p, nf, st);
         const int64_t ck_ = scan_excl(nk.p, ok.p, nf, st);
-        if ((int64_t)hp.m2l.size() + cm > (int64_t(1) << 31) - 2) throw std::runtime_error("too many M2L pairs");
-        DBuf<int32_t> m2l, p2p, kt, ks;
-        m2l.alloc(2 * cm); p2p.alloc(2 * cp); kt.alloc(ck_); ks.alloc(ck_);
+        total += cm;
+        if (total > (int64_t(1) << 31) - 2) throw std::runtime_error("too many M2L pairs");
+        m2l_levels.emplace_back();
+        LevelPairs& lp = m2l_levels.back();
+        lp.level = l;
+        lp.n = cm;
+        lp.pr.alloc(2 * cm);
+        DBuf<int32_t> p2p, kt, ks;
+        p2p.alloc(2 * cp); kt.alloc(ck_); ks.alloc(ck_);
         k_dtt_write<<<grid_for(nf, 256), 256, 0, st>>>(ft.p, fs.p, nf, om.p, op.p, ok.p, nm.p, np.p, nk.p,
-                                                       dt.first_child.p, ds.first_child.p, ds.nchild.p, m2l.p, p2p.p,
+                                                       dt.first_child.p, ds.first_child.p, ds.nchild.p, lp.pr.p, p2p.p,
                                                        kt.p, ks.p);
         ck(cudaGetLastError(), "traversal write");
-        buf.clear();
-        to_host(buf, m2l.p, 2 * cm, st);
-        std::vector<int32_t> pbuf;
+        pbuf.clear();
         to_host(pbuf, p2p.p, 2 * cp, st);
         ck(cudaStreamSynchronize(st), "traversal level");
-        for (int64_t j = 0; j < cm; ++j) hp.m2l.push_back({buf[2 * j], buf[2 * j + 1], -2});
         for (int64_t j = 0; j < cp; ++j) hp.p2p.push_back({pbuf[2 * j], pbuf[2 * j + 1]});
-        m2l_level.resize(hp.m2l.size(), l);
         ft.swap(kt);
         fs.swap(ks);
         nf = ck_;
@@ -563,6 +575,27 @@ __global__ void k_offset_keys(const int32_t* __restrict__ pr, const int32_t* __r
     idx[i] = i;
 }
 
+__global__ void k_fill_level(int32_t* __restrict__ lev, int64_t n, int32_t l) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) lev[i] = l;
+}
+
+// max over the pairs of max(|tx - sx|, |ty - sy|, |tz - sz|), into *out (zeroed by the caller)
+__global__ void k_max_offset(const int32_t* __restrict__ pr, int64_t n, const int32_t* __restrict__ tix,
+                             const int32_t* __restrict__ tiy, const int32_t* __restrict__ tiz,
+                             const int32_t* __restrict__ six, const int32_t* __restrict__ siy,
+                             const int32_t* __restrict__ siz, unsigned long long* __restrict__ out) {
+    unsigned long long m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t t = pr[2 * i], s = pr[2 * i + 1];
+        const int64_t ax = llabs((int64_t)tix[t] - six[s]), ay = llabs((int64_t)tiy[t] - siy[s]),
+                      az = llabs((int64_t)tiz[t] - siz[s]);
+        m = max(m, (unsigned long long)max(ax, max(ay, az)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 // first[i] = 1 where sorted key i differs from key i - 1
 __global__ void k_first_of_run(const uint64_t* __restrict__ key, int64_t n, int64_t* __restrict__ first) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -638,37 +671,45 @@ void device_front(const double* X, int64_t nx, const double* Y, int64_t ny, int 
     }
     hp.m2l.clear();
     hp.p2p.clear();
-    std::vector<int32_t> plev;
-    device_dtt(dt, ds, macs, hp, plev, st);
+    std::vector<LevelPairs> levels;
+    device_dtt(dt, ds, macs, hp, levels, st);
 
-    // directions of the high-frequency pairs: one search per distinct (level, offset)
-    std::vector<int32_t> hf_pair, hf_lev;
-    std::vector<int64_t> hf_at;
-    int64_t kmax = 0;
-    for (size_t i = 0; i < hp.m2l.size(); ++i) {
-        if (!hp.lv.hf[plev[i]]) { hp.m2l[i][2] = -1; continue; }
-        const int32_t t = hp.m2l[i][0], s = hp.m2l[i][1];
-        hf_pair.push_back(t);
-        hf_pair.push_back(s);
-        hf_lev.push_back(plev[i]);
-        hf_at.push_back((int64_t)i);
-        const int64_t ax = std::llabs((int64_t)tt.ix[t] - ts.ix[s]), ay = std::llabs((int64_t)tt.iy[t] - ts.iy[s]),
-                      az = std::llabs((int64_t)tt.iz[t] - ts.iz[s]);
-        kmax = std::max(kmax, std::max(ax, std::max(ay, az)));
+    // the high-frequency pairs, concatenated on the device in level order
+    int64_t nh = 0, nall = 0;
+    for (const LevelPairs& lp : levels) {
+        nall += lp.n;
+        if (hp.lv.hf[lp.level]) nh += lp.n;
     }
-    const int64_t nh = (int64_t)hf_lev.size();
     hp.marks_t.assign(tt.ncell(), {});
     hp.marks_s.assign(ts.ncell(), {});
+    std::vector<int32_t> dir;
     if (nh > 0) {
-        int B = 1;
-        while ((int64_t(1) << B) < 2 * kmax + 1) ++B;
-        if (5 + 3 * B > 64) throw std::runtime_error("M2L offsets too large for the device plan");
         DBuf<int32_t> dpr, dlev, ddir;
         dpr.alloc(2 * nh);
         dlev.alloc(nh);
         ddir.alloc(nh);
-        ck(cudaMemcpyAsync(dpr.p, hf_pair.data(), 8 * (size_t)nh, cudaMemcpyHostToDevice, st), "pairs");
-        ck(cudaMemcpyAsync(dlev.p, hf_lev.data(), 4 * (size_t)nh, cudaMemcpyHostToDevice, st), "pairs");
+        int64_t o = 0;
+        for (const LevelPairs& lp : levels) {
+            if (!hp.lv.hf[lp.level] || lp.n == 0) continue;
+            ck(cudaMemcpyAsync(dpr.p + 2 * o, lp.pr.p, 8 * (size_t)lp.n, cudaMemcpyDeviceToDevice, st), "pairs");
+            k_fill_level<<<grid_for(lp.n, 256), 256, 0, st>>>(dlev.p + o, lp.n, lp.level);
+            ck(cudaGetLastError(), "pair levels");
+            o += lp.n;
+        }
+        DBuf<unsigned long long> dk;
+        dk.alloc(1);
+        ck(cudaMemsetAsync(dk.p, 0, sizeof(unsigned long long), st), "offsets");
+        k_max_offset<<<std::min<unsigned>(grid_for(nh, 256), 4096), 256, 0, st>>>(
+            dpr.p, nh, dt.ix.p, dt.iy.p, dt.iz.p, ds.ix.p, ds.iy.p, ds.iz.p, dk.p);
+        ck(cudaGetLastError(), "offsets");
+        std::vector<unsigned long long> kv;
+        to_host(kv, dk.p, 1, st);
+        ck(cudaStreamSynchronize(st), "offsets");
+        const int64_t kmax = (int64_t)kv[0];
+        int B = 1;
+        while ((int64_t(1) << B) < 2 * kmax + 1) ++B;
+        if (5 + 3 * B > 64) throw std::runtime_error("M2L offsets too large for the device plan");
+        // directions: one search per distinct (level, offset)
         DBuf<uint64_t> key, ukey;
         DBuf<int64_t> idx, first, pos;
         key.alloc(nh);
@@ -688,7 +729,6 @@ void device_front(const double* X, int64_t nx, const double* Y, int64_t ny, int 
         ck(cudaGetLastError(), "best directions");
         k_scatter_dir<<<grid_for(nh, 256), 256, 0, st>>>(idx.p, first.p, pos.p, nh, udir.p, ddir.p);
         ck(cudaGetLastError(), "directions");
-        std::vector<int32_t> dir;
         to_host(dir, ddir.p, nh, st);
         // Alg. 2 marks, deduplicated on the device: (cell, direction) of each end of the pairs
         std::vector<uint64_t> marks[2];
@@ -703,12 +743,26 @@ void device_front(const double* X, int64_t nx, const double* Y, int64_t ny, int 
             to_host(marks[side], umk.p, nm, st);
             ck(cudaStreamSynchronize(st), "marks");
         }
-        for (int64_t j = 0; j < nh; ++j) {
-            if (dir[(size_t)j] < 0) throw std::runtime_error("internal: no direction for an M2L offset");
-            hp.m2l[(size_t)hf_at[j]][2] = dir[(size_t)j];
-        }
         for (uint64_t k : marks[0]) hp.marks_t[(size_t)(k >> 27)].push_back((int32_t)(k & ((1u << 27) - 1)));
         for (uint64_t k : marks[1]) hp.marks_s[(size_t)(k >> 27)].push_back((int32_t)(k & ((1u << 27) - 1)));
+    }
+    // the M2L list in traversal order: direction -1 on low-frequency levels
+    hp.m2l.resize((size_t)nall);
+    std::vector<int32_t> pbuf;
+    int64_t at = 0, oh = 0;
+    for (const LevelPairs& lp : levels) {
+        if (lp.n == 0) continue;
+        pbuf.clear();
+        to_host(pbuf, lp.pr.p, 2 * lp.n, st);
+        ck(cudaStreamSynchronize(st), "pairs");
+        const bool hf = hp.lv.hf[lp.level];
+        for (int64_t j = 0; j < lp.n; ++j) {
+            const int32_t d = hf ? dir[(size_t)(oh + j)] : -1;
+            if (hf && d < 0) throw std::runtime_error("internal: no direction for an M2L offset");
+            hp.m2l[(size_t)(at + j)] = {pbuf[2 * j], pbuf[2 * j + 1], d};
+        }
+        at += lp.n;
+        if (hf) oh += lp.n;
     }
     ck(cudaEventRecord(ev.b, st), "event");
     ck(cudaEventSynchronize(ev.b), "event");
