@@ -1080,31 +1080,57 @@ __global__ void __launch_bounds__(MAXM * TPM + 32, MINB) k_m2l_rows(DevCommon c,
 #pragma unroll
                 for (int x = 0; x < NX; ++x) acc[j][rr][x] = czero<C>();
         if (producer) {
-            if (lane == 0) {
-                for (int k = 0; k < nchunks; ++k) {
-                    const uint32_t u = use0 + k;
-                    const int st = u % S;
+            // The whole warp feeds the ring: lane 9 holds a chunk's spectrum count and
+            // lanes 10-11 its block range (loaded two chunks ahead), lane b the id of
+            // its block b (loaded one chunk ahead, in parallel across the lanes); each
+            // lane issues the bulk copies of its blocks after lane 0 has armed the
+            // stage's mbarrier (whose phase then completes only when every block has
+            // landed), so no global load latency sits between two chunks' copies.
+            auto scalars = [&](int cc) -> int {
+                if (lane == 9) return __ldg(&c.chk_nspec[cc]);
+                if (lane == 10 || lane == 11) return __ldg(&c.chk_blk_off[cc + lane - 10]);
+                return 0;
+            };
+            // block id of lane b of the chunk with scalars sc (b < 32)
+            auto first_ids = [&](int sc) -> int {
+                const int b0 = __shfl_sync(0xffffffffu, sc, 10), nb = __shfl_sync(0xffffffffu, sc, 11) - b0;
+                return lane < nb ? __ldg(&c.chk_blk[b0 + lane]) : 0;
+            };
+            int sc_next = nchunks > 0 ? scalars(ch0) : 0;
+            for (int k = 0; k < nchunks; ++k) {
+                const int sc = sc_next;
+                if (k + 1 < nchunks) sc_next = scalars(ch0 + k + 1);   // in flight during this chunk
+                const int ids = first_ids(sc);
+                const uint32_t u = use0 + k;
+                const int st = u % S;
+                int go = 1;
+                if (lane == 0) {
                     if (u >= (uint32_t)S && !mbar_wait(&empty[st], ((u / S) - 1) & 1)) {
                         abort_sh = 1;
                         atomicExch(c.err_flag, 1);
-                        break;
+                        go = 0;
                     }
-                    if (abort_sh) break;
-                    const int cc = ch0 + k;
-                    const int b0 = c.chk_blk_off[cc], nb = c.chk_blk_off[cc + 1] - b0, nsp = c.chk_nspec[cc];
-                    C* base = ring + (size_t)st * stage_elems;
+                    if (abort_sh) go = 0;
+                }
+                if (!__shfl_sync(0xffffffffu, go, 0)) break;
+                const int nsp = __shfl_sync(0xffffffffu, sc, 9), b0 = __shfl_sync(0xffffffffu, sc, 10);
+                const int nb = __shfl_sync(0xffffffffu, sc, 11) - b0;
+                if (lane == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_expect_tx(&full[st], (uint32_t)(nsp + (nb - nsp) * nrb) * blk_bytes);
-                    for (int b = 0; b < nb; ++b) {
-                        const int id = DEFMM_IX(c, c.chk_blk[b0 + b], b < nsp ? c.n_spec : c.n_m2f);
-                        if (b < nsp)
-                            tma_bulk_load(base + (size_t)b * NFpad, t.spec + (int64_t)id * NFpad, blk_bytes, &full[st]);
-                        else   // right-hand sides r0 .. r0+nrb-1 of one source: one contiguous copy
-                            tma_bulk_load(base + (size_t)(nsp + (b - nsp) * RB) * NFpad,
-                                          Mhat + ((int64_t)id * R + r0) * NFpad, (uint32_t)nrb * blk_bytes, &full[st]);
-                    }
-                    issued_sh = k + 1;
                 }
+                __syncwarp();
+                C* base = ring + (size_t)st * stage_elems;
+                for (int b = lane; b < nb; b += 32) {
+                    const int id = DEFMM_IX(c, b < 32 ? ids : __ldg(&c.chk_blk[b0 + b]), b < nsp ? c.n_spec : c.n_m2f);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    if (b < nsp)
+                        tma_bulk_load(base + (size_t)b * NFpad, t.spec + (int64_t)id * NFpad, blk_bytes, &full[st]);
+                    else   // right-hand sides r0 .. r0+nrb-1 of one source: one contiguous copy
+                        tma_bulk_load(base + (size_t)(nsp + (b - nsp) * RB) * NFpad,
+                                      Mhat + ((int64_t)id * R + r0) * NFpad, (uint32_t)nrb * blk_bytes, &full[st]);
+                }
+                if (lane == 0) issued_sh = k + 1;
             }
         } else if (member) {
             for (int k = 0; k < nchunks; ++k) {
