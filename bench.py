@@ -11,8 +11,10 @@ One JSON line on rank 0.  value = Mpoints*RHS/s over all ranks (replicas:
 each rank applies its own copy of the workload; there is no data-path
 collective).  With --sharded and N > 1 the ranks split the one workload
 instead (defmm_plan_set_shard: each rank computes its Morton range of target
-leaves, the upward pass replicated) and an all-reduce of p inside the timed
-region assembles the result: strong scaling.  Inputs are resident in HBM for
+leaves, the upward pass replicated), each writes its targets' potentials in
+sorted order (defmm_apply_slice), an all-gather of those slices inside the
+timed region gives every rank all of them, and defmm_assemble_slices puts
+them in the caller's order: strong scaling.  Inputs are resident in HBM for
 `value`; `e2e` times the
 host-buffer entry point (defmm_apply_host) with both copies inside.  L2 is
 flushed (a 512 MB write) before every timed step, outside the step's events.
@@ -160,18 +162,21 @@ def max_over_ranks(total_ms, dist=None, device="cpu"):
     return float(t.item())
 
 
-def exchange_shards(p, dist=None):
-    """The exchange step of the sharded apply: each rank holds its shard's
-    potentials and zeros elsewhere; an all-reduce (sum) leaves the whole result
-    on every rank (adding zeros changes no bit)."""
+def gather_slices(slice_buf, gathered, dist=None):
+    """The exchange step of the sharded apply: rank s holds its targets'
+    potentials in sorted order, slice_buf (R, ld); an all-gather leaves every
+    rank's slice at gathered[s] (gathered: (world, R, ld)) on every rank.  Each
+    rank sends its own targets only, and nothing is summed."""
+    import torch
     if dist is None:
-        return p
-    if p.is_complex():
-        v = __import__("torch").view_as_real(p)
-        dist.all_reduce(v)
-        return p
-    dist.all_reduce(p)
-    return p
+        gathered[0].copy_(slice_buf)
+        return gathered
+    parts = [gathered[s] for s in range(gathered.shape[0])]
+    if slice_buf.is_complex():
+        dist.all_gather([torch.view_as_real(t) for t in parts], torch.view_as_real(slice_buf))
+    else:
+        dist.all_gather(parts, slice_buf)
+    return gathered
 
 
 def whole_job_value(world, points, nrhs, ms_per_step):
@@ -334,8 +339,11 @@ def main():
     if args.p2p_tensor_cores:
         plan.set_tuning(p2p_tc_min_rhs=1)
     sharded = args.sharded and world > 1
-    if sharded:   # this rank computes its shard of the targets; an all-reduce assembles p
+    if sharded:   # this rank computes its shard of the targets; an all-gather of the slices assembles p
         plan.set_shard(world, rank)
+        ranges = [plan.shard_range(world, s) for s in range(world)]
+        starts = [f for f, _ in ranges] + [len(X)]
+        ld = max(1, max(n for _, n in ranges))
     info = plan.info()
     R = q.shape[1]
     qd = torch.from_numpy(np.ascontiguousarray(q)).to("cuda").to(cdt)
@@ -377,12 +385,18 @@ def main():
     torch.cuda.synchronize()
     step_ms = []
     pbuf = torch.empty((R, len(X)), dtype=cdt, device="cuda") if sharded else None
+    if sharded:
+        slice_buf = torch.empty((R, ld), dtype=cdt, device="cuda")
+        gathered = torch.empty((world, R, ld), dtype=cdt, device="cuda")
     for k in range(args.steps):
         flush.fill_(float(k))
         starts[k].record(stream)
-        plan.apply(qd, out=pbuf)
         if sharded:
-            exchange_shards(pbuf, dist)
+            plan.apply_slice(qd, out=slice_buf)
+            gather_slices(slice_buf, gathered, dist)
+            plan.assemble_slices(starts, gathered, out=pbuf)
+        else:
+            plan.apply(qd, out=pbuf)
         ends[k].record(stream)
         ends[k].synchronize()
         step_ms.append(starts[k].elapsed_time(ends[k]))
@@ -499,7 +513,7 @@ def main():
                 "config": {"workload": args.workload, "points": len(X), "kappa_d": W_["kappa_d"], "order": order,
                            "leaf": leaf, "nrhs": R, "distribution": W_["kind"], "l2": "flushed (512 MB write) before each step",
                            "p2p": "tensor cores (tcgen05)" if args.p2p_tensor_cores else "cuda cores",
-                           "parallelism": ("sharded targets, all-reduce of p" if sharded else "replicas") if world > 1
+                           "parallelism": ("sharded targets, all-gather of sorted slices" if sharded else "replicas") if world > 1
                            else "single"},
                 "roofline": roof, "m2l_roofline": m2l_roof, "m2l_views": m2l_views, "p2p_roofline": p2p_roof,
                 "cpu_baseline": cpu,

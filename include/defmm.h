@@ -376,6 +376,37 @@ defmm_status defmm_gmres(defmm_plan plan, const void* b, void* x, defmm_dtype dt
 defmm_status defmm_plan_set_shard(defmm_plan plan, int nshards, int shard, void* stream);
 defmm_status defmm_plan_shard_range(defmm_plan plan, int nshards, int shard, int64_t* first, int64_t* count);
 
+/* Exchange of a sharded apply by all-gather instead of all-reduce.  Each rank
+ * then sends only its own targets' potentials (1/nshards of p) and nothing is
+ * summed.  The paper has no multi-GPU step (Sec. 6); the split is the one above.
+ *
+ * defmm_apply_slice: defmm_apply on the plan's current shard (the whole
+ * operator when the plan is not sharded), writing only the shard's count
+ * targets (defmm_plan_shard_range), in Morton (sorted) order:
+ * slice[r * ld + j] is the potential of sorted target first + j for
+ * 0 <= j < count, column r < nrhs; entries j >= count are left untouched.
+ * q as in defmm_apply (device, nrhs columns of the caller's ny sources);
+ * slice a device buffer of nrhs * ld elements of dtype; ld >= count.  The
+ * values are bit for bit those defmm_apply writes for the same targets.
+ *
+ * defmm_assemble_slices: p (device, nrhs columns of the caller's nx targets,
+ * as defmm_apply writes it) from the slices of all nshards shards, stored one
+ * after another in `slices` (device): shard s's slice at element offset
+ * s * nrhs * ld, laid out as defmm_apply_slice writes it.  starts (host,
+ * nshards + 1 entries) are the shards' sorted-target boundaries:
+ * starts[s] = first of shard s, starts[nshards] = nx, so
+ * starts[s + 1] - starts[s] = count of shard s <= ld.  Every target of p is
+ * written once; the result equals the whole operator's defmm_apply bit for bit.
+ * Both calls only enqueue work on `stream`; the caller owns every buffer.
+ * Errors: DEFMM_ERR_ARG (NULL pointers, nrhs < 1, ld below a shard's count,
+ * starts not from 0 to nx or decreasing), DEFMM_ERR_UNSUPPORTED (dtype,
+ * host-only plan), DEFMM_ERR_BUSY, DEFMM_ERR_OOM (workspace, as defmm_apply),
+ * DEFMM_ERR_CUDA.                                                            */
+defmm_status defmm_apply_slice(defmm_plan plan, const void* q, void* slice, int64_t ld, int nrhs, defmm_dtype dtype,
+                               void* stream);
+defmm_status defmm_assemble_slices(defmm_plan plan, int nshards, const int64_t* starts, const void* slices,
+                                   int64_t ld, void* p, int nrhs, defmm_dtype dtype, void* stream);
+
 /* Frees the plan and its device memory (synchronises the device first).       */
 defmm_status defmm_destroy(defmm_plan plan);
 

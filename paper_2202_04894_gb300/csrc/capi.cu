@@ -363,12 +363,15 @@ std::once_flag g_config_once;
 cudaError_t g_config_err = cudaSuccess;
 
 template <typename T> defmm_status apply_impl(defmm_plan_s* pl, Workspace<T>& w, const void* q, void* p,
-                                               int nrhs, cudaStream_t stream) {
+                                               int nrhs, cudaStream_t stream, void* slice = nullptr,
+                                               int64_t slice_ld = 0) {
     defmm_status s = ensure_workspace<T>(pl, w, nrhs, false);
     if (s != DEFMM_OK) return s;
     DevWork<T> dw;
     dw.R = nrhs; dw.qs = w.qs; dw.ps = w.ps; dw.M = w.M; dw.Mhat = w.Mhat; dw.L = w.L; dw.nL = pl->hp.nL();
     dw.part = w.part;
+    dw.slice = static_cast<typename Cplx<T>::type*>(slice);
+    dw.slice_ld = slice_ld;
     const DevTyped<T>& typed = typed_tables(pl, (T*)nullptr);
     int launches = 0;
     const LevelList* l2l = nullptr;
@@ -793,6 +796,45 @@ defmm_status defmm_apply(defmm_plan plan, const void* q, void* p, int nrhs, defm
     if (!lk.owns_lock()) return fail(DEFMM_ERR_BUSY, "plan is in use by another thread");
     if (dtype == DEFMM_C64) return apply_impl<float>(plan, plan->wf, q, p, nrhs, (cudaStream_t)stream);
     return apply_impl<double>(plan, plan->wd, q, p, nrhs, (cudaStream_t)stream);
+}
+
+defmm_status defmm_apply_slice(defmm_plan plan, const void* q, void* slice, int64_t ld, int nrhs, defmm_dtype dtype,
+                               void* stream) {
+    if (!plan) return fail(DEFMM_ERR_ARG, "plan is NULL");
+    if (!q || !slice) return fail(DEFMM_ERR_ARG, "q and slice must be device pointers");
+    if (nrhs < 1) return fail(DEFMM_ERR_ARG, "nrhs must be >= 1");
+    if (dtype != DEFMM_C64 && dtype != DEFMM_C128) return fail(DEFMM_ERR_UNSUPPORTED, "dtype");
+    if (plan->host_only) return fail(DEFMM_ERR_UNSUPPORTED, "plan was built with DEFMM_PLAN_HOST_ONLY");
+    std::unique_lock<std::mutex> lk(plan->busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(DEFMM_ERR_BUSY, "plan is in use by another thread");
+    const int64_t count = plan->sh.nshards > 1 ? plan->sh.t1 - plan->sh.t0 : plan->hp.nx;
+    if (ld < count) return fail(DEFMM_ERR_ARG, "ld is smaller than the shard's target count");
+    if (dtype == DEFMM_C64)
+        return apply_impl<float>(plan, plan->wf, q, nullptr, nrhs, (cudaStream_t)stream, slice, ld);
+    return apply_impl<double>(plan, plan->wd, q, nullptr, nrhs, (cudaStream_t)stream, slice, ld);
+}
+
+defmm_status defmm_assemble_slices(defmm_plan plan, int nshards, const int64_t* starts, const void* slices,
+                                   int64_t ld, void* p, int nrhs, defmm_dtype dtype, void* stream) {
+    if (!plan || !starts) return fail(DEFMM_ERR_ARG, "plan and starts must not be NULL");
+    if (!slices || !p) return fail(DEFMM_ERR_ARG, "slices and p must be device pointers");
+    if (nshards < 1 || nrhs < 1) return fail(DEFMM_ERR_ARG, "nshards and nrhs must be >= 1");
+    if (dtype != DEFMM_C64 && dtype != DEFMM_C128) return fail(DEFMM_ERR_UNSUPPORTED, "dtype");
+    if (plan->host_only) return fail(DEFMM_ERR_UNSUPPORTED, "plan was built with DEFMM_PLAN_HOST_ONLY");
+    if (starts[0] != 0 || starts[nshards] != plan->hp.nx)
+        return fail(DEFMM_ERR_ARG, "starts must run from 0 to the plan's target count");
+    for (int s = 0; s < nshards; ++s) {
+        if (starts[s + 1] < starts[s]) return fail(DEFMM_ERR_ARG, "starts must not decrease");
+        if (starts[s + 1] - starts[s] > ld) return fail(DEFMM_ERR_ARG, "ld is smaller than a shard's target count");
+    }
+    const int esz = dtype == DEFMM_C64 ? 8 : 16;
+    const char* src = static_cast<const char*>(slices);
+    for (int s = 0; s < nshards; ++s) {
+        cudaError_t e = launch_unslice(src + (size_t)s * nrhs * ld * esz, ld, p, plan->common.perm_t, plan->hp.nx, nrhs,
+                                       starts[s], starts[s + 1], esz, plan->common.err_flag, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "assemble slices");
+    }
+    return DEFMM_OK;
 }
 
 defmm_status defmm_apply_host(defmm_plan plan, const void* q_host, void* p_host, int nrhs, defmm_dtype dtype,

@@ -136,6 +136,29 @@ __global__ void k_scatter(const C* __restrict__ ps, C* __restrict__ p, const int
     }
 }
 
+// A shard's potentials in sorted order: slice[r * ld + j] = ps[r * n + j0 + j].
+template <typename C>
+__global__ void k_slice(const C* __restrict__ ps, C* __restrict__ slice, int64_t n, int R, int64_t j0, int64_t j1,
+                        int64_t ld) {
+    const int64_t m = j1 - j0, total = m * R;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / m, j = i - r * m;
+        slice[r * ld + j] = ps[r * n + j0 + j];
+    }
+}
+
+// The inverse for one shard: p[r * n + perm[j0 + j]] = src[r * ld + j].
+template <typename C>
+__global__ void k_unslice(const C* __restrict__ src, int64_t ld, C* __restrict__ p, const int64_t* __restrict__ perm,
+                          int64_t n, int R, int64_t j0, int64_t j1, int* err_flag) {
+    const struct { int* err_flag; } c{err_flag};   // for the checked-build index test
+    const int64_t m = j1 - j0, total = m * R;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / m, j = i - r * m;
+        p[r * n + DEFMM_IX(c, perm[j0 + j], n)] = src[r * ld + j];
+    }
+}
+
 // ------------------------------------------------------------------ P2P
 // The hardware approximations (PTX rsqrt.approx / sin.approx / cos.approx,
 // flush-to-zero): arguments here are never subnormal (r^2 > eps_self^2 is
@@ -2227,6 +2250,19 @@ int sm_count() {
     return v;
 }
 
+cudaError_t launch_unslice(const void* src, int64_t ld, void* p, const int64_t* perm, int64_t n, int R, int64_t j0,
+                           int64_t j1, int elem_bytes, int* err_flag, cudaStream_t stream) {
+    if (j1 <= j0) return cudaSuccess;
+    const unsigned grid = (unsigned)(4 * sm_count());
+    if (elem_bytes == 8)
+        k_unslice<float2><<<grid, 256, 0, stream>>>(static_cast<const float2*>(src), ld, static_cast<float2*>(p), perm,
+                                                    n, R, j0, j1, err_flag);
+    else
+        k_unslice<double2><<<grid, 256, 0, stream>>>(static_cast<const double2*>(src), ld, static_cast<double2*>(p),
+                                                     perm, n, R, j0, j1, err_flag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wait_probe(int* flag, int spins, cudaStream_t stream) {
     k_wait_probe<<<1, 32, 0, stream>>>(flag, spins);
     return cudaGetLastError();
@@ -2402,13 +2438,18 @@ cudaError_t launch_apply(const DevCommon& c, const DevTyped<T>& t, const DevWork
         DEFMM_CHECK_LAUNCH();
     }
     DEFMM_MARK();
-    if (c.sh_on) {   // one shard: its targets, zeros elsewhere (the shards' outputs sum to the whole)
-        err = cudaMemsetAsync(p, 0, (size_t)c.nx * R * sizeof(C), stream);
-        if (err != cudaSuccess) return err;
+    if (w.slice) {   // the shard's potentials alone, in sorted order
+        const int64_t j0 = c.sh_on ? c.sh_t0 : 0, j1 = c.sh_on ? c.sh_t1 : c.nx;
+        if (j1 > j0) k_slice<C><<<sms, 256, 0, stream>>>(w.ps, w.slice, c.nx, R, j0, j1, w.slice_ld);
+    } else {
+        if (c.sh_on) {   // one shard: its targets, zeros elsewhere (the shards' outputs sum to the whole)
+            err = cudaMemsetAsync(p, 0, (size_t)c.nx * R * sizeof(C), stream);
+            if (err != cudaSuccess) return err;
+        }
+        if (!c.sh_on || c.sh_t1 > c.sh_t0)
+            k_scatter<C><<<sms, 256, 0, stream>>>(w.ps, reinterpret_cast<C*>(p), c.perm_t, c.nx, R,
+                                                  c.sh_on ? c.sh_t0 : 0, c.sh_on ? c.sh_t1 : c.nx, c.err_flag);
     }
-    if (!c.sh_on || c.sh_t1 > c.sh_t0)
-        k_scatter<C><<<sms, 256, 0, stream>>>(w.ps, reinterpret_cast<C*>(p), c.perm_t, c.nx, R,
-                                              c.sh_on ? c.sh_t0 : 0, c.sh_on ? c.sh_t1 : c.nx, c.err_flag);
     DEFMM_CHECK_LAUNCH();
     DEFMM_MARK();
 #undef DEFMM_CHECK_LAUNCH

@@ -136,6 +136,10 @@ struct DevWork {
     C* Mhat;   // [nMhat][R][NFpad]
     C* L;      // [nL][R][P3]
     int64_t nL;
+    // set: the apply writes its shard's potentials in sorted order, slice[r * slice_ld + j]
+    // for sorted target sh_t0 + j (all targets unsharded), instead of p in the caller's order
+    C* slice = nullptr;
+    int64_t slice_ld = 0;
 };
 
 struct LevelList {
@@ -154,6 +158,11 @@ constexpr int kNumPhases = 9;  // gather p2p p2m m2m m2f m2l l2l l2p scatter
 
 // One block waiting, boundedly, on an mbarrier phase nothing completes; raises *flag.
 cudaError_t launch_wait_probe(int* flag, int spins, cudaStream_t stream);
+
+// p[r * n + perm[j0 + j]] = src[r * ld + j] for 0 <= j < j1 - j0, r < R: one shard's
+// sorted-order slice put back in the caller's order (elem_bytes 8: complex64, 16: complex128).
+cudaError_t launch_unslice(const void* src, int64_t ld, void* p, const int64_t* perm, int64_t n, int R, int64_t j0,
+                           int64_t j1, int elem_bytes, int* err_flag, cudaStream_t stream);
 
 // Streaming multiprocessors of the current device (queried once per device).
 int sm_count();

@@ -26,6 +26,7 @@ EXPORTED = ["defmm_default_options", "defmm_plan_create", "defmm_apply", "defmm_
             "defmm_plan_get_tuning", "defmm_default_tune_options", "defmm_plan_autotune",
             "defmm_plan_autotune_union",
             "defmm_default_gmres_options", "defmm_gmres", "defmm_plan_set_shard", "defmm_plan_shard_range",
+            "defmm_apply_slice", "defmm_assemble_slices",
             "defmm_plan_create_union", "defmm_selftest_bounded_wait", "defmm_plan_save", "defmm_plan_load",
             "defmm_last_error"]
 PHASES = ["gather", "p2p", "p2m", "m2m", "m2f", "m2l", "l2l", "l2p", "scatter"]
@@ -148,6 +149,11 @@ def lib():
         L.defmm_plan_set_shard.restype = ctypes.c_int
         L.defmm_plan_shard_range.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.defmm_plan_shard_range.restype = ctypes.c_int
+        L.defmm_apply_slice.argtypes = [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp]
+        L.defmm_apply_slice.restype = ctypes.c_int
+        L.defmm_assemble_slices.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64), vp, i64, vp, ctypes.c_int,
+                                            ctypes.c_int, vp]
+        L.defmm_assemble_slices.restype = ctypes.c_int
         L.defmm_plan_create_union.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                               ctypes.POINTER(dbl), ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
@@ -290,12 +296,54 @@ class Plan:
     def set_shard(self, nshards: int = 1, shard: int = 0, stream=None):
         """defmm_plan_set_shard: later applies compute shard `shard` of `nshards`."""
         _check(lib().defmm_plan_set_shard(self._h, int(nshards), int(shard), _stream_handle(stream)))
+        self._shard = (int(nshards), int(shard))
 
     def shard_range(self, nshards: int, shard: int):
         """defmm_plan_shard_range: (first, count) of the shard's targets in sorted order."""
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().defmm_plan_shard_range(self._h, int(nshards), int(shard), ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def apply_slice(self, q, out=None, stream=None):
+        """defmm_apply_slice: the plan's shard of p in sorted target order.
+
+        q: complex64/complex128 CUDA tensor (ny,) or (ny, R).  out: None or a CUDA
+        tensor (R, ld) with ld >= the shard's target count, whose columns j < count
+        receive the potentials.  Returns that (R, ld) tensor."""
+        import torch
+        qm = q.reshape(-1, 1) if q.dim() == 1 else q
+        if qm.shape[0] != self.ny:
+            raise ValueError("q has %d rows, plan has %d sources" % (qm.shape[0], self.ny))
+        R = qm.shape[1]
+        qc = qm.t().contiguous()
+        if out is None:
+            out = torch.empty((R, self.shard_range(*getattr(self, "_shard", (1, 0)))[1]), dtype=qm.dtype,
+                              device=qm.device)
+        if out.dim() != 2 or out.shape[0] != R or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (R, ld) tensor")
+        _check(lib().defmm_apply_slice(self._h, ctypes.c_void_p(qc.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       out.shape[1], R, C64 if qm.dtype == torch.complex64 else C128,
+                                       _stream_handle(stream)))
+        self._last_q = qc
+        return out
+
+    def assemble_slices(self, starts, slices, out=None, stream=None):
+        """defmm_assemble_slices: p (nx, R) from every shard's slice.
+
+        starts: the nshards + 1 sorted-target boundaries; slices: a contiguous CUDA
+        tensor (nshards, R, ld) holding shard s's apply_slice output at [s]."""
+        import torch
+        nsh, R, ld = slices.shape
+        st = (ctypes.c_int64 * len(starts))(*[int(v) for v in starts])
+        if len(starts) != nsh + 1:
+            raise ValueError("starts must have nshards + 1 entries")
+        if not slices.is_contiguous():
+            raise ValueError("slices must be contiguous")
+        pc = out if out is not None else torch.empty((R, self.nx), dtype=slices.dtype, device=slices.device)
+        _check(lib().defmm_assemble_slices(self._h, nsh, st, ctypes.c_void_p(slices.data_ptr()), ld,
+                                           ctypes.c_void_p(pc.data_ptr()), R,
+                                           C64 if slices.dtype == torch.complex64 else C128, _stream_handle(stream)))
+        return pc.t()
 
     def save(self, path):
         """defmm_plan_save: the plan's host tables and coordinates to a file."""

@@ -50,34 +50,47 @@ def test_reference_arm_other_ranks_exit_quietly():
     assert r.stdout.strip() == ""
 
 
-def _shard_worker(rank, world, port, out, full, ranges):
+def _shard_worker(rank, world, port, out, full_sorted, starts):
     import numpy as np
     import torch
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
-    first, count = ranges[rank]
-    mine = np.zeros_like(full)
-    mine[first:first + count] = full[first:first + count]     # a shard's output: its rows, zeros elsewhere
-    got = bench.exchange_shards(torch.from_numpy(mine), dist)
-    np.save(out + ".%d.npy" % rank, got.numpy())
+    R = full_sorted.shape[0]
+    ld = max(starts[s + 1] - starts[s] for s in range(world))
+    mine = np.zeros((R, ld), dtype=full_sorted.dtype)      # a shard's slice: its sorted targets, padded to ld
+    mine[:, :starts[rank + 1] - starts[rank]] = full_sorted[:, starts[rank]:starts[rank + 1]]
+    gathered = torch.zeros((world, R, ld), dtype=torch.complex64)
+    bench.gather_slices(torch.from_numpy(mine), gathered, dist)
+    np.save(out + ".%d.npy" % rank, gathered.numpy())
     dist.destroy_process_group()
 
 
 def test_sharded_exchange_with_gloo(tmp_path):
-    """The exchange of the sharded apply: every rank holds its shard's rows and zeros
-    elsewhere; after the all-reduce every rank holds the whole result, unchanged bit for bit."""
+    """The exchange of the sharded apply: every rank holds its shard's potentials in
+    sorted order (a slice padded to the longest shard); after the all-gather every rank
+    holds every slice, and putting them back in the caller's order (the permutation
+    defmm_assemble_slices applies) gives the whole result, bit for bit."""
     import numpy as np
     import torch.multiprocessing as mp
     from paper_2202_04894_gb300 import defmm, workloads as W
     X = W.points("sphere", 2000, 91)
     pl = defmm.Plan(X, kappa=10.0, order=4, leaf_size=24, flags=defmm.PLAN_HOST_ONLY)
     ranges = [pl.shard_range(2, s) for s in range(2)]
+    starts = [f for f, _ in ranges] + [2000]
+    assert ranges[0][0] == 0 and ranges[0][1] == ranges[1][0] and sum(n for _, n in ranges) == 2000
+    perm = pl.table("perm_t")                         # sorted target j -> caller's index
     rng = np.random.default_rng(3)
-    full = (rng.standard_normal((2000, 3)) + 1j * rng.standard_normal((2000, 3))).astype(np.complex64)
+    full = (rng.standard_normal((3, 2000)) + 1j * rng.standard_normal((3, 2000))).astype(np.complex64)
+    full_sorted = full[:, perm]
     out = str(tmp_path / "s")
     port = 31500 + (os.getpid() % 2000)
-    mp.spawn(_shard_worker, args=(2, port, out, full, ranges), nprocs=2, join=True)
+    mp.spawn(_shard_worker, args=(2, port, out, full_sorted, starts), nprocs=2, join=True)
     for r in range(2):
-        assert np.array_equal(np.load(out + ".%d.npy" % r), full)
+        g = np.load(out + ".%d.npy" % r)
+        p = np.zeros_like(full)
+        for s in range(2):
+            n = starts[s + 1] - starts[s]
+            p[:, perm[starts[s]:starts[s + 1]]] = g[s, :, :n]
+        assert np.array_equal(p, full)
