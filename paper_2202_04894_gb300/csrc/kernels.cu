@@ -2250,6 +2250,11 @@ int sm_count() {
     return v;
 }
 
+cudaError_t launch_wait_probe(int* flag, int spins, cudaStream_t stream) {
+    k_wait_probe<<<1, 32, 0, stream>>>(flag, spins);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unslice(const void* src, int64_t ld, void* p, const int64_t* perm, int64_t n, int R, int64_t j0,
                            int64_t j1, int elem_bytes, int* err_flag, cudaStream_t stream) {
     if (j1 <= j0) return cudaSuccess;
@@ -2260,11 +2265,6 @@ cudaError_t launch_unslice(const void* src, int64_t ld, void* p, const int64_t* 
     else
         k_unslice<double2><<<grid, 256, 0, stream>>>(static_cast<const double2*>(src), ld, static_cast<double2*>(p),
                                                      perm, n, R, j0, j1, err_flag);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_wait_probe(int* flag, int spins, cudaStream_t stream) {
-    k_wait_probe<<<1, 32, 0, stream>>>(flag, spins);
     return cudaGetLastError();
 }
 
