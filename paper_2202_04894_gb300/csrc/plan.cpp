@@ -368,18 +368,26 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
     const Tree& ts = hp.ts();
 
     // ---- Alg. 3 blank downward pass on both trees (the marks of Alg. 2 are in place)
+    // Cells are stored level by level; a level's cells are independent (each writes
+    // its own marks and those of its sons), so a level's cells run on several threads.
     auto downward = [&](const Tree& tr, std::vector<std::vector<int32_t>>& marks) {
-        for (int32_t c = 0; c < tr.ncell(); ++c) {
+        auto cell = [&](int32_t c) {
             int l = tr.level[c];
             if (!lv.hf[l]) {
                 marks[c].assign(1, -1);
-                continue;
+                return;
             }
             sort_unique(marks[c]);
-            if (!lv.hf[l + 1]) continue;
+            if (!lv.hf[l + 1]) return;
             for (int32_t a = 0; a < tr.nchild[c]; ++a)
                 for (int32_t u : marks[c])
                     marks[tr.first_child[c] + a].push_back((int32_t)direction_father(lv.E(l), u));
+        };
+        for (const auto& lr : tr.level_range) {
+            const size_t n = (size_t)(lr.second - lr.first);
+            parallel_slices(n, n >= 4096 ? plan_threads() : 1, [&](size_t i0, size_t i1) {
+                for (size_t i = i0; i < i1; ++i) cell(lr.first + (int32_t)i);
+            });
         }
     };
     downward(tt, hp.marks_t);
@@ -480,31 +488,39 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         hp.spec_kbar.push_back({cn.kbar[0], cn.kbar[1], cn.kbar[2]});
         return sid;
     };
+    // the target and source expansion of every pair and the largest offset per level
+    // (independent per pair: slices on several threads, one maximum per slice), then
+    // the spectra in the order the pairs first use them (one pass)
     std::vector<int64_t> kmax(kNumLevels + 1, -1);
-    for (const auto& pr : hp.m2l) {
-        const int l = tt.level[pr[0]];
-        const int64_t k = std::max({std::llabs((int64_t)tt.ix[pr[0]] - ts.ix[pr[1]]),
-                                    std::llabs((int64_t)tt.iy[pr[0]] - ts.iy[pr[1]]),
-                                    std::llabs((int64_t)tt.iz[pr[0]] - ts.iz[pr[1]])});
-        kmax[l] = std::max(kmax[l], k);
+    recs.resize(hp.m2l.size());
+    {
+        const int nth = hp.m2l.size() >= ((size_t)1 << 20) ? plan_threads() : 1;
+        std::vector<std::vector<int64_t>> kmax_of(nth, std::vector<int64_t>(kNumLevels + 1, -1));
+        parallel_slices((size_t)nth, nth, [&](size_t j0, size_t j1) {
+            for (size_t j = j0; j < j1; ++j) {
+                std::vector<int64_t>& km = kmax_of[j];
+                const size_t i0 = hp.m2l.size() * j / nth, i1 = hp.m2l.size() * (j + 1) / nth;
+                for (size_t i = i0; i < i1; ++i) {
+                    const auto& pr = hp.m2l[i];
+                    const int32_t te = find_exp(hp.l_dir, hp.l_first[pr[0]], hp.l_count[pr[0]], pr[2]);
+                    const int32_t se = find_exp(hp.m_dir, hp.m_first[pr[1]], hp.m_count[pr[1]], pr[2]);
+                    recs[i] = {te, se, 0, 0, (int32_t)i};
+                    const int l = tt.level[pr[0]];
+                    const int64_t k = std::max({std::llabs((int64_t)tt.ix[pr[0]] - ts.ix[pr[1]]),
+                                                std::llabs((int64_t)tt.iy[pr[0]] - ts.iy[pr[1]]),
+                                                std::llabs((int64_t)tt.iz[pr[0]] - ts.iz[pr[1]])});
+                    km[l] = std::max(km[l], k);
+                }
+            }
+        });
+        for (const auto& km : kmax_of)
+            for (int l = 0; l <= kNumLevels; ++l) kmax[l] = std::max(kmax[l], km[l]);
     }
     std::vector<std::vector<int32_t>> by_offset(kNumLevels + 1);   // sid * 64 + code, -1: not yet seen
     for (int l = 0; l <= kNumLevels; ++l) {
         const int64_t w = 2 * kmax[l] + 1;
         if (kmax[l] >= 0 && w * w * w <= (int64_t(1) << 22)) by_offset[l].assign((size_t)(w * w * w), -1);
     }
-    // the target and source expansion of every pair (independent per pair: slices on
-    // several threads), then the spectra in the order the pairs first use them (one pass)
-    recs.resize(hp.m2l.size());
-    parallel_slices(hp.m2l.size(), hp.m2l.size() >= ((size_t)1 << 20) ? plan_threads() : 1,
-                    [&](size_t i0, size_t i1) {
-        for (size_t i = i0; i < i1; ++i) {
-            const auto& pr = hp.m2l[i];
-            const int32_t te = find_exp(hp.l_dir, hp.l_first[pr[0]], hp.l_count[pr[0]], pr[2]);
-            const int32_t se = find_exp(hp.m_dir, hp.m_first[pr[1]], hp.m_count[pr[1]], pr[2]);
-            recs[i] = {te, se, 0, 0, (int32_t)i};
-        }
-    });
     for (size_t i = 0; i < hp.m2l.size(); ++i) {
         auto& pr = hp.m2l[i];
         int32_t t = pr[0], s = pr[1];
