@@ -342,7 +342,7 @@ def main():
     if sharded:   # this rank computes its shard of the targets; an all-gather of the slices assembles p
         plan.set_shard(world, rank)
         ranges = [plan.shard_range(world, s) for s in range(world)]
-        starts = [f for f, _ in ranges] + [len(X)]
+        shard_starts = [f for f, _ in ranges] + [len(X)]
         ld = max(1, max(n for _, n in ranges))
     info = plan.info()
     R = q.shape[1]
@@ -394,7 +394,7 @@ def main():
         if sharded:
             plan.apply_slice(qd, out=slice_buf)
             gather_slices(slice_buf, gathered, dist)
-            plan.assemble_slices(starts, gathered, out=pbuf)
+            plan.assemble_slices(shard_starts, gathered, out=pbuf)
         else:
             plan.apply(qd, out=pbuf)
         ends[k].record(stream)
