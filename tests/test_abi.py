@@ -462,3 +462,28 @@ def test_radial_power_option():
         with pytest.raises(defmm.DefmmError) as e:
             _host_plan(X, kappa=2.0, order=4, leaf_size=16, radial_power=bad)
         assert e.value.status == 1
+
+
+def test_slice_exchange_argument_checks():
+    """defmm_apply_slice / defmm_assemble_slices on the host: NULL pointers and
+    nrhs < 1 are argument errors, starts must run from 0 to nx without decreasing
+    and fit ld, and a host-only plan cannot apply (no GPU involved)."""
+    import ctypes
+    X = W.points("sphere", 400, 7)
+    pl = _host_plan(X, kappa=3.0, order=4, leaf_size=16)
+    L = defmm.lib()
+    h = pl._h
+    i64 = ctypes.c_int64
+
+    def starts(*v):
+        return (i64 * len(v))(*v)
+
+    assert L.defmm_apply_slice(h, None, None, 10, 1, defmm.C64, None) == 1
+    assert L.defmm_apply_slice(h, ctypes.c_void_p(8), ctypes.c_void_p(8), 400, 0, defmm.C64, None) == 1
+    assert L.defmm_apply_slice(h, ctypes.c_void_p(8), ctypes.c_void_p(8), 400, 1, 7, None) == 5
+    assert L.defmm_apply_slice(h, ctypes.c_void_p(8), ctypes.c_void_p(8), 400, 1, defmm.C64, None) == 5
+    dummy = ctypes.c_void_p(8)
+    assert L.defmm_assemble_slices(h, 2, None, dummy, 400, dummy, 1, defmm.C64, None) == 1
+    assert L.defmm_assemble_slices(h, 2, starts(0, 200, 400), None, 400, dummy, 1, defmm.C64, None) == 1
+    assert L.defmm_assemble_slices(h, 0, starts(0, 400), dummy, 400, dummy, 1, defmm.C64, None) == 1
+    assert L.defmm_assemble_slices(h, 2, starts(0, 200, 400), dummy, 400, dummy, 1, defmm.C128, None) == 5
