@@ -826,12 +826,22 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         if (tt.leaf(c) && hp.l_count[c] > 0) hp.l2p_cells.push_back(c);
 
     // ---- P2P: per target leaf, the source ranges of its near pairs
+    // each near pair's source cell to every target leaf under its target cell (the
+    // order within a leaf does not matter: a leaf's list is sorted below)
     std::vector<std::vector<int32_t>> near(tt.ncell());
-    std::function<void(int32_t, int32_t)> push_down = [&](int32_t t, int32_t s) {
-        if (tt.leaf(t)) { near[t].push_back(s); return; }
-        for (int32_t a = 0; a < tt.nchild[t]; ++a) push_down(tt.first_child[t] + a, s);
-    };
-    for (auto& pr : hp.p2p) push_down(pr[0], pr[1]);
+    {
+        std::vector<int32_t> stack;
+        for (const auto& pr : hp.p2p) {
+            if (tt.leaf(pr[0])) { near[pr[0]].push_back(pr[1]); continue; }
+            stack.assign(1, pr[0]);
+            while (!stack.empty()) {
+                const int32_t t = stack.back();
+                stack.pop_back();
+                if (tt.leaf(t)) { near[t].push_back(pr[1]); continue; }
+                for (int32_t a = 0; a < tt.nchild[t]; ++a) stack.push_back(tt.first_child[t] + a);
+            }
+        }
+    }
     struct Unit { int32_t leaf; int64_t work; std::vector<int32_t> b, e; };
     for (int32_t c = 0; c < tt.ncell(); ++c)
         if (tt.leaf(c)) hp.p2p_leaf.push_back(c);
@@ -894,6 +904,13 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
     }
     // heaviest units first, so that the last blocks to start are short ones
     std::stable_sort(units.begin(), units.end(), [](const Unit& a, const Unit& b) { return a.work > b.work; });
+    {
+        size_t nr = 0;
+        for (const Unit& u : units) nr += u.b.size();
+        hp.p2p_sbeg.reserve(nr); hp.p2p_send.reserve(nr); hp.p2p_soff.reserve(nr);
+        hp.p2p_unit_leaf.reserve(units.size()); hp.p2p_part.reserve(units.size());
+        hp.p2p_unit_off.reserve(units.size() + 1);
+    }
     hp.p2p_unit_off.push_back(0);
     std::vector<std::vector<int32_t>> leaf_units(hp.p2p_leaf.size());
     int64_t parts = 0;
