@@ -262,13 +262,13 @@ static void dual_tree_traversal(HostPlan& hp) {
         }
 }
 
-// Threads for the plan's parallel passes: up to 8 (hardware permitting), or
-// DEFMM_PLAN_THREADS (1..8).
+// Threads for the plan's parallel passes: up to 16 (hardware permitting), or
+// DEFMM_PLAN_THREADS (1..16).
 static int plan_threads() {
-    int n = (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency()));
+    int n = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
     if (const char* env = std::getenv("DEFMM_PLAN_THREADS")) {
         const int v = std::atoi(env);
-        if (v >= 1) n = std::min(v, 8);
+        if (v >= 1) n = std::min(v, 16);
     }
     return n;
 }
