@@ -516,32 +516,54 @@ void build_host_plan(const double* X, int64_t nx, const double* Y, int64_t ny, d
         for (const auto& km : kmax_of)
             for (int l = 0; l <= kNumLevels; ++l) kmax[l] = std::max(kmax[l], km[l]);
     }
-    std::vector<std::vector<int32_t>> by_offset(kNumLevels + 1);   // sid * 64 + code, -1: not yet seen
+    // one dense table per level from offset to (spectrum, code), concatenated, while it stays small
+    std::vector<int64_t> tbase(kNumLevels + 2, 0);
     for (int l = 0; l <= kNumLevels; ++l) {
         const int64_t w = 2 * kmax[l] + 1;
-        if (kmax[l] >= 0 && w * w * w <= (int64_t(1) << 22)) by_offset[l].assign((size_t)(w * w * w), -1);
+        const bool dense = kmax[l] >= 0 && w * w * w <= (int64_t(1) << 22);
+        tbase[l + 1] = tbase[l] + (dense ? w * w * w : 0);
     }
-    for (size_t i = 0; i < hp.m2l.size(); ++i) {
-        auto& pr = hp.m2l[i];
-        int32_t t = pr[0], s = pr[1];
-        int l = tt.level[t];
-        int64_t kx = (int64_t)tt.ix[t] - ts.ix[s], ky = (int64_t)tt.iy[t] - ts.iy[s],
-                kz = (int64_t)tt.iz[t] - ts.iz[s];
-        int32_t sid, code;
-        if (!by_offset[l].empty()) {
+    std::vector<int32_t> by_offset((size_t)tbase[kNumLevels + 1], -1);   // sid * 64 + code, -1: not yet seen
+    auto offset_of = [&](size_t i, int* l, int64_t* kx, int64_t* ky, int64_t* kz) {
+        const int32_t t = hp.m2l[i][0], s = hp.m2l[i][1];
+        *l = tt.level[t];
+        *kx = (int64_t)tt.ix[t] - ts.ix[s];
+        *ky = (int64_t)tt.iy[t] - ts.iy[s];
+        *kz = (int64_t)tt.iz[t] - ts.iz[s];
+    };
+    // each pair's table slot (independent per pair; -1 where its level has no table), kept in
+    // recs[i].spec until the spectra are numbered in the order the pairs first use them
+    parallel_slices(hp.m2l.size(), hp.m2l.size() >= ((size_t)1 << 20) ? plan_threads() : 1,
+                    [&](size_t i0, size_t i1) {
+        for (size_t i = i0; i < i1; ++i) {
+            int l;
+            int64_t kx, ky, kz;
+            offset_of(i, &l, &kx, &ky, &kz);
             const int64_t K = kmax[l], w = 2 * K + 1;
-            int32_t& v = by_offset[l][(size_t)(((kx + K) * w + (ky + K)) * w + (kz + K))];
+            recs[i].spec = tbase[l + 1] > tbase[l] ? (int32_t)(tbase[l] + ((kx + K) * w + (ky + K)) * w + (kz + K)) : -1;
+        }
+    });
+    for (size_t i = 0; i < hp.m2l.size(); ++i) {
+        PairRec& r = recs[i];
+        if (r.tgt < 0 || r.src < 0) throw std::runtime_error("internal: M2L expansion missing");
+        int32_t sid, code;
+        if (r.spec >= 0) {
+            int32_t& v = by_offset[(size_t)r.spec];
             if (v < 0) {
+                int l;
+                int64_t kx, ky, kz;
+                offset_of(i, &l, &kx, &ky, &kz);
                 sid = spectrum_of(l, kx, ky, kz, &code);
                 v = sid * 64 + code;
             }
             sid = v >> 6;
             code = v & 63;
         } else {
+            int l;
+            int64_t kx, ky, kz;
+            offset_of(i, &l, &kx, &ky, &kz);
             sid = spectrum_of(l, kx, ky, kz, &code);
         }
-        PairRec& r = recs[i];
-        if (r.tgt < 0 || r.src < 0) throw std::runtime_error("internal: M2L expansion missing");
         r.spec = sid;
         r.code = code;
         is_src[r.src] = 1;
