@@ -169,7 +169,8 @@ def _rows(a):
 def test_plan_tables_equal_oracle_above_2_20_pairs(monkeypatch):
     """A plan of more than 2^20 M2L pairs (its chunks built by several threads): tree, DTT
     pairs with directions and effective expansions equal the oracle's (Sec. 4.2.1, Alg. 1-3)
-    bit for bit, and the schedule tables are the same whether one thread or eight build them."""
+    bit for bit, and the schedule and near-field tables are the same whether one, eight or
+    sixteen threads build them."""
     X = W.points("sphere", 60000, 7)
     D = float(np.max(X.max(0) - X.min(0)))
     kw = dict(kappa=60.0 / D, order=4, leaf_size=32)
@@ -189,12 +190,13 @@ def test_plan_tables_equal_oracle_above_2_20_pairs(monkeypatch):
     assert np.array_equal(pl.table("mult").reshape(-1, 2), mult)
     assert np.array_equal(pl.table("local").reshape(-1, 2), loc)
     names = ("grp_member_off", "grp_members", "grp_chunk_off", "chk_blk_off", "chk_nspec", "chk_blk",
-             "chk_op_off", "chk_op")
+             "chk_op_off", "chk_op", "mult", "local", "p2p_unit_leaf", "p2p_unit_off", "p2p_unit_ranges")
     threaded = {k: pl.table(k) for k in names}
-    monkeypatch.setenv("DEFMM_PLAN_THREADS", "1")
-    one = _host_plan(X, **kw)
-    for k in names:
-        assert np.array_equal(one.table(k), threaded[k]), k
+    for nth in ("1", "16"):
+        monkeypatch.setenv("DEFMM_PLAN_THREADS", nth)
+        other = _host_plan(X, **kw)
+        for k in names:
+            assert np.array_equal(other.table(k), threaded[k]), (nth, k)
 
 
 def test_degenerate_inputs_host_plan():
